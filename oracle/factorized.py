@@ -1,0 +1,305 @@
+"""Factorized CG and BiCGSTAB (Algorithms 4.1, 4.2) and the Lyapunov variant (Sec. 4.3).
+
+Test infrastructure only (see ``oracle/__init__``).  Plain numpy/scipy in
+float64.  Iterates are kept as X = V X^ W^T with V, W orthonormal bases of the
+block Krylov spaces K_k(A, C1) and K_k(B^T, C2) (Corollary 3.2) and X^ small.
+
+Readings of points the paper leaves open (each also listed in the design notes):
+
+* Thin QR of C1, C2 and of every new basis block: Householder (LAPACK via
+  ``numpy.linalg.qr``) with the sign fixed so that diag(R) > 0, which makes
+  the factors unique.
+* Block Lanczos (Sec. 3.2, used by Algorithm 4.1): three-term recurrence in
+  the order Y = A V_j - V_{j-1} H_{j-1,j}; H_{j,j} = V_j^T Y;
+  Y -= V_j H_{j,j}; Y = V_{j+1} H_{j+1,j}, with H_{j-1,j} = H_{j,j-1}^T and
+  no reorthogonalisation (the paper's per-step cost O(nnz s + n s^2) excludes
+  it).
+* Block Arnoldi (Sec. 3.2, used by Algorithm 4.2): block classical
+  Gram-Schmidt applied twice (BCGS2): H1 = V^T Y, Y -= V H1, H2 = V^T Y,
+  Y -= V H2, H_{:,j} = H1 + H2.
+* Krylov exhaustion: with nu^2 = ||H_{1:j,j}||_F^2 + ||Y||_F^2 (Y after
+  projection), a block with ||Y||_F <= delta * nu is replaced by a zero block
+  and H_{j+1,j} = 0; all later blocks are zero too.  A partial rank loss
+  (some diag(R) <= delta * nu but not all of Y) is a breakdown.
+* The convergence test uses "<=" as the algorithms print it.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+
+class Breakdown(Exception):
+    pass
+
+
+def thin_qr(Y: np.ndarray):
+    """Y = Q R, Q with orthonormal columns, R upper triangular with diag(R) >= 0."""
+    Q, R = np.linalg.qr(Y, mode="reduced")
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :], R * d[:, None]
+
+
+def pad(M: np.ndarray, t: int) -> np.ndarray:
+    """[[M, O], [O, O]]: M in the top-left corner of a matrix t rows/cols larger."""
+    out = np.zeros((M.shape[0] + t, M.shape[1] + t))
+    out[: M.shape[0], : M.shape[1]] = M
+    return out
+
+
+def inner(X: np.ndarray, Y: np.ndarray) -> float:
+    """<X, Y> = tr(X^T Y); equals the inner product of the large matrices (eq. 3.6)."""
+    return float(np.sum(X * Y))
+
+
+class BlockKrylovBasis:
+    """Orthonormal basis V_k of K_k(A, C) with A V_k = V_{k+1} H_{k+1,k} (eq. 3.4).
+
+    ``kind`` = "lanczos" (A symmetric, block tridiagonal H) or "arnoldi"
+    (block upper Hessenberg H, BCGS2).  ``A`` is anything supporting ``A @ Y``.
+    """
+
+    def __init__(self, A, C: np.ndarray, kind: str, delta: float = 1e-12):
+        self.A = A
+        self.kind = kind
+        self.delta = delta
+        self.s = C.shape[1]
+        V1, R = thin_qr(C)
+        self.R0 = R  # C = V_1 R
+        self.blocks: List[np.ndarray] = [V1]
+        self.H = np.zeros((self.s, 0))  # H_{j+1, j} grows to (j+1)s x js
+        self.exhausted = False
+
+    @property
+    def nblocks(self) -> int:
+        return len(self.blocks)
+
+    def V(self, k: Optional[int] = None) -> np.ndarray:
+        k = self.nblocks if k is None else k
+        return np.hstack(self.blocks[:k])
+
+    def Hk(self, rows: int, cols: int) -> np.ndarray:
+        """H_{rows, cols} (block sizes), the leading (rows s) x (cols s) part."""
+        return self.H[: rows * self.s, : cols * self.s]
+
+    def step(self) -> None:
+        """The j-th step: from V_j build V_{j+1} and the j-th block column of H."""
+        s = self.s
+        j = self.nblocks
+        Hn = np.zeros(((j + 1) * s, j * s))
+        Hn[: self.H.shape[0], : self.H.shape[1]] = self.H
+        if self.exhausted:
+            self.blocks.append(np.zeros_like(self.blocks[0]))
+            self.H = Hn
+            return
+        Vj = self.blocks[j - 1]
+        Y = np.asarray(self.A @ Vj, dtype=np.float64)
+        if self.kind == "lanczos":
+            if j >= 2:
+                Hn[(j - 2) * s:(j - 1) * s, (j - 1) * s:j * s] = Hn[(j - 1) * s:j * s, (j - 2) * s:(j - 1) * s].T
+                Y = Y - self.blocks[j - 2] @ Hn[(j - 2) * s:(j - 1) * s, (j - 1) * s:j * s]
+            Hjj = Vj.T @ Y
+            Y = Y - Vj @ Hjj
+            Hn[(j - 1) * s:j * s, (j - 1) * s:j * s] = Hjj
+        elif self.kind == "arnoldi":
+            Vall = self.V(j)
+            H1 = Vall.T @ Y
+            Y = Y - Vall @ H1
+            H2 = Vall.T @ Y
+            Y = Y - Vall @ H2
+            Hn[: j * s, (j - 1) * s:j * s] = H1 + H2
+        else:
+            raise ValueError(self.kind)
+        ynorm = np.linalg.norm(Y)
+        nu = np.sqrt(np.sum(Hn[: j * s, (j - 1) * s:j * s] ** 2) + ynorm**2)
+        if ynorm <= self.delta * nu:
+            self.exhausted = True
+            self.blocks.append(np.zeros_like(Vj))
+            self.H = Hn
+            return
+        Q, R = thin_qr(Y)
+        if np.min(np.abs(np.diag(R))) <= self.delta * nu:
+            raise Breakdown(f"partial rank loss in block {j + 1}")
+        Hn[j * s:(j + 1) * s, (j - 1) * s:j * s] = R
+        self.blocks.append(Q)
+        self.H = Hn
+
+
+def small_sylvester(H: np.ndarray, Z: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Factored Sylvester operator, eq. (3.7):
+
+    A (V_k Z W_k^T) + (V_k Z W_k^T) B = V_{k+1} ([H Z, O] + [Z G^T; O]) W_{k+1}^T
+    with H = H_{k+1,k}, G = G_{k+1,k} ((k+1)s x ks) and Z (ks x ks).
+    """
+    r = Z.shape[0]
+    rp = H.shape[0]
+    out = np.zeros((rp, rp))
+    out[:, :r] += H @ Z
+    out[:r, :] += Z @ G.T
+    return out
+
+
+def small_lyapunov(H: np.ndarray, Z: np.ndarray) -> np.ndarray:
+    """Sec. 4.3: with B = A^T, C2 = C1 and Z symmetric, [Z H^T; O] = [H Z, O]^T,
+    so one product gives the operator: M + M^T with M = [H Z, O]."""
+    r = Z.shape[0]
+    rp = H.shape[0]
+    M = np.zeros((rp, rp))
+    M[:, :r] = H @ Z
+    return M + M.T
+
+
+@dataclasses.dataclass
+class FactorizedResult:
+    V: np.ndarray
+    Xhat: np.ndarray
+    W: np.ndarray
+    iters: int
+    status: str  # "converged" | "maxit" | "breakdown"
+    history: List[float]
+    Xhats: Optional[List[np.ndarray]] = None  # X^_k for k = 0.. (if kept)
+    basisA: Optional[BlockKrylovBasis] = None
+    basisB: Optional[BlockKrylovBasis] = None
+
+    def X(self) -> np.ndarray:
+        return self.V @ self.Xhat @ self.W.T
+
+    def X_at(self, k: int, width_blocks: int) -> np.ndarray:
+        """X_k = V X^_k W^T using the first ``width_blocks`` blocks of each basis."""
+        V = self.basisA.V(width_blocks)
+        W = (self.basisB or self.basisA).V(width_blocks)
+        return V @ self.Xhats[k] @ W.T
+
+
+def factorized_cg(A, B, C1: np.ndarray, C2: Optional[np.ndarray], tol: float, maxit: int,
+                  lyapunov: bool = False, delta: float = 1e-12, keep_iterates: bool = False) -> FactorizedResult:
+    """Algorithm 4.1 (A, B symmetric positive definite).
+
+    With ``lyapunov`` (B = A^T, C2 = C1; pass B = None, C2 = None) one basis
+    serves both sides and the operator is ``small_lyapunov`` (Sec. 4.3).
+    Returns V_{k+1}, X^_{k+1}, W_{k+1} (width (k+1)s) at convergence.
+    """
+    s = C1.shape[1]
+    bA = BlockKrylovBasis(A, C1, "lanczos", delta)
+    bB = bA if lyapunov else BlockKrylovBasis(B.T, C2, "lanczos", delta)
+    RL, RR = bA.R0, bB.R0
+    Rh = RL @ RR.T
+    if lyapunov:
+        Rh = 0.5 * (Rh + Rh.T)
+    Xh = np.zeros((0, 0))
+    Ph = Rh.copy()
+    rho = inner(Rh, Rh)
+    r0 = np.sqrt(inner(Rh, Rh))
+    hist = [1.0]
+    xs = [Xh.copy()] if keep_iterates else None
+
+    def result(k, status):
+        w = Xh.shape[0] // s
+        return FactorizedResult(bA.V(w), Xh, bB.V(w), k, status, hist, xs, bA, None if lyapunov else bB)
+
+    for k in range(maxit):
+        # block Lanczos step k+1 on both sides -> V_{k+2}, H_{k+2,k+1}
+        try:
+            bA.step()
+            if not lyapunov:
+                bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        H = bA.Hk(k + 2, k + 1)
+        if lyapunov:
+            Qh = small_lyapunov(H, Ph)
+        else:
+            Qh = small_sylvester(H, Ph, bB.Hk(k + 2, k + 1))
+        r = (k + 1) * s
+        pq = inner(Ph, Qh[:r, :r])
+        if not np.isfinite(pq) or pq <= 0.0:
+            return result(k, "breakdown")
+        alpha = rho / pq
+        Xh = pad(Xh, s) + alpha * Ph
+        Rh = pad(Rh, s) - alpha * Qh
+        rn = np.sqrt(inner(Rh, Rh))
+        hist.append(rn / r0)
+        if xs is not None:
+            xs.append(Xh.copy())
+        if not np.isfinite(rn):
+            return result(k + 1, "breakdown")
+        if rn <= r0 * tol:
+            return result(k + 1, "converged")
+        rho_new = inner(Rh, Rh)
+        beta = rho_new / rho
+        rho = rho_new
+        Ph = Rh + pad(beta * Ph, s)
+    return result(maxit, "maxit")
+
+
+def factorized_bicgstab(A, B, C1: np.ndarray, C2: np.ndarray, tol: float, maxit: int, delta: float = 1e-12,
+                        keep_iterates: bool = False, callback=None) -> FactorizedResult:
+    """Algorithm 4.2 (general A, B; block Arnoldi bases).
+
+    Returns V_{2k+2}, X^_{k+1}, W_{2k+2} (width (2k+2)s) at convergence.
+    """
+    s = C1.shape[1]
+    bA = BlockKrylovBasis(A, C1, "arnoldi", delta)
+    bB = BlockKrylovBasis(B.T, C2, "arnoldi", delta)
+    Rh = bA.R0 @ bB.R0.T
+    Ph = Rh.copy()
+    Rt = Rh.copy()  # shadow residual R~_0 (s x s)
+    rho = inner(Rt, Rh)
+    Xh = np.zeros((0, 0))
+    r0 = np.sqrt(inner(Rh, Rh))
+    hist = [1.0]
+    xs = [Xh.copy()] if keep_iterates else None
+
+    def result(k, status):
+        w = Xh.shape[0] // s
+        return FactorizedResult(bA.V(w), Xh, bB.V(w), k, status, hist, xs, bA, bB)
+
+    for k in range(maxit):
+        # Arnoldi step 2k+1 on both sides -> V_{2k+2}, H_{2k+2,2k+1}
+        try:
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        Qh = small_sylvester(bA.Hk(2 * k + 2, 2 * k + 1), Ph, bB.Hk(2 * k + 2, 2 * k + 1))
+        d = inner(Rt, Qh[:s, :s])
+        if not np.isfinite(d) or d == 0.0:
+            return result(k, "breakdown")
+        alpha = rho / d
+        Sh = pad(Rh, s) - alpha * Qh
+        # Arnoldi step 2k+2 -> V_{2k+3}, H_{2k+3,2k+2}
+        try:
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        Th = small_sylvester(bA.Hk(2 * k + 3, 2 * k + 2), Sh, bB.Hk(2 * k + 3, 2 * k + 2))
+        rs = (2 * k + 2) * s
+        tt = inner(Th, Th)
+        if not np.isfinite(tt) or tt == 0.0:
+            return result(k, "breakdown")
+        omega = inner(Th[:rs, :rs], Sh) / tt
+        if omega == 0.0:
+            return result(k, "breakdown")
+        Xh = pad(Xh, 2 * s) + pad(alpha * Ph, s) + omega * Sh
+        Rh = pad(Sh, s) - omega * Th
+        rn = np.sqrt(inner(Rh, Rh))
+        hist.append(rn / r0)
+        if callback is not None:
+            callback(k + 1, rn / r0)
+        if xs is not None:
+            xs.append(Xh.copy())
+        if not np.isfinite(rn):
+            return result(k + 1, "breakdown")
+        if rn <= r0 * tol:
+            return result(k + 1, "converged")
+        rho_new = inner(Rt, Rh[:s, :s])
+        if rho_new == 0.0:
+            return result(k + 1, "breakdown")
+        beta = (alpha / omega) * (rho_new / rho)
+        rho = rho_new
+        Ph = Rh + beta * (pad(Ph, 2 * s) - omega * pad(Qh, s))
+    return result(maxit, "maxit")

@@ -1,0 +1,96 @@
+"""Matrix-oriented CG and BiCGSTAB on full n x m iterates (Algorithms 2.1, 2.2).
+
+Test infrastructure only (see ``oracle/__init__``).  These are the plain
+definitions that the factorized methods are mathematically equivalent to
+(Sec. 5.1): every vector operation of CG / BiCGSTAB on the Kronecker system
+(eq. 1.2) is done on the n x m matrix it represents (Sec. 2):
+addition -> matrix addition, inner product -> <X, Y> = tr(X^T Y),
+matrix-vector product -> the Sylvester operator A X + X B.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+
+def sylvester_op(A, B, X: np.ndarray) -> np.ndarray:
+    """A X + X B (the Sylvester operator, Sec. 2).  A, B scipy sparse or dense."""
+    return np.asarray(A @ X) + np.asarray((B.T @ X.T).T)
+
+
+def inner(X: np.ndarray, Y: np.ndarray) -> float:
+    """<X, Y> = tr(X^T Y) (Sec. 2)."""
+    return float(np.sum(X * Y))
+
+
+@dataclasses.dataclass
+class FullResult:
+    X: np.ndarray
+    iters: int
+    status: str
+    history: List[float]
+    iterates: Optional[List[np.ndarray]] = None
+
+
+def cg(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False) -> FullResult:
+    """Algorithm 2.1 with X_0 = 0 (Sec. 4.1).
+
+    Stops at the first k with ||R_{k+1}|| <= ||R_0|| tol and returns X_{k+1};
+    otherwise returns X_maxit with status "maxit".
+    """
+    X = np.zeros_like(C)
+    R = C - sylvester_op(A, B, X)
+    P = R.copy()
+    rho = inner(R, R)
+    r0 = np.linalg.norm(R)
+    hist = [1.0]
+    its = [X.copy()] if keep_iterates else None
+    for k in range(maxit):
+        Q = sylvester_op(A, B, P)            # Q_k = A P_k + P_k B
+        alpha = rho / inner(P, Q)
+        X = X + alpha * P
+        R = R - alpha * Q
+        rn = np.linalg.norm(R)
+        hist.append(rn / r0)
+        if its is not None:
+            its.append(X.copy())
+        if rn <= r0 * tol:
+            return FullResult(X, k + 1, "converged", hist, its)
+        rho_new = inner(R, R)
+        beta = rho_new / rho
+        rho = rho_new
+        P = R + beta * P
+    return FullResult(X, maxit, "maxit", hist, its)
+
+
+def bicgstab(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False) -> FullResult:
+    """Algorithm 2.2 with X_0 = 0 and the shadow residual R~_0 = R_0."""
+    X = np.zeros_like(C)
+    R = C - sylvester_op(A, B, X)
+    Rt = R.copy()
+    P = R.copy()
+    rho = inner(R, Rt)
+    r0 = np.linalg.norm(R)
+    hist = [1.0]
+    its = [X.copy()] if keep_iterates else None
+    for k in range(maxit):
+        Q = sylvester_op(A, B, P)            # Q_k = A P_k + P_k B
+        alpha = rho / inner(Rt, Q)
+        S = R - alpha * Q
+        T = sylvester_op(A, B, S)            # T_k = A S_k + S_k B
+        omega = inner(T, S) / inner(T, T)
+        X = X + alpha * P + omega * S
+        R = S - omega * T
+        rn = np.linalg.norm(R)
+        hist.append(rn / r0)
+        if its is not None:
+            its.append(X.copy())
+        if rn <= r0 * tol:
+            return FullResult(X, k + 1, "converged", hist, its)
+        rho_new = inner(R, Rt)
+        beta = alpha / omega * rho_new / rho
+        rho = rho_new
+        P = R + beta * (P - omega * Q)
+    return FullResult(X, maxit, "maxit", hist, its)
