@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the factorized Krylov solver on one GB300.
+
+Default workload (one "step" = one full solve from X_0 = 0 to relative residual
+1e-8): factorized BiCGSTAB (Algorithm 4.2) in float64 on A = 3D upwind
+convection-diffusion 64^3 (n = 262,144, wind seed 1), B = the same operator on
+48^3 (m = 110,592, wind seed 2), s = 4, C1, C2 ~ N(0,1) seed 0, tol 1e-8,
+maxit 300.  Inputs are synthetic (``workloads``).
+
+Prints ONE JSON line.  ``value`` = device time per solve (CUDA events on the
+solve stream, inputs already in HBM); ``e2e`` = the same through the public C
+ABI with host buffers (create + solve + factors back, pinned host memory);
+``roofline`` = the dominant kernel class, timed live by the library's CUDA-event
+profiler; ``cpu_baseline`` = the CPU FP64 oracle on the host cores (a bounded,
+measured sample of the same workload, extrapolated with the algorithm's cost
+structure; see ``oracle_time_to_tol``).
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica
+of the workload (the solver does not shard); the line reports the max over
+ranks.  ``--impl reference`` times the CPU oracle alone (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "time to rel. residual 1e-8 (mixed/batched vs FP64 factorized), SpMM+Gram HBM GB/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def workload():
+    p = wl.cfg_convdiff_bicgstab(64, 48, 4, tol=1e-8, maxit=300)
+    return p
+
+
+def config_of(p):
+    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_fp64", "method": "factorized BiCGSTAB (Algorithm 4.2)",
+            "n": p.A.nrows, "m": p.B.nrows, "nnzA": p.A.nnz, "nnzB": p.B.nnz, "s": p.s, "tol": p.tol,
+            "maxit": p.maxit, "precision": "fp64",
+            "l2": "inputs larger than L2: the basis grows to ~2 GB per side per solve (L2 = 126 MB)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (read-only query)."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/sylv_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_time_to_tol(p, iters: int):
+    """Seconds the CPU FP64 oracle needs for ``iters`` iterations of factorized
+    BiCGSTAB on workload ``p``, from a bounded measured sample.
+
+    The oracle itself is run, as it stands, on pieces of the same workload:
+    (1) block Arnoldi steps (``BlockKrylovBasis.step``, BCGS2) of both bases at a
+        narrow and at the final width (cost is linear in the number of blocks j:
+        one SpMM plus four passes over n x js);
+    (2) the small-matrix part of one iteration (two factored Sylvester
+        operators, the inner products and padded updates of Algorithm 4.2) at
+        half and at the final order r (cost c3 r^3 + c2 r^2);
+    then sums the fitted per-step and per-iteration costs over the iteration
+    structure (Arnoldi steps 1..2*iters on each side, small orders
+    (2k+1)s, (2k+2)s).  Returns (seconds, sample_seconds, details).
+    """
+    from oracle import factorized as fz
+
+    rng = np.random.default_rng(123)
+    s = p.s
+    A = p.A.to_scipy()
+    Bt = p.B.to_scipy().T.tocsr()
+    t_sample0 = time.perf_counter()
+
+    def arnoldi_step_time(Op, n, j):
+        b = fz.BlockKrylovBasis(Op, rng.standard_normal((n, s)), "arnoldi")
+        b.blocks = [rng.standard_normal((n, s)) for _ in range(j)]  # cost-equivalent blocks
+        b.H = np.zeros((j * s, (j - 1) * s))
+        t = time.perf_counter()
+        b.step()
+        return time.perf_counter() - t
+
+    jmax = 2 * iters
+    lin = {}
+    for name, Op, n in (("A", A, p.A.nrows), ("B", Bt, p.B.nrows)):
+        t1 = min(arnoldi_step_time(Op, n, 2) for _ in range(2))
+        t2 = arnoldi_step_time(Op, n, jmax)
+        slope = (t2 - t1) / (jmax - 2)
+        lin[name] = (t1 - 2 * slope, slope)
+    basis = 0.0
+    for j in range(1, jmax + 1):
+        for a0, a1 in lin.values():
+            basis += a0 + a1 * j
+
+    def small_iter_time(k):
+        r = (2 * k + 1) * s
+        H = np.triu(rng.standard_normal((r + 2 * s, r + s)), -s)
+        G = np.triu(rng.standard_normal((r + 2 * s, r + s)), -s)
+        P, R, X = rng.standard_normal((3, r, r))
+        Rt = rng.standard_normal((s, s))
+        t = time.perf_counter()
+        Qh = fz.small_sylvester(H[: r + s, :r], P, G[: r + s, :r])
+        alpha = 1.0 / fz.inner(Rt, Qh[:s, :s])
+        Sh = fz.pad(R, s) - alpha * Qh
+        Th = fz.small_sylvester(H, Sh, G)
+        omega = fz.inner(Th[: r + s, : r + s], Sh) / fz.inner(Th, Th)
+        X2 = fz.pad(X[: r - s, : r - s], 2 * s) + fz.pad(alpha * P, s) + omega * Sh
+        R2 = fz.pad(Sh, s) - omega * Th
+        rn = np.sqrt(fz.inner(R2, R2))
+        rho = fz.inner(Rt, R2[:s, :s])
+        P2 = R2 + (rho + rn) * (fz.pad(P, 2 * s) - omega * fz.pad(Qh, s))
+        del X2, P2
+        return time.perf_counter() - t
+
+    k_hi = iters - 1
+    k_lo = max(1, k_hi // 2)
+    th = min(small_iter_time(k_hi) for _ in range(2))
+    tl = min(small_iter_time(k_lo) for _ in range(2))
+    r_hi, r_lo = (2 * k_hi + 1) * s, (2 * k_lo + 1) * s
+    # t(r) = c3 r^3 + c2 r^2 through the two samples
+    M = np.array([[r_lo**3, r_lo**2], [r_hi**3, r_hi**2]], dtype=float)
+    c3, c2 = np.linalg.solve(M, np.array([tl, th]))
+    small = sum(max(0.0, c3 * ((2 * k + 1) * s) ** 3 + c2 * ((2 * k + 1) * s) ** 2) for k in range(iters))
+    sample = time.perf_counter() - t_sample0
+    return basis + small, sample, {"arnoldi_step_s": {k: [round(v[0], 6), round(v[1], 8)] for k, v in lin.items()},
+                                   "small_iter_s": {"k_lo": k_lo, "t_lo": tl, "k_hi": k_hi, "t_hi": th}}
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def golden_iterations():
+    path = os.path.join(ROOT, "tests", "golden", "convdiff64x48_s4_bicgstab_history.txt")
+    try:
+        rows = [ln for ln in open(path) if ln.strip() and not ln.startswith("#")]
+        return len(rows) - 1
+    except OSError:
+        return None
+
+
+def cpu_baseline(p, iters):
+    t, sample, det = oracle_time_to_tol(p, iters)
+    return {"value": t, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"measured {sample:.1f} s of the CPU FP64 oracle on this workload (BCGS2 Arnoldi steps of both "
+                       f"bases at widths 2 and {2 * iters} blocks, small-matrix iterations at orders "
+                       f"{(2 * det['small_iter_s']['k_lo'] + 1) * p.s} and {(2 * det['small_iter_s']['k_hi'] + 1) * p.s})"
+                       f", summed over {iters} iterations with the per-step cost structure"),
+            "details": det}
+
+
+# ----------------------------------------------------------------------------- our arm
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2605_28274_gb300 as ps
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = workload()
+    stream = torch.cuda.Stream()
+    sv = ps.Solver(p.A, p.B, p.C1, p.C2, precision="fp64", profile=True, cuda_stream=stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        info = sv.bicgstab(p.tol, p.maxit)
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos, prof = [], {}
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = sv.bicgstab(p.tol, p.maxit)
+        infos.append(info)
+        for e in sv.profile():
+            d = prof.setdefault(e["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for key in ("launches", "ms", "bytes", "flops"):
+                d[key] += e[key]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    ms_step = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    iters = infos[-1]["iters"]
+    status = infos[-1]["status_name"]
+    launches = int(sum(i["kernel_launches"] for i in infos))
+
+    # roofline of the dominant kernel class (live CUDA-event timing inside the library)
+    pk = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    ai = d["flops"] / max(d["bytes"], 1.0)
+    ridge = FP64_NOMINAL_TFLOPS * 1e12 / (pk["hbm_gbs"] * 1e9)
+    if ai > ridge or dname.startswith("small_gemm"):
+        roof = {"bound": "alu", "achieved": d["flops"] / (d["ms"] * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "kernel": dname,
+                "peak_src": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure in MEASURED_PEAKS)"}
+    else:
+        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "kernel": dname, "peak_src": f"{pk['src']} HBM copy"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["launches"] = d["launches"]
+    roof["avg_launch_us"] = d["ms"] * 1e3 / max(1, d["launches"])
+    hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
+    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
+    spmm_gram = {"gbs": hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None, "frac_of_measured_hbm":
+                 (hb_bytes / (hb_ms * 1e-3) / 1e9 / pk["hbm_gbs"]) if hb_ms else None,
+                 "tflops_fp64": sum(x["flops"] for x in hb) / (hb_ms * 1e-3) / 1e12 if hb_ms else None}
+    total_ms = sum(x["ms"] for x in prof.values())
+    breakdown = {k: {"share": round(v["ms"] / total_ms, 4), "ms_per_solve": v["ms"] / args.steps,
+                     "launches_per_solve": v["launches"] // args.steps,
+                     "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None,
+                     "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] else None}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the public API with pinned host buffers
+    e2e_steps = max(1, args.steps)
+
+    def pinned(a):
+        dt = torch.float64 if a.dtype == np.float64 else torch.int32
+        if a.ndim == 2:  # column-major, as the C ABI takes it
+            tn = torch.empty(a.shape[::-1], dtype=dt, pin_memory=True).numpy()
+            tn[...] = a.T
+            return tn.T
+        tn = torch.empty(a.shape, dtype=dt, pin_memory=True).numpy()
+        tn[...] = a
+        return tn
+
+    Ap = wl.CSR(p.A.nrows, p.A.ncols, pinned(p.A.row_ptr), pinned(p.A.col_idx), pinned(p.A.val))
+    Bp = wl.CSR(p.B.nrows, p.B.ncols, pinned(p.B.row_ptr), pinned(p.B.col_idx), pinned(p.B.val))
+    C1p, C2p = pinned(p.C1), pinned(p.C2)
+    width = infos[-1]["width"]
+    outV = torch.empty(p.A.nrows * width, dtype=torch.float64, pin_memory=True).numpy()
+    outW = torch.empty(p.B.nrows * width, dtype=torch.float64, pin_memory=True).numpy()
+    outX = torch.empty(width * width, dtype=torch.float64, pin_memory=True).numpy()
+    h2d = (Ap.row_ptr.nbytes + Ap.col_idx.nbytes + Ap.val.nbytes + Bp.row_ptr.nbytes + Bp.col_idx.nbytes +
+           Bp.val.nbytes + C1p.nbytes + C2p.nbytes)
+    barrier()
+    e2e_times, d2h = [], 0
+    for _ in range(e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ps.Solver(Ap, Bp, C1p, C2p, precision="fp64", cuda_stream=stream.cuda_stream) as sv2:
+            inf2 = sv2.bicgstab(p.tol, p.maxit)
+            V, X, W = sv2.factors(out={"V": outV, "X": outX, "W": outW})
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = V.nbytes + X.nbytes + W.nbytes
+    e2e_s = statistics.mean(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    sv.close()
+
+    line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(p),
+            "iters": iters, "status": status, "rel_res": infos[-1]["rel_res"],
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "status": STATUS(inf2)},
+            "roofline": roof, "spmm_gram_hbm": spmm_gram, "kernel_breakdown": breakdown,
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(p, iters)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def STATUS(info):
+    return info.get("status_name", str(info.get("status")))
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    p = workload()
+    iters = golden_iterations() or 125
+    for _ in range(args.warmup):
+        oracle_time_to_tol(p, iters)
+    vals, samples = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, smp, det = oracle_time_to_tol(p, iters)
+        vals.append(v)
+        samples.append(smp)
+    wall = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(p),
+            "iters": iters,
+            "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+                             "sample": (f"each step measures {statistics.mean(samples):.1f} s of the CPU FP64 oracle "
+                                        f"on this workload (Arnoldi steps at 2 and {2 * iters} blocks, small-matrix "
+                                        f"iterations at two orders) and sums the fitted costs over the oracle's "
+                                        f"{iters} iterations (tests/golden)")},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

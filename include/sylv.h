@@ -1,0 +1,181 @@
+/*
+ * sylv.h -- C ABI of the GB300 (sm_103a) factorized Krylov solver for the
+ * Sylvester equation
+ *
+ *        A X + X B = C1 C2^T,   A: n x n, B: m x m sparse, C1: n x s, C2: m x s,
+ *
+ * (Satake, Fukaya, Sogabe, Zhang, "Factorized Krylov subspace methods for
+ * solving large Sylvester equations", eq. 1.1) and its Lyapunov case
+ * B = A^T, C2 = C1 (Sec. 4.3).  The solution is returned in factored form
+ * X = V X^ W^T with V (n x r), W (m x r) column-orthonormal block Krylov
+ * bases and X^ (r x r) small (Corollary 3.2).
+ *
+ * Conventions for every entry point:
+ *  - Host pointers unless stated otherwise.  Dense matrices are column-major
+ *    with leading dimension = number of rows.  CSR is 0-based with int32
+ *    indices and float64 values; column indices inside a row may come in any
+ *    order, duplicates are summed.
+ *  - Return value: 0 (SYLV_OK) or one of the sylv_status codes below.  No
+ *    entry point aborts or exits; after SYLV_ECUDA the handle should be
+ *    destroyed.  sylv_strerror() gives a message; sylv_last_error() gives the
+ *    detail of the last failure on the calling thread.
+ *  - A handle is not thread safe: one thread at a time per handle.
+ */
+#ifndef SYLV_H_
+#define SYLV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SYLV_OK = 0,         /* converged: ||R^_k|| <= tol ||R^_0|| (Algorithms 4.1/4.2 test) */
+  SYLV_EINVAL = 1,     /* bad argument: shape, NULL, malformed CSR, s < 1, tol < 0 ... */
+  SYLV_ENOMEM = 2,     /* device allocation failed */
+  SYLV_ENOTCONV = 3,   /* maxit reached; the factors hold the last iterate */
+  SYLV_EBREAKDOWN = 4, /* zero denominator (CG: <P^,Q^> <= 0; BiCGSTAB: <R~0,Q^(1:s,1:s)> = 0,
+                          omega = 0, rho = 0) or a block that lost part of its rank */
+  SYLV_ENONFINITE = 5, /* NaN/Inf in the iteration (e.g. from non-finite inputs) */
+  SYLV_ETIMEOUT = 6,   /* the host gave up waiting for the device (sylv_options.timeout_s) */
+  SYLV_ECUDA = 7,      /* a CUDA runtime call failed */
+  SYLV_ESTATE = 8      /* call out of order (e.g. factors requested before any solve) */
+} sylv_status;
+
+typedef enum {
+  SYLV_FP64 = 0, /* factors, sparse products and Gram products in float64 */
+  SYLV_MIXED = 1 /* factors, SpMM and Gram in float32 (FP32 accumulation inside a CTA),
+                    small coefficient recurrences, residual checks and an outer
+                    iterative refinement on the true residual in float64 */
+} sylv_precision;
+
+/* Sparse matrix in CSR form (host memory, read during sylv_create only). */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  const int32_t* row_ptr; /* nrows + 1 entries, row_ptr[0] = 0, nondecreasing, row_ptr[nrows] = nnz */
+  const int32_t* col_idx; /* nnz entries in [0, ncols) */
+  const double* val;      /* nnz entries */
+} sylv_csr;
+
+typedef struct {
+  int32_t precision;   /* sylv_precision */
+  int32_t lyapunov;    /* 1: B = A^T and C2 = C1 (Sec. 4.3); pass B = NULL, C2 = NULL */
+  int32_t poll_every;  /* iterations enqueued between host polls of the device status (0: 8) */
+  int32_t refine_max;  /* SYLV_MIXED: maximum outer refinement rounds (0: 4) */
+  double deflate_tol;  /* block Krylov exhaustion threshold delta (0: 1e-12 FP64, 1e-6 mixed) */
+  double timeout_s;    /* host wait limit per solve (0: 3600 s) */
+  void* cuda_stream;   /* cudaStream_t to run on, or NULL for a stream owned by the handle */
+  int32_t profile;     /* 1: time every kernel launch with CUDA events (see sylv_get_profile) */
+  int32_t reserved;
+} sylv_options;
+
+typedef struct {
+  int32_t status;       /* sylv_status of the solve */
+  int32_t iters;        /* completed iterations k (sum over refinement rounds in SYLV_MIXED) */
+  int64_t matvecs;      /* sparse block products A*V_j (equal count for B^T*W_j) */
+  int64_t width;        /* r: columns of V and W returned; X^ is r x r */
+  double rel_res;       /* ||R^_k|| / ||R^_0||, the monitored residual of Algorithms 4.1/4.2 */
+  double true_rel_res;  /* ||C1 C2^T - A X - X B||_F / ||C1 C2^T||_F in float64, or -1 if not computed */
+  double solve_ms;      /* wall time of the solve call on the host */
+  int32_t refinements;  /* SYLV_MIXED: outer refinement rounds used */
+  int32_t reserved;
+  int64_t kernel_launches; /* CUDA kernels this call enqueued (no-ops after a stop included) */
+} sylv_info;
+
+/* Per-kernel-class totals of the last solve (sylv_options.profile = 1).
+ * bytes / flops are the algorithmic amounts (each operand read once, each
+ * result written once), so bytes / (ms 1e-3) is the achieved bandwidth. */
+typedef struct {
+  char name[24];      /* "spmm", "gram", "update", "cholqr_scale", "reduce", "small_gemm", ... */
+  int64_t launches;
+  double ms;          /* summed kernel time (CUDA events on the solve stream) */
+  double bytes;       /* summed algorithmic DRAM bytes */
+  double flops;       /* summed algorithmic floating-point operations */
+} sylv_kernel_stat;
+
+typedef struct sylv_handle sylv_handle;
+
+/* Default options (FP64, Sylvester, poll every 8 iterations). */
+void sylv_default_options(sylv_options* opt);
+
+/*
+ * Problem statement, eq. 1.1 (Sec. 1).  Checks the input and copies A, B^T
+ * (built from B on the host), C1 and C2 to device memory; the caller keeps
+ * ownership of its buffers.  The thin QR factorisations C1 = V_1 R_L,
+ * C2 = W_1 R_R (CholQR2, diag(R) > 0) that start Algorithms 4.1/4.2 run at the
+ * start of each solve.
+ *   A        n x n CSR;   B  m x m CSR (NULL when opt->lyapunov)
+ *   C1       n x s column-major;  C2 m x s column-major (NULL when opt->lyapunov)
+ *   s        number of columns of C1, C2 (1 <= s <= 8)
+ *   opt      NULL for defaults
+ *   out      receives the handle (NULL on failure)
+ * Errors: SYLV_EINVAL (shapes, CSR), SYLV_ENOMEM, SYLV_ECUDA (also: no device),
+ *         SYLV_ENONFINITE (NaN/Inf in A, B, C1 or C2).
+ */
+int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const double* C2, int64_t s,
+                const sylv_options* opt, sylv_handle** out);
+
+/*
+ * Factorized CG, Algorithm 4.1 (A, B symmetric positive definite; block
+ * Lanczos bases).  Runs at most maxit iterations from X_0 = 0 and stops at the
+ * first k with ||R^_{k+1}|| <= tol ||R^_0||.  The factors V_{k+1}, X^_{k+1},
+ * W_{k+1} (r = (k+1)s) stay on the device for sylv_get_factors.
+ * Device memory for maxit iterations is (re)allocated here.  A rank-deficient
+ * C1 or C2 (including C = 0) returns SYLV_EBREAKDOWN.
+ * Returns the status also stored in info->status (info may be NULL).
+ */
+int sylv_cg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
+
+/*
+ * Factorized BiCGSTAB, Algorithm 4.2 (general A, B; block Arnoldi bases with
+ * block classical Gram-Schmidt applied twice).  Returns V_{2k+2}, X^_{k+1},
+ * W_{2k+2} (r = (2k+2)s).  Otherwise as sylv_cg.
+ */
+int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
+
+/*
+ * Copies the factors of the last solve: V (n x r), X^ (r x r), W (m x r),
+ * column-major, float64.  Any of V, Xhat, W may be NULL to skip it; *r
+ * receives r (the call with all three NULL only queries r).  In the Lyapunov
+ * case W equals V.  Errors: SYLV_ESTATE (no solve yet), SYLV_ECUDA.
+ */
+int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t* r);
+
+/*
+ * Residual history of the last solve: hist[0] = 1, hist[k] = ||R^_k||/||R^_0||.
+ * Writes min(cap, len) values; *len receives the full length (hist may be NULL).
+ */
+int sylv_get_history(sylv_handle* h, double* hist, int64_t cap, int64_t* len);
+
+/*
+ * Block Hessenberg matrix of one basis from the last solve (eq. 3.4,
+ * A V_k = V_{k+1} H_{k+1,k}): side 0 -> H of (A, C1), side 1 -> G of (B^T, C2).
+ * Copies the leading rows x cols part (column-major, leading dimension rows)
+ * with rows = (nblocks) s and cols = (nblocks - 1) s; *nblocks receives the
+ * number of basis blocks built.  H may be NULL to query nblocks.
+ */
+int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, int32_t* nblocks);
+
+/*
+ * Sparse block product through the solver's SpMM kernel (the sparse apply of
+ * eq. 3.4): Y = Op X with Op = A (side 0) or B^T (side 1), X and Y column-major
+ * (rows x k), 1 <= k <= 8, host memory.  Runs in the handle's precision.
+ */
+int sylv_apply(sylv_handle* h, int32_t side, const double* X, double* Y, int64_t k);
+
+/*
+ * Kernel timing of the last solve, one entry per kernel class (only with
+ * sylv_options.profile = 1; otherwise *count = 0).  Writes min(cap, count)
+ * entries to out (may be NULL to query count).
+ */
+int sylv_get_profile(sylv_handle* h, sylv_kernel_stat* out, int32_t cap, int32_t* count);
+
+const char* sylv_strerror(int status);
+const char* sylv_last_error(void);
+void sylv_destroy(sylv_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYLV_H_ */

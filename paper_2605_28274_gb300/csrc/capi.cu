@@ -1,0 +1,835 @@
+// C ABI of libsylv: handle management, device memory, and the host drivers of
+// factorized CG (Algorithm 4.1) and factorized BiCGSTAB (Algorithm 4.2).
+//
+// The host only enqueues kernels: every scalar of the recurrences stays on the
+// device (DevState) and every kernel is a no-op once the device status says the
+// solve stopped.  The host copies the status back once every `poll_every`
+// iterations, one chunk behind the enqueue point, so the GPU never idles
+// waiting for the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/sylv.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using sylv::DevState;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CU(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      if (e_ == cudaErrorMemoryAllocation) {                                                  \
+        cudaGetLastError();                                                                   \
+        return fail(SYLV_ENOMEM, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+      }                                                                                       \
+      return fail(SYLV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    }                                                                                         \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != SYLV_OK) return rc_; \
+  } while (0)
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Side {
+  int64_t n = 0, nnz = 0;
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* vald = nullptr;
+  float* valf = nullptr;
+  double* C = nullptr;  // n x s column-major, float64
+  void* V = nullptr;    // maxb blocks, block-row-major, factor precision
+  double* H = nullptr;  // ldh x ldh column-major
+  double* RQR = nullptr;
+  double* R1 = nullptr;
+  double* Rinv = nullptr;
+  void* RinvT = nullptr;
+};
+
+enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2 };
+
+// Kernel classes timed by the optional profiler.
+enum KClass {
+  KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_SCALE, KC_SETUP,
+  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_NUM
+};
+const char* const kKcNames[KC_NUM] = {"spmm",   "gram",  "reduce_h",   "update",          "cholqr_chol",
+                                      "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise"};
+
+struct Prof {
+  struct Rec {
+    int cls, k;
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Rec> recs;
+  int64_t launches[KC_NUM] = {};
+  double ms[KC_NUM] = {}, bytes[KC_NUM] = {}, flops[KC_NUM] = {};
+  int cur_k = -1;
+  bool valid = false;
+};
+
+}  // namespace
+
+struct sylv_handle {
+  sylv_options opt{};
+  int64_t s = 0;
+  bool lyap = false, mixed = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Side side[2];
+  std::vector<void*> fixed_allocs, solve_allocs;
+  // per-solve capacity
+  int maxb = 0, cap_method = M_NONE;
+  int64_t lds = 0;
+  double *Xh = nullptr, *Rh = nullptr, *Ph = nullptr, *Qh = nullptr, *Sh = nullptr, *Th = nullptr, *Rt = nullptr;
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;  // pinned, 2 slots
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double* gpart = nullptr;  // Gram partials
+  double* spart = nullptr;  // self-Gram partials
+  double* Hc = nullptr;
+  double* psmall = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  Prof prof;
+  int64_t launches = 0;  // kernels enqueued by the current solve
+  // last solve
+  int method = M_NONE;
+  int iters = 0;
+  int status = -1;
+  int64_t width = 0;
+  int nblocks = 0;
+};
+
+namespace {
+
+int dev_alloc(sylv_handle* h, std::vector<void*>& list, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? SYLV_ENOMEM : SYLV_ECUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  list.push_back(*p);
+  return SYLV_OK;
+}
+
+template <typename P>
+int alloc_fixed(sylv_handle* h, P** p, size_t count) {
+  return dev_alloc(h, h->fixed_allocs, (void**)p, count * sizeof(P));
+}
+template <typename P>
+int alloc_solve(sylv_handle* h, P** p, size_t count) {
+  return dev_alloc(h, h->solve_allocs, (void**)p, count * sizeof(P));
+}
+
+void free_solve(sylv_handle* h) {
+  for (void* p : h->solve_allocs) cudaFree(p);
+  h->solve_allocs.clear();
+  h->maxb = 0;
+  h->cap_method = M_NONE;
+  for (auto& sd : h->side) {
+    sd.V = nullptr;
+    sd.H = nullptr;
+  }
+}
+
+int check_csr(const sylv_csr* M, const char* name, int64_t expect_n) {
+  if (M == nullptr) return fail(SYLV_EINVAL, std::string(name) + " is NULL");
+  if (M->nrows <= 0 || M->ncols != M->nrows) return fail(SYLV_EINVAL, std::string(name) + " must be square and non-empty");
+  if (expect_n >= 0 && M->nrows != expect_n) return fail(SYLV_EINVAL, std::string(name) + " has the wrong size");
+  if (M->nrows > INT32_MAX - 1 || M->nnz < 0 || M->nnz > INT32_MAX)
+    return fail(SYLV_EINVAL, std::string(name) + ": sizes exceed int32 indexing");
+  if (!M->row_ptr || (M->nnz > 0 && (!M->col_idx || !M->val))) return fail(SYLV_EINVAL, std::string(name) + ": NULL arrays");
+  if (M->row_ptr[0] != 0 || M->row_ptr[M->nrows] != M->nnz) return fail(SYLV_EINVAL, std::string(name) + ": bad row_ptr ends");
+  for (int64_t i = 0; i < M->nrows; ++i)
+    if (M->row_ptr[i + 1] < M->row_ptr[i]) return fail(SYLV_EINVAL, std::string(name) + ": row_ptr decreases");
+  for (int64_t p = 0; p < M->nnz; ++p)
+    if (M->col_idx[p] < 0 || M->col_idx[p] >= M->ncols) return fail(SYLV_EINVAL, std::string(name) + ": column index out of range");
+  return SYLV_OK;
+}
+
+// Upload Op (A, or B^T built on the host by a counting sort) to the device.
+int upload_operator(sylv_handle* h, Side& sd, const sylv_csr* M, bool transpose) {
+  const int64_t n = M->nrows, nnz = M->nnz;
+  std::vector<int32_t> rp(n + 1), ci(nnz);
+  std::vector<double> val(nnz);
+  if (!transpose) {
+    std::copy(M->row_ptr, M->row_ptr + n + 1, rp.begin());
+    std::copy(M->col_idx, M->col_idx + nnz, ci.begin());
+    std::copy(M->val, M->val + nnz, val.begin());
+  } else {
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int64_t p = 0; p < nnz; ++p) cnt[M->col_idx[p] + 1]++;
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t i = 0; i <= n; ++i) rp[i] = (int32_t)cnt[i];
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = M->row_ptr[i]; p < M->row_ptr[i + 1]; ++p) {
+        const int64_t q = pos[M->col_idx[p]]++;
+        ci[q] = (int32_t)i;
+        val[q] = M->val[p];
+      }
+  }
+  for (double v : val)
+    if (!std::isfinite(v)) return fail(SYLV_ENONFINITE, "non-finite matrix entry");
+  sd.n = n;
+  sd.nnz = nnz;
+  TRY(alloc_fixed(h, &sd.rp, n + 1));
+  TRY(alloc_fixed(h, &sd.ci, std::max<int64_t>(nnz, 1)));
+  TRY(alloc_fixed(h, &sd.vald, std::max<int64_t>(nnz, 1)));
+  CU(cudaMemcpyAsync(sd.rp, rp.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  if (nnz) {
+    CU(cudaMemcpyAsync(sd.ci, ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(sd.vald, val.data(), nnz * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  if (h->mixed) {
+    TRY(alloc_fixed(h, &sd.valf, std::max<int64_t>(nnz, 1)));
+    sylv::launch_convert<float>(h->stream, nnz, sd.vald, sd.valf);
+  }
+  CU(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+  return SYLV_OK;
+}
+
+int upload_rhs(sylv_handle* h, Side& sd, const double* C) {
+  const int64_t cnt = sd.n * h->s;
+  for (int64_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(C[i])) return fail(SYLV_ENONFINITE, "non-finite right-hand side entry");
+  TRY(alloc_fixed(h, &sd.C, cnt));
+  CU(cudaMemcpyAsync(sd.C, C, cnt * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  TRY(alloc_fixed(h, &sd.RQR, 64));
+  TRY(alloc_fixed(h, &sd.R1, 64));
+  TRY(alloc_fixed(h, &sd.Rinv, 64));
+  TRY(alloc_fixed(h, (double**)&sd.RinvT, 64));
+  return SYLV_OK;
+}
+
+int nsides(const sylv_handle* h) { return h->lyap ? 1 : 2; }
+
+cudaEvent_t prof_event(sylv_handle* h) {
+  Prof& p = h->prof;
+  if (p.used == p.pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    p.pool.push_back(e);
+  }
+  return p.pool[p.used++];
+}
+
+cudaEvent_t prof_begin(sylv_handle* h) {
+  if (!h->prof.on) return nullptr;
+  cudaEvent_t a = prof_event(h);
+  if (a) cudaEventRecord(a, h->stream);
+  return a;
+}
+
+void prof_end(sylv_handle* h, int cls, double bytes, double flops, cudaEvent_t a) {
+  if (!h->prof.on || !a) return;
+  cudaEvent_t b = prof_event(h);
+  if (!b) return;
+  cudaEventRecord(b, h->stream);
+  h->prof.recs.push_back({cls, h->prof.cur_k, a, b, bytes, flops});
+}
+
+void prof_reset(sylv_handle* h) {
+  Prof& p = h->prof;
+  p.on = h->opt.profile != 0;
+  p.used = 0;
+  p.recs.clear();
+  p.cur_k = -1;
+  p.valid = false;
+  for (int i = 0; i < KC_NUM; ++i) {
+    p.launches[i] = 0;
+    p.ms[i] = p.bytes[i] = p.flops[i] = 0.0;
+  }
+}
+
+// After the final synchronisation: sum the launches that belong to completed iterations.
+void prof_finish(sylv_handle* h, int iters) {
+  Prof& p = h->prof;
+  if (!p.on) return;
+  for (const auto& r : p.recs) {
+    if (r.k >= iters) continue;  // enqueued after the stop: no-op launches
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    p.launches[r.cls] += 1;
+    p.ms[r.cls] += ms;
+    p.bytes[r.cls] += r.bytes;
+    p.flops[r.cls] += r.flops;
+  }
+  p.valid = true;
+}
+
+#define PROF(h, cls, bytes, flops, stmt)            \
+  do {                                              \
+    cudaEvent_t prof_a_ = prof_begin(h);            \
+    stmt;                                           \
+    (h)->launches += 1;                             \
+    prof_end((h), (cls), (bytes), (flops), prof_a_); \
+  } while (0)
+
+// Device buffers sized for `maxb` basis blocks per side.
+int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
+  if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE) return SYLV_OK;
+  free_solve(h);
+  const int64_t s = h->s;
+  const size_t fsz = h->mixed ? sizeof(float) : sizeof(double);
+  const int64_t ldh = (int64_t)maxb * s;
+  h->lds = ldh;
+  for (int i = 0; i < nsides(h); ++i) {
+    Side& sd = h->side[i];
+    TRY(dev_alloc(h, h->solve_allocs, &sd.V, (size_t)maxb * sd.n * s * fsz));
+    TRY(alloc_solve(h, &sd.H, (size_t)(ldh * ldh)));
+  }
+  const size_t l2 = (size_t)(h->lds * h->lds);
+  TRY(alloc_solve(h, &h->Xh, l2));
+  TRY(alloc_solve(h, &h->Rh, l2));
+  TRY(alloc_solve(h, &h->Ph, l2));
+  TRY(alloc_solve(h, &h->Qh, l2));
+  TRY(alloc_solve(h, &h->Sh, l2));
+  TRY(alloc_solve(h, &h->Th, l2));
+  TRY(alloc_solve(h, &h->Rt, 64));
+  TRY(alloc_solve(h, &h->hist, (size_t)hist_need));
+  // Gram partials: at most 2*SMs CTAs x (maxb * s * s)
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TRY(alloc_solve(h, &h->gpart, (size_t)(2 * sms) * maxb * s * s));
+  TRY(alloc_solve(h, &h->spart, (size_t)(4 * sms) * 64));
+  TRY(alloc_solve(h, &h->Hc, (size_t)maxb * s * s));
+  const int64_t gtiles = (h->lds + 63) / 64;
+  const size_t psz = std::max<size_t>((size_t)((h->lds + sylv::NT - 1) / sylv::NT) * h->lds, 2 * gtiles * gtiles) + 64;
+  TRY(alloc_solve(h, &h->psmall, psz));
+  h->maxb = maxb;
+  h->hist_cap = hist_need;
+  h->cap_method = method;
+  return SYLV_OK;
+}
+
+template <typename T>
+const T* op_val(const Side& sd);
+template <>
+const double* op_val<double>(const Side& sd) { return sd.vald; }
+template <>
+const float* op_val<float>(const Side& sd) { return sd.valf; }
+
+double deflate_tol(const sylv_handle* h) {
+  if (h->opt.deflate_tol > 0) return h->opt.deflate_tol;
+  return h->mixed ? 1e-6 : 1e-12;
+}
+
+// Thin QR of C (CholQR2) into block 0; R -> sd.RQR.
+template <typename T>
+void setup_qr(sylv_handle* h, int si) {
+  Side& sd = h->side[si];
+  const int s = (int)h->s;
+  T* V0 = (T*)sd.V;
+  sylv::launch_pack<T>(h->stream, sd.n, s, sd.C, V0);
+  int nc = sylv::launch_selfgram<T>(h->stream, h->st, sd.n, s, V0, h->spart);
+  sylv::CholArgs a{};
+  a.side = si;
+  a.s = s;
+  a.delta = deflate_tol(h);
+  a.R1 = sd.R1;
+  a.Rinv = sd.Rinv;
+  a.RinvT = sd.RinvT;
+  a.factor_is_float = h->mixed ? 1 : 0;
+  a.setup = 1;
+  a.pass = 1;
+  a.ldh = 0;
+  sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
+  nc = sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, h->spart);
+  a.pass = 2;
+  a.Rout = sd.RQR;
+  sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
+  sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr);
+  h->launches += 5;  // pack, self-Gram, Cholesky, scale+Gram, Cholesky, scale (one counted by PROF)
+}
+
+// One block Lanczos (lanczos=true) or BCGS2 block Arnoldi step on side si:
+// from blocks 0..q build block q+1 and column block q of H (eq. 3.4).
+template <typename T>
+void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
+  Side& sd = h->side[si];
+  const int s = (int)h->s;
+  const int64_t n = sd.n, bstride = n * s, ldh = h->lds;
+  const double b = (double)sizeof(T);
+  const double ns = (double)n * s;
+  T* V = (T*)sd.V;
+  T* Vq = V + (int64_t)q * bstride;
+  T* Y = V + (int64_t)(q + 1) * bstride;
+  cudaStream_t st = h->stream;
+  int nc;
+  // algorithmic bytes: CSR once, gathered block once, result once (+ V_{j-1} for Lanczos)
+  const double spmm_bytes = (double)sd.nnz * (4.0 + b) + 4.0 * (n + 1) + 2.0 * ns * b + (lanczos && q >= 1 ? ns * b : 0.0);
+  const double spmm_flops = 2.0 * sd.nnz * s + (lanczos && q >= 1 ? 2.0 * ns * s : 0.0);
+  const int nb = lanczos ? 1 : q + 1;
+  const T* Vfirst = lanczos ? Vq : V;
+  const double gram_bytes = ns * b * (nb + 1), gram_flops = 2.0 * ns * nb * s;
+  const double upd_bytes = ns * b * (nb + 2), upd_flops = 2.0 * ns * nb * s;
+  if (lanczos) {
+    const T* Vprev = q >= 1 ? V + (int64_t)(q - 1) * bstride : nullptr;
+    const double* M = q >= 1 ? sd.H + (int64_t)(q - 1) * s + (int64_t)q * s * ldh : nullptr;
+    PROF(h, KC_SPMM, spmm_bytes, spmm_flops,
+         sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, Vprev, M, ldh));
+  } else {
+    PROF(h, KC_SPMM, spmm_bytes, spmm_flops,
+         sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, nullptr, nullptr, 0));
+  }
+  const int passes = lanczos ? 1 : 2;  // block Lanczos: one projection; Arnoldi: BCGS2
+  for (int pass = 0; pass < passes; ++pass) {
+    PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, h->gpart));
+    PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
+         sylv::launch_reduce_H(st, h->st, h->gpart, nc, nb, s, sd.H, ldh, lanczos ? (int64_t)q * s : 0,
+                               (int64_t)q * s, h->Hc, pass == 1));
+    const bool last = pass == passes - 1;
+    PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
+         nc = sylv::launch_update<T>(st, h->st, n, s, Vfirst, bstride, nb, h->Hc, Y, last ? h->spart : nullptr));
+  }
+  sylv::CholArgs a{};
+  a.side = si;
+  a.s = s;
+  a.delta = deflate_tol(h);
+  a.Hcol = sd.H + (int64_t)q * s * ldh;
+  a.ldh = ldh;
+  a.hrows = (int64_t)(q + 1) * s;
+  a.R1 = sd.R1;
+  a.Rinv = sd.Rinv;
+  a.RinvT = sd.RinvT;
+  a.factor_is_float = h->mixed ? 1 : 0;
+  a.pass = 1;
+  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, h->spart, nc, a));
+  PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1) + ns * s,
+       nc = sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, h->spart));
+  a.pass = 2;
+  a.Hsub = sd.H + (int64_t)(q + 1) * s + (int64_t)q * s * ldh;
+  a.Hsup = lanczos ? sd.H + (int64_t)q * s + (int64_t)(q + 1) * s * ldh : nullptr;
+  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, h->spart, nc, a));
+  PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1), sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr));
+}
+
+sylv::SmallCtx small_ctx(sylv_handle* h) {
+  sylv::SmallCtx c{};
+  c.st = h->st;
+  c.hist = h->hist;
+  c.s = (int)h->s;
+  c.lds = h->lds;
+  c.Xh = h->Xh;
+  c.Rh = h->Rh;
+  c.Ph = h->Ph;
+  c.Qh = h->Qh;
+  c.Sh = h->Sh;
+  c.Th = h->Th;
+  c.Rt = h->Rt;
+  c.H = h->side[0].H;
+  c.G = h->lyap ? h->side[0].H : h->side[1].H;
+  c.ldh = h->lds;
+  c.partials = h->psmall;
+  c.lyapunov = h->lyap ? 1 : 0;
+  return c;
+}
+
+// Copy the device status to pinned slot `slot` and record its event.
+int post_status(sylv_handle* h, int slot) {
+  CU(cudaMemcpyAsync(&h->st_host[slot], h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaEventRecord(h->ev[slot], h->stream));
+  return SYLV_OK;
+}
+
+int wait_status(sylv_handle* h, int slot, double deadline) {
+  for (;;) {
+    cudaError_t e = cudaEventQuery(h->ev[slot]);
+    if (e == cudaSuccess) return SYLV_OK;
+    if (e != cudaErrorNotReady) return fail(SYLV_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+    if (now_s() > deadline) return fail(SYLV_ETIMEOUT, "device did not finish within the timeout");
+    std::this_thread::yield();
+  }
+}
+
+template <typename T>
+int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
+  const double t0 = now_s();
+  const double deadline = t0 + (h->opt.timeout_s > 0 ? h->opt.timeout_s : 3600.0);
+  if (!(tol >= 0.0) || maxit < 0) return fail(SYLV_EINVAL, "tol must be >= 0 and maxit >= 0");
+  const int maxb = std::max(2, method == M_CG ? maxit + 1 : 2 * maxit + 1);
+  TRY(ensure_capacity(h, method, maxb, maxit + 1));
+  const int s = (int)h->s;
+  cudaStream_t strm = h->stream;
+  CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), strm));
+  const size_t l2 = (size_t)(h->lds * h->lds) * sizeof(double);
+  for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th}) CU(cudaMemsetAsync(p, 0, l2, strm));
+  for (int i = 0; i < nsides(h); ++i) {
+    CU(cudaMemsetAsync(h->side[i].H, 0, l2, strm));
+    }
+  prof_reset(h);
+  h->launches = 0;
+  for (int i = 0; i < nsides(h); ++i) {
+    PROF(h, KC_SETUP, 0.0, 0.0, setup_qr<T>(h, i));
+  }
+  sylv::SmallCtx c = small_ctx(h);
+  const Side& sA = h->side[0];
+  const Side& sB = h->side[h->lyap ? 0 : 1];
+  sylv::launch_init_small(strm, c, sA.RQR, sB.RQR, tol, method == M_BICG);
+  h->launches += 1;
+  CU(cudaGetLastError());
+  const int poll = h->opt.poll_every > 0 ? h->opt.poll_every : 8;
+  int slot = 0, pending = -1;
+  bool stopped = false;
+  const double e8 = 8.0;
+  for (int k = 0; k < maxit && !stopped; ++k) {
+    h->prof.cur_k = k;
+    if (method == M_CG) {
+      basis_step<T>(h, 0, k, true);
+      if (!h->lyap) basis_step<T>(h, 1, k, true);
+      const int r = (k + 1) * s, rp = r + s;
+      const double r2 = (double)rp * rp;
+      const double opflops = 2.0 * 2.0 * r2 * 3.0 * s;
+      if (h->lyap) {
+        PROF(h, KC_SMALL_OP, e8 * (2.0 * r2), opflops / 2, sylv::launch_cg_q(strm, c, 1, r));
+        PROF(h, KC_SMALL_OP, e8 * (3.0 * r2), r2, sylv::launch_cg_q(strm, c, 2, r));
+      } else {
+        PROF(h, KC_SMALL_OP, e8 * (2.0 * r2), opflops, sylv::launch_cg_q(strm, c, 0, r));
+      }
+      PROF(h, KC_SMALL_ELEM, e8 * 6.0 * r2, 4.0 * r2, sylv::launch_cg_update(strm, c, k, r));
+      PROF(h, KC_SMALL_ELEM, e8 * 3.0 * r2, 2.0 * r2, sylv::launch_cg_p(strm, c, rp));
+    } else {
+      const int r1 = (2 * k + 1) * s, rp = r1 + s, rpp = rp + s;
+      const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
+      basis_step<T>(h, 0, 2 * k, false);
+      basis_step<T>(h, 1, 2 * k, false);
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * (double)r1 * r1 + q2), sylv::sylv_gemm_flops(r1, s),
+           sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false));
+      PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
+      PROF(h, KC_SMALL_ELEM, e8 * 3.0 * q2, 2.0 * q2, sylv::launch_bicg_s(strm, c, rp));
+      basis_step<T>(h, 0, 2 * k + 1, false);
+      basis_step<T>(h, 1, 2 * k + 1, false);
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + t2), sylv::sylv_gemm_flops(rp, s) + 4.0 * t2,
+           sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true));
+      PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
+           sylv::launch_bicg_update(strm, c, k, rp, rpp));
+      PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));
+    }
+    if ((k + 1) % poll == 0 && k + 1 < maxit) {
+      CU(cudaGetLastError());
+      TRY(post_status(h, slot));
+      if (pending >= 0) {
+        TRY(wait_status(h, pending, deadline));
+        if (h->st_host[pending].status != sylv::ST_RUNNING) stopped = true;
+      }
+      pending = slot;
+      slot ^= 1;
+    }
+  }
+  CU(cudaGetLastError());
+  TRY(post_status(h, slot));
+  TRY(wait_status(h, slot, deadline));
+  const DevState& ds = h->st_host[slot];
+  prof_finish(h, ds.iters);
+  h->method = method;
+  h->iters = ds.iters;
+  h->width = (int64_t)(method == M_CG ? ds.iters : 2 * ds.iters) * s;
+  h->nblocks = method == M_CG ? ds.iters + 1 : 2 * ds.iters + 1;
+  int rc;
+  switch (ds.status) {
+    case sylv::ST_CONVERGED: rc = SYLV_OK; break;
+    case sylv::ST_RUNNING: rc = SYLV_ENOTCONV; break;
+    case sylv::ST_BREAKDOWN: rc = SYLV_EBREAKDOWN; g_err = "breakdown (site " + std::to_string(ds.breakdown_where) + ")"; break;
+    default: rc = SYLV_ENONFINITE; g_err = "non-finite value (site " + std::to_string(ds.breakdown_where) + ")"; break;
+  }
+  if (maxit == 0 && ds.status == sylv::ST_RUNNING) rc = SYLV_ENOTCONV;
+  h->status = rc;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = rc;
+    info->iters = ds.iters;
+    info->matvecs = (int64_t)(method == M_CG ? ds.iters : 2 * ds.iters);
+    info->width = h->width;
+    info->rel_res = ds.r0 > 0 ? ds.rnorm / ds.r0 : 0.0;
+    info->true_rel_res = -1.0;
+    info->solve_ms = (now_s() - t0) * 1e3;
+    info->kernel_launches = h->launches;
+  }
+  return rc;
+}
+
+int solve(sylv_handle* h, int method, double tol, int32_t maxit, sylv_info* info) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (info) std::memset(info, 0, sizeof(*info));
+  return h->mixed ? run_solve<float>(h, method, tol, maxit, info) : run_solve<double>(h, method, tol, maxit, info);
+}
+
+template <typename T>
+int unpack_to_host(sylv_handle* h, const Side& sd, int nb, double* out) {
+  const int s = (int)h->s;
+  const int64_t n = sd.n, bstride = n * s;
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(256ll << 20) / (n * s * 8)));
+  double* scratch = nullptr;
+  CU(cudaMalloc(&scratch, (size_t)chunk * n * s * sizeof(double)));
+  int rc = SYLV_OK;
+  for (int b0 = 0; b0 < nb && rc == SYLV_OK; b0 += chunk) {
+    const int cb = std::min(chunk, nb - b0);
+    sylv::launch_unpack<T>(h->stream, n, s, cb, (const T*)sd.V + (int64_t)b0 * bstride, bstride, scratch);
+    cudaError_t e = cudaMemcpyAsync(out + (int64_t)b0 * s * n, scratch, (size_t)cb * n * s * sizeof(double),
+                                    cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = fail(SYLV_ECUDA, std::string("get_factors: ") + cudaGetErrorString(e));
+  }
+  cudaFree(scratch);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sylv_default_options(sylv_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = SYLV_FP64;
+  opt->poll_every = 8;
+  opt->refine_max = 4;
+  opt->timeout_s = 3600.0;
+}
+
+int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const double* C2, int64_t s,
+                const sylv_options* opt, sylv_handle** out) {
+  g_err.clear();
+  if (!out) return fail(SYLV_EINVAL, "out is NULL");
+  *out = nullptr;
+  sylv_options o;
+  sylv_default_options(&o);
+  if (opt) o = *opt;
+  if (s < 1 || s > 8) return fail(SYLV_EINVAL, "s must be in [1, 8]");
+  if (o.precision != SYLV_FP64 && o.precision != SYLV_MIXED) return fail(SYLV_EINVAL, "unknown precision");
+  TRY(check_csr(A, "A", -1));
+  const bool lyap = o.lyapunov != 0;
+  if (lyap) {
+    if (B != nullptr || C2 != nullptr) return fail(SYLV_EINVAL, "Lyapunov case: pass B = NULL and C2 = NULL");
+  } else {
+    TRY(check_csr(B, "B", -1));
+    if (!C2) return fail(SYLV_EINVAL, "C2 is NULL");
+  }
+  if (!C1) return fail(SYLV_EINVAL, "C1 is NULL");
+  if (A->nrows < s || (!lyap && B->nrows < s)) return fail(SYLV_EINVAL, "need n, m >= s");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(SYLV_ECUDA, "no CUDA device");
+  }
+  sylv_handle* h = new sylv_handle();
+  h->opt = o;
+  h->s = s;
+  h->lyap = lyap;
+  h->mixed = o.precision == SYLV_MIXED;
+  auto bail = [&](int rc) {
+    std::string msg = g_err;
+    sylv_destroy(h);
+    g_err = msg;
+    return rc;
+  };
+  if (o.cuda_stream) {
+    h->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(SYLV_ECUDA, "stream"));
+    h->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(SYLV_ECUDA, "event"));
+  if (cudaMallocHost(&h->st_host, 2 * sizeof(DevState)) != cudaSuccess) return bail(fail(SYLV_ECUDA, "pinned status"));
+  int rc = alloc_fixed(h, &h->st, 1);
+  if (rc) return bail(rc);
+  rc = upload_operator(h, h->side[0], A, false);
+  if (!rc) rc = upload_rhs(h, h->side[0], C1);
+  if (!rc && !lyap) rc = upload_operator(h, h->side[1], B, true);
+  if (!rc && !lyap) rc = upload_rhs(h, h->side[1], C2);
+  if (rc) return bail(rc);
+  *out = h;
+  return SYLV_OK;
+}
+
+int sylv_cg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
+  g_err.clear();
+  return solve(h, M_CG, tol, maxit, info);
+}
+
+int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
+  g_err.clear();
+  return solve(h, M_BICG, tol, maxit, info);
+}
+
+int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t* r) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
+  if (r) *r = h->width;
+  const int s = (int)h->s;
+  const int nb = (int)(h->width / s);
+  if (Xhat && h->width > 0) {
+    CU(cudaMemcpy2DAsync(Xhat, h->width * sizeof(double), h->Xh, h->lds * sizeof(double), h->width * sizeof(double),
+                         h->width, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  for (int i = 0; i < 2; ++i) {
+    double* dst = i == 0 ? V : W;
+    if (!dst || nb == 0) continue;
+    const Side& sd = h->side[(i == 1 && !h->lyap) ? 1 : 0];
+    TRY(h->mixed ? unpack_to_host<float>(h, sd, nb, dst) : unpack_to_host<double>(h, sd, nb, dst));
+  }
+  return SYLV_OK;
+}
+
+int sylv_get_history(sylv_handle* h, double* hist, int64_t cap, int64_t* len) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
+  const int64_t L = h->iters + 1;
+  if (len) *len = L;
+  if (hist && cap > 0) {
+    CU(cudaMemcpyAsync(hist, h->hist, std::min(cap, L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return SYLV_OK;
+}
+
+int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, int32_t* nblocks) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
+  if (side < 0 || side > 1) return fail(SYLV_EINVAL, "side must be 0 or 1");
+  const int nb = h->nblocks;
+  if (nblocks) *nblocks = nb;
+  if (!H) return SYLV_OK;
+  const int64_t rows = (int64_t)nb * h->s, cols = (int64_t)(nb - 1) * h->s;
+  if (cap < rows * cols) return fail(SYLV_EINVAL, "H buffer too small");
+  const Side& sd = h->side[(side == 1 && !h->lyap) ? 1 : 0];
+  if (rows > 0 && cols > 0) {
+    CU(cudaMemcpy2DAsync(H, rows * sizeof(double), sd.H, h->lds * sizeof(double), rows * sizeof(double), cols,
+                         cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return SYLV_OK;
+}
+
+int sylv_apply(sylv_handle* h, int32_t side, const double* X, double* Y, int64_t k) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (side < 0 || side > 1 || k < 1 || k > 8 || !X || !Y) return fail(SYLV_EINVAL, "bad sylv_apply arguments");
+  const Side& sd = h->side[(side == 1 && !h->lyap) ? 1 : 0];
+  const int64_t n = sd.n;
+  const size_t fsz = h->mixed ? sizeof(float) : sizeof(double);
+  double* xc = nullptr;
+  void *xb = nullptr, *yb = nullptr;
+  CU(cudaMalloc(&xc, n * k * sizeof(double)));
+  int rc = SYLV_OK;
+  cudaError_t e = cudaMalloc(&xb, n * k * fsz);
+  if (e == cudaSuccess) e = cudaMalloc(&yb, n * k * fsz);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xc, X, n * k * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    if (h->mixed) {
+      sylv::launch_pack<float>(h->stream, n, (int)k, xc, (float*)xb);
+      sylv::launch_spmm<float>(h->stream, nullptr, n, (int)k, sd.rp, sd.ci, sd.valf, (float*)xb, (float*)yb, nullptr,
+                               nullptr, 0);
+      sylv::launch_unpack<float>(h->stream, n, (int)k, 1, (float*)yb, n * k, xc);
+    } else {
+      sylv::launch_pack<double>(h->stream, n, (int)k, xc, (double*)xb);
+      sylv::launch_spmm<double>(h->stream, nullptr, n, (int)k, sd.rp, sd.ci, sd.vald, (double*)xb, (double*)yb,
+                                nullptr, nullptr, 0);
+      sylv::launch_unpack<double>(h->stream, n, (int)k, 1, (double*)yb, n * k, xc);
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Y, xc, n * k * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) rc = fail(e == cudaErrorMemoryAllocation ? SYLV_ENOMEM : SYLV_ECUDA, cudaGetErrorString(e));
+  cudaFree(xc);
+  cudaFree(xb);
+  cudaFree(yb);
+  return rc;
+}
+
+int sylv_get_profile(sylv_handle* h, sylv_kernel_stat* out, int32_t cap, int32_t* count) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  int cnt = 0;
+  if (h->prof.valid) {
+    for (int i = 0; i < KC_NUM; ++i) {
+      if (h->prof.launches[i] == 0) continue;
+      if (out && cnt < cap) {
+        sylv_kernel_stat& e = out[cnt];
+        std::memset(&e, 0, sizeof(e));
+        std::strncpy(e.name, kKcNames[i], sizeof(e.name) - 1);
+        e.launches = h->prof.launches[i];
+        e.ms = h->prof.ms[i];
+        e.bytes = h->prof.bytes[i];
+        e.flops = h->prof.flops[i];
+      }
+      ++cnt;
+    }
+  }
+  if (count) *count = cnt;
+  return SYLV_OK;
+}
+
+const char* sylv_strerror(int status) {
+  switch (status) {
+    case SYLV_OK: return "converged";
+    case SYLV_EINVAL: return "invalid argument";
+    case SYLV_ENOMEM: return "out of device memory";
+    case SYLV_ENOTCONV: return "maximum number of iterations reached";
+    case SYLV_EBREAKDOWN: return "breakdown (zero denominator or rank-deficient block)";
+    case SYLV_ENONFINITE: return "non-finite value";
+    case SYLV_ETIMEOUT: return "timed out waiting for the device";
+    case SYLV_ECUDA: return "CUDA error";
+    case SYLV_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* sylv_last_error(void) { return g_err.c_str(); }
+
+void sylv_destroy(sylv_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_solve(h);
+  for (void* p : h->fixed_allocs) cudaFree(p);
+  h->fixed_allocs.clear();
+  if (h->st_host) cudaFreeHost(h->st_host);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->prof.pool) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Device-side definitions shared by the solver kernels.
+//
+// The whole iteration of Algorithms 4.1/4.2 runs on the device: the scalars
+// alpha, beta, omega, rho, the residual norm and the convergence flag live in
+// a DevState in device memory.  Every kernel first reads DevState::status and
+// returns at once when the solve has stopped (converged, breakdown, non-finite),
+// so the host can enqueue iterations ahead of the device and poll only every
+// few iterations.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sylv {
+
+enum DevStatus : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3 };
+
+// Tickets for the "last CTA finishes the reduction" pattern, one per kernel kind.
+enum Ticket : int {
+  TK_CG_Q = 0,
+  TK_CG_UPD = 1,
+  TK_BI_T = 2,
+  TK_BI_UPD = 3,
+  TK_NUM = 8
+};
+
+struct DevState {
+  double rho, alpha, beta, omega;
+  double r0;     // ||R^_0||_F
+  double rnorm;  // ||R^_k||_F of the latest iterate
+  double tol;
+  int status;    // DevStatus
+  int iters;     // completed iterations
+  int exhausted[2];  // per basis side: the block Krylov space is exhausted
+  int breakdown_where;  // diagnostic code of the first breakdown
+  int pad;
+  unsigned int tickets[TK_NUM];
+};
+
+constexpr int NT = 256;  // threads per CTA for the streaming kernels
+
+__device__ __forceinline__ bool stopped(const DevState* st) {
+  return st != nullptr && *((volatile const int*)&st->status) != ST_RUNNING;
+}
+
+// Deterministic block-wide sum of one double per thread (NT threads).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+    sh[0] = t;
+  }
+  __syncthreads();
+  t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// Last-CTA detection after each CTA has written its partial result.
+// Returns true in exactly one CTA (the last to arrive); that CTA resets the ticket.
+__device__ __forceinline__ bool last_cta(unsigned int* ticket, int* flag_sh) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(ticket, 1u);
+    *flag_sh = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *flag_sh != 0;
+  if (last) {
+    __threadfence();
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+  return last;
+}
+
+}  // namespace sylv

@@ -1,0 +1,111 @@
+// Host-side launchers of the solver kernels (internal to libsylv).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sylv {
+
+// ---------------------------------------------------------------- basis side
+// All factor blocks are stored block-row-major: block b is an n x s row-major
+// array at V + b * bstride (bstride = n * s elements).
+
+// Y = Op X (- Xprev M): CSR SpMM over an s-wide block; the optional term is the
+// three-term recurrence of block Lanczos (M = H_{j-1,j}, s x s, column-major ld ldm).
+template <typename T>
+void launch_spmm(cudaStream_t, const DevState*, int64_t n, int s, const int32_t* rp, const int32_t* ci,
+                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm);
+
+// Per-CTA partial Gram products  P_c = sum over the CTA's rows of V_b^T Y  for
+// blocks b = 0..nb-1 (V points at the first block).  Returns the number of CTAs.
+template <typename T>
+int launch_gram(cudaStream_t, const DevState*, int64_t n, int s, const T* V, int64_t bstride, int nb,
+                const T* Y, double* partial);
+
+// Sum the partials in a fixed order: Hc[e] = sum_c partial[c][e], e < nb*s*s, and
+// store (add) the nb*s x s result into H at (row0, col0) (column-major, ld ldh).
+void launch_reduce_H(cudaStream_t, const DevState*, const double* partial, int ncta, int nb, int s, double* H,
+                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add);
+
+// Y -= [V_0 .. V_{nb-1}] Hc  (Hc: nb*s x s row-major).  With self_partial != NULL also
+// writes per-CTA partials of Y^T Y.  Returns the number of CTAs.
+template <typename T>
+int launch_update(cudaStream_t, const DevState*, int64_t n, int s, const T* V, int64_t bstride, int nb,
+                  const double* Hc, T* Y, double* self_partial);
+
+// Per-CTA partials of Y^T Y.  Returns the number of CTAs.
+template <typename T>
+int launch_selfgram(cudaStream_t, const DevState*, int64_t n, int s, const T* Y, double* self_partial);
+
+// Y <- Y Rinv (Rinv s x s upper triangular, column-major), optionally with partials of
+// the new Y^T Y.  Returns the number of CTAs.
+template <typename T>
+int launch_scale(cudaStream_t, const DevState*, int64_t n, int s, T* Y, const T* RinvT, double* self_partial);
+
+// One Cholesky pass of CholQR2 on the s x s Gram reduced from the partials.
+struct CholArgs {
+  int side;           // 0: A basis, 1: B^T basis (exhaustion flag slot)
+  int pass;           // 1 or 2
+  int s;
+  double delta;       // exhaustion / rank-loss threshold
+  const double* Hcol; // pass 1: projection coefficients of this step (column block), or NULL
+  int64_t ldh, hrows; // rows of Hcol to include in nu
+  double* R1;         // pass 1 writes R1 here; pass 2 reads it
+  double* Rinv;       // s x s inverse of this pass's R (float64)
+  void* RinvT;        // same in the factor precision
+  int factor_is_float;
+  double* Hsub;       // pass 2: H_{j+1,j} = R2 R1 stored here (ld ldh), or NULL
+  double* Hsup;       // pass 2, Lanczos: H_{j,j+1} = (R2 R1)^T stored here, or NULL
+  double* Rout;       // pass 2: R2 R1 also stored here (s x s, ld s), or NULL
+  int setup;          // QR of C1/C2: any loss of rank is a breakdown
+};
+void launch_chol(cudaStream_t, DevState*, const double* self_partial, int ncta, const CholArgs&);
+
+// Copy a column-major n x s float64 matrix into block-row-major factor storage.
+template <typename T>
+void launch_pack(cudaStream_t, int64_t n, int s, const double* Ccol, T* Vblk);
+// Block-row-major factors (nb blocks) -> column-major n x (nb s) float64.
+template <typename T>
+void launch_unpack(cudaStream_t, int64_t n, int s, int nb, const T* Vblk, int64_t bstride, double* Vcol);
+// Element-wise float64 -> T conversion.
+template <typename T>
+void launch_convert(cudaStream_t, int64_t count, const double* src, T* dst);
+
+// ---------------------------------------------------------------- small side (float64)
+// Small matrices are column-major with a fixed leading dimension lds, zero outside
+// their extent, so the zero padding of Algorithms 4.1/4.2 costs nothing.
+struct SmallCtx {
+  DevState* st;
+  double* hist;  // residual history
+  int s;
+  int64_t lds;
+  double *Xh, *Rh, *Ph, *Qh, *Sh, *Th, *Rt;  // Rt: shadow residual R~_0 (s x s, ld s)
+  const double* H;  // A-side block Hessenberg (ld ldh)
+  const double* G;  // B^T-side (== H in the Lyapunov case)
+  int64_t ldh;
+  double* partials;  // per-CTA scratch for the fused reductions
+  int lyapunov;
+};
+
+// R^_0 = R_L R_R^T, P^_0 = R^_0, R~_0 = R^_0, rho_0, ||R^_0||, history[0] = 1.
+void launch_init_small(cudaStream_t, const SmallCtx&, const double* RL, const double* RR, double tol, int bicg);
+
+// Algorithm 4.1 pieces.  cg_q: mode 0 Q^ = [H P^, 0] + [P^ G^T; 0]; mode 1 M = [H P^, 0]
+// (Lyapunov, into the T^ buffer); mode 2 Q^ = M + M^T.  Modes 0/2 also set alpha.
+void launch_cg_q(cudaStream_t, const SmallCtx&, int mode, int r);
+// X^ += alpha P^, R^ -= alpha Q^, residual test, rho, beta (extent r -> r+s).
+void launch_cg_update(cudaStream_t, const SmallCtx&, int k, int r);
+// P^ = R^ + beta P^ over extent rp.
+void launch_cg_p(cudaStream_t, const SmallCtx&, int rp);
+
+// Algorithm 4.2 pieces.  Out = [H Z, 0] + [Z G^T; 0] with Z of extent r (block upper
+// Hessenberg H, G); with omega also reduces <Out(1:r,1:r), Z>, <Out, Out> and sets omega.
+void launch_sylv_gemm(cudaStream_t, const SmallCtx&, int r, const double* Z, double* Out, bool omega);
+double sylv_gemm_flops(int r, int s);
+void launch_bicg_alpha(cudaStream_t, const SmallCtx&);
+void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);
+void launch_bicg_update(cudaStream_t, const SmallCtx&, int k, int rp, int rpp);
+void launch_bicg_p(cudaStream_t, const SmallCtx&, int rpp);
+
+}  // namespace sylv

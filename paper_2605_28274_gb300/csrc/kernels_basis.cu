@@ -1,0 +1,575 @@
+// Basis-side kernels of the factorized Krylov methods: the sparse apply and the
+// block orthogonalisation that realise A V_k = V_{k+1} H_{k+1,k} (eq. 3.4) for
+// block Lanczos (Algorithm 4.1) and block Arnoldi (Algorithm 4.2).
+//
+// Data layout: a basis block V_b (n x s) is stored row-major, so one row's s
+// coefficients are contiguous (one 16/32-byte vector) and consecutive rows are
+// consecutive in memory.  The sparse apply gathers whole rows; the Gram and
+// update kernels stream blocks with fully coalesced accesses.
+//
+// Precision: T = double (FP64 mode) or float (mixed mode: FP32 factors, FP32
+// accumulation inside a CTA, FP64 reduction across CTAs and FP64 H).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sylv {
+
+namespace {
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+template <typename T>
+struct AccOf { using type = T; };
+
+// Vector load/store of one row of an s-wide block.
+template <typename T, int S>
+__device__ __forceinline__ void ld_row(const T* p, T (&v)[S]) {
+  if constexpr ((S * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < (int)(S * sizeof(T) / 16); ++i) {
+      uint4 q = *(reinterpret_cast<const uint4*>(p) + i);
+      memcpy(&v[i * 16 / sizeof(T)], &q, 16);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) v[u] = p[u];
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void ld_row_ro(const T* __restrict__ p, T (&v)[S]) {
+  if constexpr ((S * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < (int)(S * sizeof(T) / 16); ++i) {
+      uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + i);
+      memcpy(&v[i * 16 / sizeof(T)], &q, 16);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) v[u] = __ldg(p + u);
+  }
+}
+
+template <typename T, int S>
+__device__ __forceinline__ void st_row(T* p, const T (&v)[S]) {
+  if constexpr ((S * sizeof(T)) % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < (int)(S * sizeof(T) / 16); ++i) {
+      uint4 q;
+      memcpy(&q, &v[i * 16 / sizeof(T)], 16);
+      *(reinterpret_cast<uint4*>(p) + i) = q;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < S; ++u) p[u] = v[u];
+  }
+}
+
+// Block-wide reduction of an S x S register tile into out[0..S*S) (NT threads).
+template <typename A, int S>
+__device__ __forceinline__ void block_reduce_tile(A (&acc)[S][S], double* out, double* sh /* (NT/32) * S*S */) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int u = 0; u < S; ++u)
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      A v = acc[u][t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (l == 0) sh[w * S * S + u * S + t] = (double)v;
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sh[i * S * S + e];
+    out[e] = s;
+  }
+}
+
+// ---------------------------------------------------------------- SpMM
+// One thread per (row, column t): Y[row][t] = sum_p val[p] X[col[p]][t] (- sum_u Xprev[row][u] M[u][t]).
+// The s threads of a row read the same (col, val) pair (broadcast) and s adjacent
+// values of the gathered row (one sector).
+template <typename T, int S>
+__global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n, const int32_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci, const T* __restrict__ val,
+                                                  const T* __restrict__ X, T* __restrict__ Y,
+                                                  const T* __restrict__ Xprev, const double* __restrict__ M,
+                                                  int64_t ldm) {
+  if (stopped(st)) return;
+  const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t row = gid / S;
+  const int t = (int)(gid - row * S);
+  if (row >= n) return;
+  using A = typename AccOf<T>::type;
+  A acc = 0;
+  const int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
+  for (int p = p0; p < p1; ++p) acc += (A)__ldg(val + p) * (A)__ldg(X + (int64_t)__ldg(ci + p) * S + t);
+  if (Xprev != nullptr) {
+#pragma unroll
+    for (int u = 0; u < S; ++u) acc -= (A)__ldg(Xprev + row * S + u) * (A)M[u + (int64_t)t * ldm];
+  }
+  Y[row * S + t] = (T)acc;
+}
+
+// ---------------------------------------------------------------- Gram (TSGEMM)
+// CTA c owns rows [c*rpc, (c+1)*rpc).  Warp tasks = (block b, row slice); a task
+// streams V_b over its rows (lanes = consecutive rows, coalesced), accumulates the
+// S x S tile V_b^T Y in registers, reduces it across the warp and writes it.
+// When there are fewer blocks than warps, rows are split into slices and the
+// slice tiles are summed through shared memory in a fixed order.
+template <typename T, int S>
+__global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n, int64_t rpc, const T* __restrict__ V,
+                                                  int64_t bstride, int nb, const T* __restrict__ Y,
+                                                  double* __restrict__ partial) {
+  if (stopped(st)) return;
+  __shared__ double sh[(NT / 32) * S * S];
+  using A = typename AccOf<T>::type;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = NT / 32;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc;
+  const int64_t r1 = min(n, r0 + rpc);
+  const int slices = nb >= nw ? 1 : nw / nb;
+  const int ntasks = nb * slices;
+  double* out = partial + (int64_t)blockIdx.x * nb * S * S;
+  for (int task = w; task < ntasks; task += nw) {
+    const int b = task / slices, sl = task - b * slices;
+    const T* Vb = V + (int64_t)b * bstride;
+    A acc[S][S];
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[u][t] = 0;
+    for (int64_t row = r0 + (int64_t)sl * 32 + l; row < r1; row += 32 * slices) {
+      T v[S], y[S];
+      ld_row_ro<T, S>(Vb + row * S, v);
+      ld_row<T, S>(Y + row * S, y);
+#pragma unroll
+      for (int u = 0; u < S; ++u)
+#pragma unroll
+        for (int t = 0; t < S; ++t) acc[u][t] += (A)v[u] * (A)y[t];
+    }
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        A v = acc[u][t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int e = u * S + t;
+        if (slices == 1) {
+          if (l == (e & 31)) out[b * S * S + e] = (double)v;
+        } else {
+          if (l == (e & 31)) sh[task * S * S + e] = (double)v;
+        }
+      }
+  }
+  if (slices > 1) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * S * S; e += NT) {
+      const int b = e / (S * S), r = e - b * S * S;
+      double s = 0.0;
+      for (int sl = 0; sl < slices; ++sl) s += sh[(b * slices + sl) * S * S + r];
+      out[e] = s;
+    }
+  }
+}
+
+__global__ void reduce_H_kernel(const DevState* st, const double* __restrict__ partial, int ncta, int nb, int s,
+                                double* __restrict__ H, int64_t ldh, int64_t row0, int64_t col0,
+                                double* __restrict__ Hc, int add) {
+  if (stopped(st)) return;
+  const int E = nb * s * s;
+  const int e = blockIdx.x * NT + threadIdx.x;
+  if (e >= E) return;
+  double v = 0.0;
+  for (int c = 0; c < ncta; ++c) v += partial[(int64_t)c * E + e];
+  Hc[e] = v;
+  const int b = e / (s * s), r = e - b * s * s, u = r / s, t = r - u * s;
+  double* h = H + (row0 + (int64_t)b * s + u) + (col0 + t) * ldh;
+  *h = add ? (*h + v) : v;
+}
+
+// ---------------------------------------------------------------- block update
+// One thread per row (grid-stride): y -= sum_b V_b[row] Hc_b, with Hc staged in
+// shared memory in chunks; optionally accumulates the partial Y^T Y of the result.
+template <typename T, int S>
+constexpr int upd_chunk() {
+  return (int)std::max<size_t>(1, (32 * 1024) / (S * S * sizeof(T)));
+}
+
+template <typename T, int S, bool SELF>
+__global__ void __launch_bounds__(NT) update_kernel(const DevState* st, int64_t n, const T* __restrict__ V,
+                                                    int64_t bstride, int nb, const double* __restrict__ Hc,
+                                                    T* __restrict__ Y, double* __restrict__ partial) {
+  if (stopped(st)) return;
+  constexpr int CH = upd_chunk<T, S>();
+  __shared__ __align__(16) T hs[CH * S * S];
+  __shared__ double sh[(NT / 32) * S * S];
+  using A = typename AccOf<T>::type;
+  A acc[S][S];
+  if constexpr (SELF) {
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[u][t] = 0;
+  }
+  for (int64_t base = (int64_t)blockIdx.x * NT; base < n; base += (int64_t)gridDim.x * NT) {
+    const int64_t row = base + threadIdx.x;
+    T y[S];
+    if (row < n) ld_row<T, S>(Y + row * S, y);
+    for (int b0 = 0; b0 < nb; b0 += CH) {
+      const int cb = min(CH, nb - b0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cb * S * S; e += NT) hs[e] = (T)Hc[(int64_t)b0 * S * S + e];
+      __syncthreads();
+      if (row < n) {
+        for (int b = 0; b < cb; ++b) {
+          T v[S];
+          ld_row_ro<T, S>(V + (int64_t)(b0 + b) * bstride + row * S, v);
+#pragma unroll
+          for (int u = 0; u < S; ++u)
+#pragma unroll
+            for (int t = 0; t < S; ++t) y[t] -= v[u] * hs[(b * S + u) * S + t];
+        }
+      }
+    }
+    if (row < n) {
+      st_row<T, S>(Y + row * S, y);
+      if constexpr (SELF) {
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+          for (int t = 0; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];
+      }
+    }
+  }
+  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(NT) selfgram_kernel(const DevState* st, int64_t n, const T* __restrict__ Y,
+                                                      double* __restrict__ partial) {
+  if (stopped(st)) return;
+  __shared__ double sh[(NT / 32) * S * S];
+  using A = typename AccOf<T>::type;
+  A acc[S][S];
+#pragma unroll
+  for (int u = 0; u < S; ++u)
+#pragma unroll
+    for (int t = 0; t < S; ++t) acc[u][t] = 0;
+  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
+    T y[S];
+    ld_row<T, S>(Y + row * S, y);
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];
+  }
+  block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+}
+
+template <typename T, int S, bool SELF>
+__global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n, T* __restrict__ Y,
+                                                   const T* __restrict__ Rinv, double* __restrict__ partial) {
+  if (stopped(st)) return;
+  __shared__ T rs[S * S];
+  __shared__ double sh[(NT / 32) * S * S];
+  if (threadIdx.x < S * S) rs[threadIdx.x] = Rinv[threadIdx.x];
+  __syncthreads();
+  using A = typename AccOf<T>::type;
+  A acc[S][S];
+  if constexpr (SELF) {
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[u][t] = 0;
+  }
+  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
+    T y[S], z[S];
+    ld_row<T, S>(Y + row * S, y);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      T a = 0;
+#pragma unroll
+      for (int u = 0; u <= t; ++u) a += y[u] * rs[u + t * S];
+      z[t] = a;
+    }
+    st_row<T, S>(Y + row * S, z);
+    if constexpr (SELF) {
+#pragma unroll
+      for (int u = 0; u < S; ++u)
+#pragma unroll
+        for (int t = 0; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];
+    }
+  }
+  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+}
+
+// ---------------------------------------------------------------- CholQR pass
+// Single CTA: G = sum of the partial Gram tiles; nu^2 = ||H_{1:j,j}||^2 + tr(G);
+// exhaustion if tr(G) <= delta^2 nu^2 (the block becomes zero); Cholesky G = R^T R
+// (upper R, positive diagonal); a pivot <= (delta nu)^2 on pass 1 is a partial loss
+// of rank (breakdown).  Writes R^{-1} for the scale kernel and, on pass 2,
+// H_{j+1,j} = R2 R1.
+__global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __restrict__ partial, int ncta,
+                                                  CholArgs a) {
+  if (stopped(st)) return;
+  __shared__ double G[64], R[64], Ri[64], sh[32];
+  __shared__ double nu2_sh;
+  __shared__ int exh_sh;
+  const int s = a.s, E = s * s;
+  for (int e = 0; e < E; ++e) {
+    double v = 0.0;
+    for (int c = threadIdx.x; c < ncta; c += NT) v += partial[(int64_t)c * E + e];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) G[e] = v;
+  }
+  double hsq = 0.0;
+  if (a.pass == 1 && a.Hcol != nullptr) {
+    for (int64_t i = threadIdx.x; i < a.hrows * s; i += NT) {
+      const int64_t rr = i % a.hrows, cc = i / a.hrows;
+      const double h = a.Hcol[rr + cc * a.ldh];
+      hsq += h * h;
+    }
+  }
+  hsq = block_sum(hsq, sh);
+  if (threadIdx.x == 0) {
+    // G[u*s+t] = sum_rows y_u y_t (symmetric)
+    double tr = 0.0;
+    bool finite = true;
+    for (int e = 0; e < E; ++e) finite = finite && isfinite(G[e]);
+    for (int u = 0; u < s; ++u) tr += G[u * s + u];
+    const double nu2 = hsq + tr;
+    nu2_sh = nu2;
+    int exh = (a.pass == 2) ? st->exhausted[a.side] : 0;
+    int bad = 0;
+    if (!finite || !isfinite(hsq)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 100 + a.side;
+      bad = 1;
+    } else if (a.pass == 1 && !a.setup && tr <= a.delta * a.delta * nu2) {
+      exh = 1;
+      st->exhausted[a.side] = 1;
+    }
+    for (int e = 0; e < 64; ++e) { R[e] = 0.0; Ri[e] = 0.0; }
+    if (!bad && !exh) {
+      const double thr = (a.pass == 1) ? a.delta * a.delta * nu2 : 0.0;
+      for (int j = 0; j < s && !bad; ++j) {
+        double d = G[j * s + j];
+        for (int k = 0; k < j; ++k) d -= R[k + j * s] * R[k + j * s];
+        if (!(d > thr)) {
+          bad = 1;
+          st->status = ST_BREAKDOWN;
+          st->breakdown_where = 10 + a.side;
+          break;
+        }
+        const double rjj = sqrt(d);
+        R[j + j * s] = rjj;
+        for (int i = j + 1; i < s; ++i) {
+          double g = G[j * s + i];
+          for (int k = 0; k < j; ++k) g -= R[k + j * s] * R[k + i * s];
+          R[j + i * s] = g / rjj;
+        }
+      }
+      if (!bad) {
+        for (int j = 0; j < s; ++j) {
+          Ri[j + j * s] = 1.0 / R[j + j * s];
+          for (int i = j - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int k = i; k < j; ++k) acc += Ri[i + k * s] * R[k + j * s];
+            Ri[i + j * s] = -acc / R[j + j * s];
+          }
+        }
+      }
+    }
+    exh_sh = exh;
+    if (!bad) {
+      for (int e = 0; e < E; ++e) {
+        a.Rinv[e] = Ri[e];
+        if (a.factor_is_float) ((float*)a.RinvT)[e] = (float)Ri[e];
+        else ((double*)a.RinvT)[e] = Ri[e];
+      }
+      if (a.pass == 1) {
+        for (int e = 0; e < E; ++e) a.R1[e] = R[e];
+      } else {
+        // R2 R1 (both upper triangular)
+        for (int j = 0; j < s; ++j)
+          for (int i = 0; i < s; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < s; ++k) acc += R[i + k * s] * a.R1[k + j * s];
+            if (exh) acc = 0.0;
+            if (a.Hsub) a.Hsub[i + j * a.ldh] = acc;
+            if (a.Hsup) a.Hsup[j + i * a.ldh] = acc;
+            if (a.Rout) a.Rout[i + j * s] = acc;
+          }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- layout helpers
+template <typename T, int S>
+__global__ void pack_kernel(int64_t n, const double* __restrict__ Ccol, T* __restrict__ V) {
+  const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (gid >= n * S) return;
+  const int64_t row = gid / S;
+  const int t = (int)(gid - row * S);
+  V[gid] = (T)Ccol[row + t * n];
+}
+
+template <typename T>
+__global__ void unpack_kernel(int64_t n, int s, int64_t total, const T* __restrict__ V, int64_t bstride,
+                              double* __restrict__ Vcol) {
+  const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (gid >= total) return;
+  const int64_t col = gid / n, row = gid - col * n;
+  const int64_t b = col / s, t = col - b * s;
+  Vcol[gid] = (double)V[b * bstride + row * s + t];
+}
+
+template <typename T>
+__global__ void convert_kernel(int64_t count, const double* __restrict__ src, T* __restrict__ dst) {
+  const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (gid < count) dst[gid] = (T)src[gid];
+}
+
+int grid_for(int64_t work, int64_t per, int cap) {
+  int64_t g = (work + per - 1) / per;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+#define SYLV_S_CASES(MACRO) \
+  MACRO(1) MACRO(2) MACRO(3) MACRO(4) MACRO(5) MACRO(6) MACRO(7) MACRO(8)
+
+template <typename T>
+void launch_spmm(cudaStream_t strm, const DevState* st, int64_t n, int s, const int32_t* rp, const int32_t* ci,
+                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm) {
+  const int64_t threads = n * s;
+  const int grid = (int)((threads + NT - 1) / NT);
+  if (grid == 0) return;
+#define CASE(SV) \
+  case SV: spmm_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm); break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+}
+
+template <typename T>
+int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T* V, int64_t bstride, int nb,
+                const T* Y, double* partial) {
+  const int grid = grid_for(n, 64, 2 * num_sms());
+  const int64_t rpc = (n + grid - 1) / grid;
+#define CASE(SV) \
+  case SV: gram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, partial); break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+void launch_reduce_H(cudaStream_t strm, const DevState* st, const double* partial, int ncta, int nb, int s, double* H,
+                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add) {
+  const int E = nb * s * s;
+  reduce_H_kernel<<<(E + NT - 1) / NT, NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc, add ? 1 : 0);
+}
+
+template <typename T>
+int launch_update(cudaStream_t strm, const DevState* st, int64_t n, int s, const T* V, int64_t bstride, int nb,
+                  const double* Hc, T* Y, double* self_partial) {
+  const int grid = grid_for(n, NT, 4 * num_sms());
+#define CASE(SV)                                                                                         \
+  case SV:                                                                                               \
+    if (self_partial)                                                                                    \
+      update_kernel<T, SV, true><<<grid, NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, self_partial);     \
+    else                                                                                                 \
+      update_kernel<T, SV, false><<<grid, NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, nullptr);         \
+    break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+template <typename T>
+int launch_selfgram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T* Y, double* self_partial) {
+  const int grid = grid_for(n, NT, 4 * num_sms());
+#define CASE(SV) \
+  case SV: selfgram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, Y, self_partial); break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+template <typename T>
+int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, const T* RinvT, double* self_partial) {
+  const int grid = grid_for(n, NT, 4 * num_sms());
+#define CASE(SV)                                                                               \
+  case SV:                                                                                     \
+    if (self_partial)                                                                          \
+      scale_kernel<T, SV, true><<<grid, NT, 0, strm>>>(st, n, Y, RinvT, self_partial);         \
+    else                                                                                       \
+      scale_kernel<T, SV, false><<<grid, NT, 0, strm>>>(st, n, Y, RinvT, nullptr);             \
+    break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+void launch_chol(cudaStream_t strm, DevState* st, const double* self_partial, int ncta, const CholArgs& a) {
+  chol_kernel<<<1, NT, 0, strm>>>(st, self_partial, ncta, a);
+}
+
+template <typename T>
+void launch_pack(cudaStream_t strm, int64_t n, int s, const double* Ccol, T* Vblk) {
+  const int grid = (int)((n * s + NT - 1) / NT);
+  if (grid == 0) return;
+#define CASE(SV) \
+  case SV: pack_kernel<T, SV><<<grid, NT, 0, strm>>>(n, Ccol, Vblk); break;
+  switch (s) { SYLV_S_CASES(CASE) }
+#undef CASE
+}
+
+template <typename T>
+void launch_unpack(cudaStream_t strm, int64_t n, int s, int nb, const T* Vblk, int64_t bstride, double* Vcol) {
+  const int64_t total = n * s * (int64_t)nb;
+  if (total == 0) return;
+  unpack_kernel<T><<<(unsigned)((total + NT - 1) / NT), NT, 0, strm>>>(n, s, total, Vblk, bstride, Vcol);
+}
+
+template <typename T>
+void launch_convert(cudaStream_t strm, int64_t count, const double* src, T* dst) {
+  if (count == 0) return;
+  convert_kernel<T><<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, src, dst);
+}
+
+#define SYLV_INST(T)                                                                                              \
+  template void launch_spmm<T>(cudaStream_t, const DevState*, int64_t, int, const int32_t*, const int32_t*,      \
+                               const T*, const T*, T*, const T*, const double*, int64_t);                        \
+  template int launch_gram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, int64_t, int, const T*,     \
+                              double*);                                                                          \
+  template int launch_update<T>(cudaStream_t, const DevState*, int64_t, int, const T*, int64_t, int,             \
+                                const double*, T*, double*);                                                     \
+  template int launch_selfgram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, double*);               \
+  template int launch_scale<T>(cudaStream_t, const DevState*, int64_t, int, T*, const T*, double*);              \
+  template void launch_pack<T>(cudaStream_t, int64_t, int, const double*, T*);                                  \
+  template void launch_unpack<T>(cudaStream_t, int64_t, int, int, const T*, int64_t, double*);                  \
+  template void launch_convert<T>(cudaStream_t, int64_t, const double*, T*);
+
+SYLV_INST(double)
+SYLV_INST(float)
+
+}  // namespace sylv

@@ -1,0 +1,445 @@
+// Small-matrix side of the factorized methods, all in float64 on the device:
+// the factored Sylvester operator (eq. 3.7), the inner products that give
+// alpha, beta, omega, rho (eq. 3.6), the padded updates of X^, R^, P^ (and S^,
+// T^), and the convergence test ||R^_{k+1}|| <= tol ||R^_0|| (Algorithms 4.1, 4.2).
+//
+// Small matrices are column-major with one fixed leading dimension and are
+// zero outside their current extent, so each padding [M O; O O] of the
+// algorithms is free: a kernel only ever writes inside the new extent.
+// Reductions are deterministic: every CTA writes its partial sum, the last CTA
+// to finish adds them in index order and updates the scalars in DevState.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sylv {
+
+namespace {
+
+// ---------------------------------------------------------------- init
+__global__ void init_small_kernel(DevState* st, double* hist, int s, int64_t lds, double* Rh, double* Ph,
+                                  double* Rt, const double* __restrict__ RL, const double* __restrict__ RR,
+                                  double tol, int bicg) {
+  // one CTA, thread 0 (s <= 8)
+  if (threadIdx.x != 0) return;
+  hist[0] = 1.0;
+  if (st->status != ST_RUNNING) return;  // the QR of C1 or C2 already failed
+  double nrm2 = 0.0;
+  for (int t = 0; t < s; ++t)
+    for (int u = 0; u < s; ++u) {
+      double acc = 0.0;  // (R_L R_R^T)[u][t] = sum_c R_L[u][c] R_R[t][c]
+      for (int c = 0; c < s; ++c) acc += RL[u + c * s] * RR[t + c * s];
+      Rh[u + t * lds] = acc;
+      Ph[u + t * lds] = acc;
+      Rt[u + t * s] = acc;
+      nrm2 += acc * acc;
+    }
+  st->r0 = sqrt(nrm2);
+  st->rnorm = st->r0;
+  st->rho = nrm2;  // <R^_0, R^_0> (CG) = <R~_0, R^_0> (BiCGSTAB, R~_0 = R^_0)
+  st->alpha = st->beta = st->omega = 0.0;
+  st->tol = tol;
+  st->iters = 0;
+  st->exhausted[0] = st->exhausted[1] = 0;
+  if (!isfinite(nrm2)) st->status = ST_NONFINITE;
+  else if (nrm2 == 0.0) st->status = ST_CONVERGED;  // C1 C2^T = 0: X = 0
+  else st->status = ST_RUNNING;
+  (void)bicg;
+}
+
+// ---------------------------------------------------------------- CG: Q^ for block tridiagonal H, G
+// mode 0: Q^ = [H P^, 0] + [P^ G^T; 0]   (Sylvester)
+// mode 1: M  = [H P^, 0]                 (Lyapunov, first half)
+// mode 2: Q^ = M + M^T                   (Lyapunov, second half; Out is Q^, In is M)
+// Modes 0 and 2 also reduce <P^, Q^(1:r,1:r)> and set alpha = rho / that (last CTA).
+__global__ void __launch_bounds__(NT) cg_q_kernel(DevState* st, int mode, int r, int s, const double* __restrict__ H,
+                                                  const double* __restrict__ G, int64_t ldh,
+                                                  const double* __restrict__ P, const double* __restrict__ In,
+                                                  double* __restrict__ Out, int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int rp = r + s;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  double pq = 0.0;
+  if (a < rp) {
+    double q = 0.0;
+    if (mode == 2) {
+      q = In[a + (int64_t)b * lds] + In[b + (int64_t)a * lds];
+    } else {
+      const int ba = a / s;
+      if (b < r) {  // [H P^, 0]: H_{ba, c} nonzero for blocks ba-1..ba+1
+        const int c0 = max(0, (ba - 1) * s), c1 = min(r, (ba + 2) * s);
+        for (int c = c0; c < c1; ++c) q += H[a + (int64_t)c * ldh] * P[c + (int64_t)b * lds];
+      }
+      if (mode == 0 && a < r) {  // [P^ G^T; 0]
+        const int bb = b / s;
+        const int c0 = max(0, (bb - 1) * s), c1 = min(r, (bb + 2) * s);
+        double q2 = 0.0;
+        for (int c = c0; c < c1; ++c) q2 += P[a + (int64_t)c * lds] * G[b + (int64_t)c * ldh];
+        q += q2;
+      }
+    }
+    Out[a + (int64_t)b * lds] = q;
+    if (a < r && b < r) pq = P[a + (int64_t)b * lds] * q;
+  }
+  if (mode == 1) return;
+  pq = block_sum(pq, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = pq;
+  if (last_cta(&st->tickets[TK_CG_Q], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    if (!isfinite(tot)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 1;
+    } else if (!(tot > 0.0)) {  // <P, Q> <= 0: F not positive definite on this direction
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 2;
+    } else {
+      st->alpha = st->rho / tot;
+    }
+  }
+}
+
+// X^ <- pad(X^) + alpha P^ (extent r), R^ <- pad(R^) - alpha Q^ (extent r+s); then the
+// test, rho_{k+1} = <R^,R^>, beta = rho_{k+1}/rho_k (last CTA).
+__global__ void __launch_bounds__(NT) cg_update_kernel(DevState* st, double* hist, int k, int r, int s,
+                                                       double* __restrict__ X, double* __restrict__ R,
+                                                       const double* __restrict__ P, const double* __restrict__ Q,
+                                                       int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int rp = r + s;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  const double alpha = st->alpha;
+  double rr = 0.0;
+  if (a < rp) {
+    const int64_t i = a + (int64_t)b * lds;
+    if (a < r && b < r) X[i] = X[i] + alpha * P[i];
+    const double v = R[i] - alpha * Q[i];
+    R[i] = v;
+    rr = v * v;
+  }
+  rr = block_sum(rr, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = rr;
+  if (last_cta(&st->tickets[TK_CG_UPD], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    const double rn = sqrt(tot);
+    hist[k + 1] = rn / st->r0;
+    st->rnorm = rn;
+    st->iters = k + 1;
+    if (!isfinite(rn)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 3;
+    } else if (rn <= st->r0 * st->tol) {
+      st->status = ST_CONVERGED;
+    } else {
+      st->beta = tot / st->rho;
+      st->rho = tot;
+    }
+  }
+}
+
+// P^ <- R^ + beta pad(P^) over extent rp.
+__global__ void __launch_bounds__(NT) cg_p_kernel(const DevState* st, int rp, double* __restrict__ P,
+                                                  const double* __restrict__ R, int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= rp) return;
+  const int64_t i = a + (int64_t)b * lds;
+  P[i] = R[i] + st->beta * P[i];
+}
+
+// ---------------------------------------------------------------- BiCGSTAB: dense factored operator
+// Out = [H Z, 0] + [Z G^T; 0] for Z with extent r (H, G block upper Hessenberg,
+// (r+s) x r).  64 x 64 output tiles, 16-deep k-slices in shared memory, 4 x 4
+// outputs per thread; k-slices left of the Hessenberg band of a tile are skipped.
+// With OMEGA, the tile also reduces <Out(1:r,1:r), Z> and <Out, Out> and the last
+// CTA sets omega (Algorithm 4.2).
+constexpr int GBM = 64, GBK = 16;
+
+template <bool OMEGA>
+__global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int s, const double* __restrict__ H,
+                                                       const double* __restrict__ G, int64_t ldh,
+                                                       const double* __restrict__ Z, double* __restrict__ Out,
+                                                       int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ double As[GBK][GBM + 1];
+  __shared__ double Bs[GBK][GBM + 1];
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int rp = r + s;
+  const int a0 = blockIdx.x * GBM, b0 = blockIdx.y * GBM;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  // term 1: (H Z)[a][b] for b < r
+  if (b0 < r) {
+    const int clo = max(0, (a0 / s - 1) * s);
+    for (int c0 = clo; c0 < r; c0 += GBK) {
+      for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
+        const int aa = e % GBM, kk = e / GBM;  // H column-major: contiguous in a
+        const int a = a0 + aa, c = c0 + kk;
+        As[kk][aa] = (a < rp && c < r) ? H[a + (int64_t)c * ldh] : 0.0;
+        const int kk2 = e % GBK, bb = e / GBK;  // Z column-major: contiguous in c
+        const int c2 = c0 + kk2, b = b0 + bb;
+        Bs[kk2][bb] = (c2 < r && b < r) ? Z[c2 + (int64_t)b * lds] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+      __syncthreads();
+    }
+  }
+  // term 2: (Z G^T)[a][b] for a < r
+  if (a0 < r) {
+    const int clo = max(0, (b0 / s - 1) * s);
+    for (int c0 = clo; c0 < r; c0 += GBK) {
+      for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
+        const int aa = e % GBM, kk = e / GBM;
+        const int a = a0 + aa, c = c0 + kk;
+        As[kk][aa] = (a < r && c < r) ? Z[a + (int64_t)c * lds] : 0.0;
+        const int b = b0 + aa;  // G^T[c][b] = G[b][c]: contiguous in b
+        Bs[kk][aa] = (b < rp && c < r) ? G[b + (int64_t)c * ldh] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GBK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+      }
+      __syncthreads();
+    }
+  }
+  double ts = 0.0, tt = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + tx + 16 * i, b = b0 + ty + 16 * j;
+      if (a < rp && b < rp) {
+        Out[a + (int64_t)b * lds] = acc[i][j];
+        if (OMEGA) {
+          tt += acc[i][j] * acc[i][j];
+          if (a < r && b < r) ts += acc[i][j] * Z[a + (int64_t)b * lds];
+        }
+      }
+    }
+  if (!OMEGA) return;
+  ts = block_sum(ts, sh);
+  tt = block_sum(tt, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) {
+    partials[2 * bid] = ts;
+    partials[2 * bid + 1] = tt;
+  }
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      s1 += __ldcg(partials + 2 * i);
+      s2 += __ldcg(partials + 2 * i + 1);
+    }
+    if (!isfinite(s1) || !isfinite(s2)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 4;
+    } else if (s2 == 0.0 || s1 == 0.0) {  // T = 0 or omega = 0
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 5;
+    } else {
+      st->omega = s1 / s2;
+    }
+  }
+}
+
+// alpha_k = rho_k / <R~_0, Q^(1:s,1:s)>  (one CTA)
+__global__ void bicg_alpha_kernel(DevState* st, int s, const double* __restrict__ Rt, const double* __restrict__ Q,
+                                  int64_t lds) {
+  if (stopped(st)) return;
+  if (threadIdx.x != 0) return;
+  double d = 0.0;
+  for (int t = 0; t < s; ++t)
+    for (int u = 0; u < s; ++u) d += Rt[u + t * s] * Q[u + (int64_t)t * lds];
+  if (!isfinite(d)) {
+    st->status = ST_NONFINITE;
+    st->breakdown_where = 6;
+  } else if (d == 0.0) {
+    st->status = ST_BREAKDOWN;
+    st->breakdown_where = 7;
+  } else {
+    st->alpha = st->rho / d;
+  }
+}
+
+// S^ = pad(R^) - alpha Q^ over extent rp
+__global__ void __launch_bounds__(NT) bicg_s_kernel(const DevState* st, int rp, double* __restrict__ S,
+                                                    const double* __restrict__ R, const double* __restrict__ Q,
+                                                    int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= rp) return;
+  const int64_t i = a + (int64_t)b * lds;
+  S[i] = R[i] - st->alpha * Q[i];
+}
+
+// X^ <- pad(X^) + pad(alpha P^) + omega S^ (extent rp); R^ <- pad(S^) - omega T^ (extent rpp);
+// then the test, rho_{k+1} = <R~_0, R^(1:s,1:s)>, beta = (alpha/omega)(rho_{k+1}/rho_k).
+__global__ void __launch_bounds__(NT) bicg_update_kernel(DevState* st, double* hist, int k, int rp, int rpp, int s,
+                                                         double* __restrict__ X, double* __restrict__ R,
+                                                         const double* __restrict__ P,
+                                                         const double* __restrict__ S,
+                                                         const double* __restrict__ T, const double* __restrict__ Rt,
+                                                         int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  const double alpha = st->alpha, omega = st->omega;
+  double rr = 0.0;
+  if (a < rpp) {
+    const int64_t i = a + (int64_t)b * lds;
+    if (a < rp && b < rp) X[i] = X[i] + alpha * P[i] + omega * S[i];
+    const double v = S[i] - omega * T[i];
+    R[i] = v;
+    rr = v * v;
+  }
+  rr = block_sum(rr, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = rr;
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    const double rn = sqrt(tot);
+    hist[k + 1] = rn / st->r0;
+    st->rnorm = rn;
+    st->iters = k + 1;
+    if (!isfinite(rn)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 8;
+    } else if (rn <= st->r0 * st->tol) {
+      st->status = ST_CONVERGED;
+    } else {
+      double rho_new = 0.0;
+      for (int t = 0; t < s; ++t)
+        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+      if (rho_new == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 9;
+      } else {
+        st->beta = (alpha / omega) * (rho_new / st->rho);
+        st->rho = rho_new;
+      }
+    }
+  }
+}
+
+// P^ <- R^ + beta (pad(P^) - omega pad(Q^)) over extent rpp
+__global__ void __launch_bounds__(NT) bicg_p_kernel(const DevState* st, int rpp, double* __restrict__ P,
+                                                    const double* __restrict__ R, const double* __restrict__ Q,
+                                                    int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= rpp) return;
+  const int64_t i = a + (int64_t)b * lds;
+  P[i] = R[i] + st->beta * (P[i] - st->omega * Q[i]);
+}
+
+dim3 elem_grid(int rows, int cols) { return dim3((unsigned)((rows + NT - 1) / NT), (unsigned)cols); }
+
+}  // namespace
+
+void launch_init_small(cudaStream_t strm, const SmallCtx& c, const double* RL, const double* RR, double tol,
+                       int bicg) {
+  init_small_kernel<<<1, 32, 0, strm>>>(c.st, c.hist, c.s, c.lds, c.Rh, c.Ph, c.Rt, RL, RR, tol, bicg);
+}
+
+void launch_cg_q(cudaStream_t strm, const SmallCtx& c, int mode, int r) {
+  const int rp = r + c.s;
+  double* out = mode == 1 ? c.Th : c.Qh;  // Lyapunov: the T^ buffer holds M = [H P^, 0]
+  cg_q_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, mode, r, c.s, c.H, c.G, c.ldh, c.Ph, c.Th, out, c.lds,
+                                                  c.partials);
+}
+
+void launch_cg_update(cudaStream_t strm, const SmallCtx& c, int k, int r) {
+  const int rp = r + c.s;
+  cg_update_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, c.hist, k, r, c.s, c.Xh, c.Rh, c.Ph, c.Qh, c.lds,
+                                                       c.partials);
+}
+
+void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
+  cg_p_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, rp, c.Ph, c.Rh, c.lds);
+}
+
+void launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
+  const int rp = r + c.s;
+  const dim3 gg((rp + GBM - 1) / GBM, (rp + GBM - 1) / GBM);
+  if (omega)
+    sylv_gemm_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
+  else
+    sylv_gemm_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
+}
+
+double sylv_gemm_flops(int r, int s) {
+  // structural flops of [H Z, 0] + [Z G^T; 0] with block upper Hessenberg H, G
+  double f = 0.0;
+  const int rp = r + s;
+  for (int a = 0; a < rp; ++a) {
+    const int lo = std::max(0, (a / s - 1) * s);
+    f += 2.0 * (double)r * (double)std::max(0, r - lo);  // row a of H Z (r columns) / column a of Z G^T
+  }
+  return 2.0 * f;
+}
+
+void launch_bicg_alpha(cudaStream_t strm, const SmallCtx& c) {
+  bicg_alpha_kernel<<<1, 32, 0, strm>>>(c.st, c.s, c.Rt, c.Qh, c.lds);
+}
+
+void launch_bicg_s(cudaStream_t strm, const SmallCtx& c, int rp) {
+  bicg_s_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, rp, c.Sh, c.Rh, c.Qh, c.lds);
+}
+
+void launch_bicg_update(cudaStream_t strm, const SmallCtx& c, int k, int rp, int rpp) {
+  bicg_update_kernel<<<elem_grid(rpp, rpp), NT, 0, strm>>>(c.st, c.hist, k, rp, rpp, c.s, c.Xh, c.Rh, c.Ph, c.Sh,
+                                                           c.Th, c.Rt, c.lds, c.partials);
+}
+
+void launch_bicg_p(cudaStream_t strm, const SmallCtx& c, int rpp) {
+  bicg_p_kernel<<<elem_grid(rpp, rpp), NT, 0, strm>>>(c.st, rpp, c.Ph, c.Rh, c.Qh, c.lds);
+}
+
+}  // namespace sylv
