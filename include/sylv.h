@@ -171,6 +171,37 @@ int sylv_apply(sylv_handle* h, int32_t side, const double* X, double* Y, int64_t
  */
 int sylv_get_profile(sylv_handle* h, sylv_kernel_stat* out, int32_t cap, int32_t* count);
 
+/* Largest n * k accepted by sylv_spmm_noalloc: the size, in doubles, of its
+ * fixed staging area for X (the same again is reserved for Y, 16 MiB in all). */
+#define SYLV_NOALLOC_MAX_ELEMS (1 << 20)
+
+/*
+ * Y = A X without allocating device memory: the sparse block product of
+ * sylv_apply for callers that cannot call cudaMalloc -- processes whose device
+ * memory is owned by another allocator (for example a framework's caching pool
+ * holding the device memory budget) and latency-bound loops that cannot afford
+ * the device-wide synchronisation cudaMalloc/cudaFree may cause.  The paper has
+ * no counterpart; this is a library facility.
+ *   n, nnz, row_ptr, col_idx, val   A (n x n) in CSR form, all DEVICE pointers
+ *   X, Y                            DEVICE pointers, n x k column-major; 1 <= k <= 8
+ *   cuda_stream                     cudaStream_t (NULL: the legacy default stream)
+ * Float64.  Asynchronous: returns once the kernels are enqueued on cuda_stream;
+ * launch errors are returned, errors inside the kernels surface at the caller's
+ * next synchronisation.  The inputs and outputs stay owned by the caller.
+ * Staging uses one fixed device array compiled into the library (every GPU that
+ * loads it holds 16 MiB until the process exits).  Limits and rules:
+ *  - n * k > SYLV_NOALLOC_MAX_ELEMS returns SYLV_EINVAL (use sylv_apply);
+ *  - the first call on each device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture;
+ *  - every call, on every stream, shares the one array: calls that can overlap
+ *    on the GPU (different streams without ordering) race and corrupt each
+ *    other's results; order them on one stream or with events.
+ * Errors: SYLV_EINVAL (arguments, size limit), SYLV_ECUDA.
+ */
+int sylv_spmm_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                      const double* X, double* Y, int64_t k, void* cuda_stream);
+
 const char* sylv_strerror(int status);
 const char* sylv_last_error(void);
 void sylv_destroy(sylv_handle* h);

@@ -28,8 +28,8 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_get_factors",
-           "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_strerror",
-           "sylv_last_error", "sylv_destroy"]
+           "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
+           "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
 
 class sylv_csr(ctypes.Structure):
@@ -99,6 +99,10 @@ def load(path: Optional[str] = None):
     lib.sylv_apply.restype = ctypes.c_int
     lib.sylv_get_profile.argtypes = [ctypes.c_void_p, P(sylv_kernel_stat), ctypes.c_int32, P(ctypes.c_int32)]
     lib.sylv_get_profile.restype = ctypes.c_int
+    lib.sylv_spmm_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_void_p]
+    lib.sylv_spmm_noalloc.restype = ctypes.c_int
     lib.sylv_strerror.argtypes = [ctypes.c_int]
     lib.sylv_strerror.restype = ctypes.c_char_p
     lib.sylv_last_error.argtypes = []
@@ -252,6 +256,12 @@ def sylv_get_profile(h) -> list:
         raise SylvError(rc, "sylv_get_profile")
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes,
              "flops": arr[i].flops} for i in range(cnt.value)]
+
+
+def sylv_spmm_noalloc(n: int, nnz: int, row_ptr: int, col_idx: int, val: int, X: int, Y: int, k: int,
+                      stream: int = 0) -> int:
+    """Y = A X with device pointers only (integers); allocates nothing.  Returns the status code."""
+    return load().sylv_spmm_noalloc(n, nnz, row_ptr, col_idx, val, X, Y, k, stream or None)
 
 
 def sylv_destroy(h) -> None:

@@ -96,6 +96,10 @@ struct Prof {
 
 }  // namespace
 
+namespace sylv {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sylv
+
 struct sylv_handle {
   sylv_options opt{};
   int64_t s = 0;

@@ -3,9 +3,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace sylv {
+
+// Sets the message returned by sylv_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------- basis side
 // All factor blocks are stored block-row-major: block b is an n x s row-major
