@@ -52,8 +52,8 @@ def peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def workload():
-    p = wl.cfg_convdiff_bicgstab(64, 48, 4, tol=1e-8, maxit=300)
+def workload(maxit: int = 0):
+    p = wl.cfg_convdiff_bicgstab(64, 48, 4, tol=1e-8, maxit=maxit or 300)
     return p
 
 
@@ -249,7 +249,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    p = workload()
+    p = workload(args.maxit)
     stream = torch.cuda.Stream()
     sv = ps.Solver(p.A, p.B, p.C1, p.C2, precision="fp64", profile=True, cuda_stream=stream.cuda_stream)
 
@@ -413,6 +413,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--maxit", type=int, default=0, help="override maxit (a short solve, e.g. for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -62,18 +62,18 @@ typedef struct {
   int32_t precision;   /* sylv_precision */
   int32_t lyapunov;    /* 1: B = A^T and C2 = C1 (Sec. 4.3); pass B = NULL, C2 = NULL */
   int32_t poll_every;  /* iterations enqueued between host polls of the device status (0: 8) */
-  int32_t refine_max;  /* SYLV_MIXED: maximum outer refinement rounds (0: 4) */
+  int32_t refine_max;  /* SYLV_MIXED: maximum outer refinement rounds (0: 8) */
   double deflate_tol;  /* block Krylov exhaustion threshold delta (0: 1e-12 FP64, 1e-6 mixed) */
   double timeout_s;    /* host wait limit per solve (0: 3600 s) */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a stream owned by the handle */
   int32_t profile;     /* 1: time every kernel launch with CUDA events (see sylv_get_profile) */
-  int32_t reserved;
+  int32_t no_true_residual; /* SYLV_FP64 only: 1 skips the float64 true-residual estimate after the solve */
 } sylv_options;
 
 typedef struct {
   int32_t status;       /* sylv_status of the solve */
   int32_t iters;        /* completed iterations k (sum over refinement rounds in SYLV_MIXED) */
-  int64_t matvecs;      /* sparse block products A*V_j (equal count for B^T*W_j) */
+  int64_t matvecs;      /* sparse block products A*V_j (equal count for B^T*W_j), all rounds */
   int64_t width;        /* r: columns of V and W returned; X^ is r x r */
   double rel_res;       /* ||R^_k|| / ||R^_0||, the monitored residual of Algorithms 4.1/4.2 */
   double true_rel_res;  /* ||C1 C2^T - A X - X B||_F / ||C1 C2^T||_F in float64, or -1 if not computed */

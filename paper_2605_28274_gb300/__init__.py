@@ -41,7 +41,8 @@ class sylv_csr(ctypes.Structure):
 class sylv_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("lyapunov", ctypes.c_int32), ("poll_every", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("deflate_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
+                ("no_true_residual", ctypes.c_int32)]
 
 
 class sylv_kernel_stat(ctypes.Structure):

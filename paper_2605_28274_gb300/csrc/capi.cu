@@ -73,10 +73,11 @@ enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2 };
 // Kernel classes timed by the optional profiler.
 enum KClass {
   KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_SCALE, KC_SETUP,
-  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_NUM
+  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_NUM
 };
-const char* const kKcNames[KC_NUM] = {"spmm",   "gram",  "reduce_h",   "update",          "cholqr_chol",
-                                      "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise"};
+const char* const kKcNames[KC_NUM] = {"spmm",         "gram",  "reduce_h",   "update",           "cholqr_chol",
+                                      "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise",
+                                      "true_residual"};
 
 struct Prof {
   struct Rec {
@@ -129,6 +130,19 @@ struct sylv_handle {
   int status = -1;
   int64_t width = 0;
   int nblocks = 0;
+  // float64 true residual (randomised sketch) and mixed-precision refinement
+  Side opAt, opB;                  // CSR of A^T and of B (float64) for R^T Q and R Omega
+  double* C1rm = nullptr;          // C1, C2 row-major float64 (n x s, m x s)
+  double* C2rm = nullptr;
+  double* Om = nullptr;            // two m x 8 Gaussian probe blocks (row-major)
+  double cnorm = -1.0;             // ||C1 C2^T||_F
+  DevState* st_sk = nullptr;       // status word of the sketch's CholQR
+  std::vector<std::pair<void*, size_t>> sk;  // sketch scratch buffers (pointer, bytes)
+  std::vector<sylv_handle*> subs;  // correction solves of the last mixed solve
+  bool is_sub = false;
+  double true_rel = -1.0;
+  int refinements = 0;
+  int64_t total_iters = 0, total_width = 0;
 };
 
 namespace {
@@ -336,7 +350,7 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   TRY(alloc_solve(h, &h->gpart, (size_t)(2 * sms) * maxb * s * s));
   TRY(alloc_solve(h, &h->spart, (size_t)(4 * sms) * 64));
   TRY(alloc_solve(h, &h->Hc, (size_t)maxb * s * s));
-  const int64_t gtiles = (h->lds + 63) / 64;
+  const int64_t gtiles = (h->lds + 31) / 32;
   const size_t psz = std::max<size_t>((size_t)((h->lds + sylv::NT - 1) / sylv::NT) * h->lds, 2 * gtiles * gtiles) + 64;
   TRY(alloc_solve(h, &h->psmall, psz));
   h->maxb = maxb;
@@ -486,7 +500,7 @@ int wait_status(sylv_handle* h, int slot, double deadline) {
 }
 
 template <typename T>
-int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
+int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
   const double t0 = now_s();
   const double deadline = t0 + (h->opt.timeout_s > 0 ? h->opt.timeout_s : 3600.0);
   if (!(tol >= 0.0) || maxit < 0) return fail(SYLV_EINVAL, "tol must be >= 0 and maxit >= 0");
@@ -591,6 +605,385 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   return rc;
 }
 
+
+// ------------------------------------------------------------------ float64 true residual
+// R = C1 C2^T - A X - X B for X = sum over rounds of V_i X^_i W_i^T is applied to thin
+// blocks only, with float64 accumulation:
+//   R Om   = C1 (C2^T Om) - A (X Om) - X (B Om)
+//   R^T Q  = C2 (C1^T Q)  - X^T (A^T Q) - B^T (X^T Q)
+// A rank-8 randomised range finder with one power iteration gives R ~ Q Z^T with Q
+// orthonormal; ||R||_F^2 = ||Z||_F^2 + ||(I - Q Q^T) R||_F^2, the second term from a
+// second Gaussian probe block (unbiased).  Q, Z are also the right-hand side factors of
+// the next refinement round.
+
+double* sk_buf(sylv_handle* h, size_t idx, size_t bytes, int* rc) {
+  if (h->sk.size() <= idx) h->sk.resize(idx + 1, {nullptr, 0});
+  auto& b = h->sk[idx];
+  if (b.second < bytes) {
+    if (b.first) cudaFree(b.first);
+    b.first = nullptr;
+    b.second = 0;
+    cudaError_t e = cudaMalloc(&b.first, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *rc = fail(e == cudaErrorMemoryAllocation ? SYLV_ENOMEM : SYLV_ECUDA, "sketch buffer");
+      return nullptr;
+    }
+    b.second = bytes;
+  }
+  return (double*)b.first;
+}
+
+void free_sketch(sylv_handle* h) {
+  for (auto& b : h->sk)
+    if (b.first) cudaFree(b.first);
+  h->sk.clear();
+}
+
+void free_subs(sylv_handle* h);
+
+int prepare_residual_ops(sylv_handle* h, const sylv_csr* A, const sylv_csr* B) {
+  TRY(upload_operator(h, h->opAt, A, true));
+  if (h->lyap)
+    h->opB = h->opAt;  // B = A^T
+  else
+    TRY(upload_operator(h, h->opB, B, false));
+  const int s = (int)h->s;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  TRY(alloc_fixed(h, &h->C1rm, n * s));
+  TRY(alloc_fixed(h, &h->C2rm, m * s));
+  sylv::launch_pack<double>(h->stream, n, s, h->side[0].C, h->C1rm);
+  sylv::launch_pack<double>(h->stream, m, s, h->lyap ? h->side[0].C : h->side[1].C, h->C2rm);
+  // Gaussian probes: SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller, fixed seed
+  std::vector<double> om((size_t)m * 16);
+  uint64_t state = 0x5eedc0de12345678ull;
+  auto next = [&state]() {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (size_t i = 0; i < om.size(); i += 2) {
+    const double u1 = ((double)(next() >> 11) + 1.0) * 0x1.0p-53, u2 = (double)(next() >> 11) * 0x1.0p-53;
+    const double rr = std::sqrt(-2.0 * std::log(u1));
+    om[i] = rr * std::cos(6.283185307179586 * u2);
+    if (i + 1 < om.size()) om[i + 1] = rr * std::sin(6.283185307179586 * u2);
+  }
+  TRY(alloc_fixed(h, &h->Om, om.size()));
+  CU(cudaMemcpyAsync(h->Om, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  TRY(alloc_fixed(h, &h->st_sk, 1));
+  CU(cudaStreamSynchronize(h->stream));
+  return SYLV_OK;
+}
+
+struct RoundView {
+  const void* V;
+  const void* W;
+  int64_t bsV, bsW;
+  int s, nb;
+  const double* Xh;
+  int64_t lds;
+};
+
+std::vector<RoundView> round_views(const sylv_handle* h) {
+  std::vector<RoundView> out;
+  auto add = [&out](const sylv_handle* x) {
+    if (x->width <= 0) return;
+    const Side& a = x->side[0];
+    const Side& b = x->side[x->lyap ? 0 : 1];
+    out.push_back({a.V, b.V, a.n * x->s, b.n * x->s, (int)x->s, (int)(x->width / x->s), x->Xh, x->lds});
+  };
+  add(h);
+  for (const sylv_handle* sb : h->subs) add(sb);
+  return out;
+}
+
+constexpr int SKK = 8;  // columns of the sketch blocks
+
+// Yout (rows x 8) = X Min (trans = false; Min is m x 8) or X^T Min (trans = true; Min is n x 8).
+template <typename T>
+int apply_X(sylv_handle* h, bool trans, const double* Min, double* Yout) {
+  int rc = SYLV_OK;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
+  auto views = round_views(h);
+  int maxw = 1;
+  for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
+  const int max_rc = 32;
+  double* P = sk_buf(h, 0, (size_t)maxw * SKK * sizeof(double), &rc);
+  double* P2 = sk_buf(h, 1, (size_t)maxw * SKK * sizeof(double), &rc);
+  double* part = sk_buf(h, 2, (size_t)max_rc * maxw * SKK * sizeof(double), &rc);
+  if (rc) return rc;
+  bool first = true;
+  for (auto& v : views) {
+    const T* Uin = (const T*)(trans ? v.V : v.W);
+    const T* Uout = (const T*)(trans ? v.W : v.V);
+    const int64_t bsin = trans ? v.bsV : v.bsW, bsout = trans ? v.bsW : v.bsV;
+    const int r = v.nb * v.s;
+    sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, SKK, part, max_rc, P);
+    sylv::launch_small_apply(h->stream, r, SKK, v.Xh, v.lds, trans, P, P2);
+    sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, SKK, 1.0, first ? 0.0 : 1.0, Yout);
+    h->launches += 4;
+    first = false;
+  }
+  if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * SKK * sizeof(double), h->stream));
+  return SYLV_OK;
+}
+
+// Y (n x 8) = R Om (Om m x 8)
+template <typename T>
+int sketch_R(sylv_handle* h, const double* Om, double* Y) {
+  int rc = SYLV_OK;
+  const int s = (int)h->s;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  double* G = sk_buf(h, 3, 64 * SKK * sizeof(double), &rc);
+  double* part = sk_buf(h, 4, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  double* Tm = sk_buf(h, 5, (size_t)m * SKK * sizeof(double), &rc);
+  double* Xa = sk_buf(h, 6, (size_t)n * SKK * sizeof(double), &rc);
+  double* Xb = sk_buf(h, 7, (size_t)n * SKK * sizeof(double), &rc);
+  if (rc) return rc;
+  const Side& Aop = h->side[0];
+  sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, Om, SKK, part, 32, G);       // C2^T Om
+  sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, h->opB.rp, h->opB.ci, h->opB.vald, Om, Tm, nullptr,
+                            nullptr, 0);                                                     // B Om
+  TRY(apply_X<T>(h, false, Om, Xa));                                                         // X Om
+  TRY(apply_X<T>(h, false, Tm, Xb));                                                         // X B Om
+  sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, Aop.rp, Aop.ci, Aop.vald, Xa, Y, nullptr, nullptr, 0);
+  sylv::launch_neg_sum(h->stream, n * SKK, Y, Xb, Y);                                        // -(A X Om + X B Om)
+  sylv::launch_lowrank_axpy(h->stream, n, s, SKK, h->C1rm, G, 1.0, Y);                       // + C1 (C2^T Om)
+  h->launches += 6;
+  return SYLV_OK;
+}
+
+// Z (m x 8) = R^T Q (Q n x 8)
+template <typename T>
+int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
+  int rc = SYLV_OK;
+  const int s = (int)h->s;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  double* G = sk_buf(h, 3, 64 * SKK * sizeof(double), &rc);
+  double* part = sk_buf(h, 4, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  double* Tn = sk_buf(h, 8, (size_t)n * SKK * sizeof(double), &rc);
+  double* Za = sk_buf(h, 9, (size_t)m * SKK * sizeof(double), &rc);
+  double* Zb = sk_buf(h, 10, (size_t)m * SKK * sizeof(double), &rc);
+  if (rc) return rc;
+  const Side& Bt = h->side[h->lyap ? 0 : 1];  // B^T
+  sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, Q, SKK, part, 32, G);        // C1^T Q
+  sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, h->opAt.rp, h->opAt.ci, h->opAt.vald, Q, Tn, nullptr,
+                            nullptr, 0);                                                     // A^T Q
+  TRY(apply_X<T>(h, true, Tn, Za));                                                          // X^T A^T Q
+  TRY(apply_X<T>(h, true, Q, Zb));                                                           // X^T Q
+  sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, Bt.rp, Bt.ci, Bt.vald, Zb, Z, nullptr, nullptr, 0);
+  sylv::launch_neg_sum(h->stream, m * SKK, Z, Za, Z);
+  sylv::launch_lowrank_axpy(h->stream, m, s, SKK, h->C2rm, G, 1.0, Z);
+  h->launches += 6;
+  return SYLV_OK;
+}
+
+// In-place CholQR2 of an n x 8 float64 block (status in st_sk).
+void qr8(sylv_handle* h, int64_t n, double* Y, double* Rout) {
+  double* R1 = Rout + 64;
+  double* Rinv = Rout + 128;
+  double* RinvT = Rout + 192;
+  sylv::CholArgs a{};
+  a.side = 0;
+  a.s = SKK;
+  a.delta = 1e-10;
+  a.R1 = R1;
+  a.Rinv = Rinv;
+  a.RinvT = RinvT;
+  a.factor_is_float = 0;
+  a.setup = 1;
+  a.pass = 1;
+  int nc = sylv::launch_selfgram<double>(h->stream, h->st_sk, n, SKK, Y, h->spart);
+  sylv::launch_chol(h->stream, h->st_sk, h->spart, nc, a);
+  nc = sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, h->spart);
+  a.pass = 2;
+  a.Rout = Rout;
+  sylv::launch_chol(h->stream, h->st_sk, h->spart, nc, a);
+  sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, nullptr);
+  h->launches += 5;
+}
+
+// ||R||_F estimate; leaves Q (n x 8, buffer 11) and Z (m x 8, buffer 12) with R ~ Q Z^T.
+template <typename T>
+int sketch(sylv_handle* h, double* est, bool* ok) {
+  int rc = SYLV_OK;
+  const int s = (int)h->s;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  double* Q = sk_buf(h, 11, (size_t)n * SKK * sizeof(double), &rc);
+  double* Z = sk_buf(h, 12, (size_t)m * SKK * sizeof(double), &rc);
+  double* Y3 = sk_buf(h, 13, (size_t)n * SKK * sizeof(double), &rc);
+  double* Rk = sk_buf(h, 14, 256 * sizeof(double), &rc);
+  double* sums = sk_buf(h, 15, 8 * sizeof(double), &rc);
+  double* part = sk_buf(h, 16, (size_t)256 * sizeof(double) + 64, &rc);
+  double* P = sk_buf(h, 17, 64 * sizeof(double), &rc);
+  double* part2 = sk_buf(h, 18, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  if (rc) return rc;
+  unsigned int* ticket = (unsigned int*)(part + 256);
+  CU(cudaMemsetAsync(h->st_sk, 0, sizeof(DevState), h->stream));
+  CU(cudaMemsetAsync(ticket, 0, 16, h->stream));
+  if (h->cnorm < 0) {
+    // ||C1 C2^T||_F^2 = tr((C1^T C1)(C2^T C2))
+    double* G1 = sk_buf(h, 19, 128 * sizeof(double), &rc);
+    if (rc) return rc;
+    sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, h->C1rm, s, part2, 32, G1);
+    sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, h->C2rm, s, part2, 32, G1 + 64);
+    sylv::launch_trace_prod(h->stream, s, G1, G1 + 64, sums + 2);
+    h->launches += 5;
+  }
+  const double* Om1 = h->Om;
+  const double* Om2 = h->Om + m * SKK;
+  TRY(sketch_R<T>(h, Om1, Q));  // Y = R Om1
+  qr8(h, n, Q, Rk);
+  TRY(sketch_Rt<T>(h, Q, Z));   // Z1 = R^T Q1
+  TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1
+  qr8(h, n, Q, Rk);
+  TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
+  TRY(sketch_R<T>(h, Om2, Y3)); // tail probe
+  sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 32, P);
+  sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Y3);
+  sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
+  sylv::launch_sumsq(h->stream, n * SKK, Y3, part, ticket + 1, sums + 1);
+  h->launches += 6;
+  double hs[3] = {0, 0, 0};
+  CU(cudaMemcpyAsync(hs, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DevState dst;
+  CU(cudaMemcpyAsync(&dst, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (h->cnorm < 0) h->cnorm = std::sqrt(std::max(0.0, hs[2]));
+  *ok = dst.status == sylv::ST_RUNNING;
+  // with a rank-deficient sketch (R of rank < 8) the probe estimate alone is used
+  *est = *ok ? std::sqrt(hs[0] + hs[1] / SKK) : std::sqrt(hs[1] / SKK);
+  return SYLV_OK;
+}
+
+// A correction solve A dX + dX B = Q Z^T on the same operators (s = 8).
+int make_sub(sylv_handle* P, sylv_handle** out) {
+  *out = nullptr;
+  sylv_handle* h = new sylv_handle();
+  h->is_sub = true;
+  h->opt = P->opt;
+  h->s = SKK;
+  h->lyap = false;
+  h->mixed = P->mixed;
+  h->stream = P->stream;
+  h->own_stream = false;
+  auto bail = [&](int rc) {
+    std::string msg = g_err;
+    sylv_destroy(h);
+    g_err = msg;
+    return rc;
+  };
+  if (cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(SYLV_ECUDA, "event"));
+  if (cudaMallocHost(&h->st_host, 2 * sizeof(DevState)) != cudaSuccess) return bail(fail(SYLV_ECUDA, "pinned status"));
+  int rc = alloc_fixed(h, &h->st, 1);
+  if (rc) return bail(rc);
+  const Side* src[2] = {&P->side[0], &P->side[P->lyap ? 0 : 1]};
+  const int64_t n = P->side[0].n;
+  const int64_t m = P->lyap ? n : P->side[1].n;
+  double* rhs[2] = {(double*)P->sk[11].first, (double*)P->sk[12].first};  // Q (n x 8), Z (m x 8), row-major
+  for (int i = 0; i < 2; ++i) {
+    Side& sd = h->side[i];
+    sd.n = src[i]->n;
+    sd.nnz = src[i]->nnz;
+    sd.rp = src[i]->rp;
+    sd.ci = src[i]->ci;
+    sd.vald = src[i]->vald;
+    sd.valf = src[i]->valf;
+    const int64_t rows = i == 0 ? n : m;
+    if ((rc = alloc_fixed(h, &sd.C, rows * SKK))) return bail(rc);
+    sylv::launch_unpack<double>(h->stream, rows, SKK, 1, rhs[i], rows * SKK, sd.C);
+    if ((rc = alloc_fixed(h, &sd.RQR, 64)) || (rc = alloc_fixed(h, &sd.R1, 64)) || (rc = alloc_fixed(h, &sd.Rinv, 64)) ||
+        (rc = alloc_fixed(h, (double**)&sd.RinvT, 64)))
+      return bail(rc);
+  }
+  *out = h;
+  return SYLV_OK;
+}
+
+void prof_add(sylv_handle* dst, const sylv_handle* src) {
+  for (int i = 0; i < KC_NUM; ++i) {
+    dst->prof.launches[i] += src->prof.launches[i];
+    dst->prof.ms[i] += src->prof.ms[i];
+    dst->prof.bytes[i] += src->prof.bytes[i];
+    dst->prof.flops[i] += src->prof.flops[i];
+  }
+}
+
+// Outer driver: the factorized solve, then (unless disabled) the float64 true residual;
+// in the mixed mode, refinement rounds A dX + dX B = (rank-8 part of R) until the true
+// residual meets tol.
+template <typename T>
+int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
+  const double t0 = now_s();
+  free_subs(h);
+  h->true_rel = -1.0;
+  h->refinements = 0;
+  int rc = run_inner<T>(h, method, tol, maxit, info);
+  h->total_iters = h->iters;
+  h->total_width = h->width;
+  const bool check = !h->is_sub && (h->mixed || !h->opt.no_true_residual) && h->C1rm != nullptr;
+  if (check && (rc == SYLV_OK || rc == SYLV_ENOTCONV) && h->width > 0) {
+    const int refine_max = h->opt.refine_max > 0 ? h->opt.refine_max : 8;
+    const double tol_c = 0.05;  // a correction only has to beat the rank-8 truncation of R
+    for (int round = 0;; ++round) {
+      double est = 0.0;
+      bool ok = false;
+      cudaEvent_t pa = prof_begin(h);
+      TRY(sketch<T>(h, &est, &ok));
+      if (pa) {
+        cudaEvent_t pb = prof_event(h);
+        if (pb) {
+          cudaEventRecord(pb, h->stream);
+          cudaEventSynchronize(pb);
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, pa, pb) == cudaSuccess) {
+            h->prof.launches[KC_RESID] += 1;
+            h->prof.ms[KC_RESID] += ms;
+          }
+        }
+      }
+      h->true_rel = h->cnorm > 0 ? est / h->cnorm : 0.0;
+      if (!h->mixed) break;
+      if (h->true_rel <= tol) {
+        rc = SYLV_OK;
+        break;
+      }
+      rc = SYLV_ENOTCONV;
+      if (!ok || round >= refine_max) break;
+      sylv_handle* sub = nullptr;
+      TRY(make_sub(h, &sub));
+      h->subs.push_back(sub);
+      sylv_info si;
+      const int src = run_inner<T>(sub, method, tol_c, maxit, &si);
+      prof_add(h, sub);
+      h->launches += sub->launches;
+      h->total_iters += sub->iters;
+      h->total_width += sub->width;
+      if (info) info->matvecs += (int64_t)(method == M_CG ? sub->iters : 2 * sub->iters);
+      h->refinements += 1;
+      if (src != SYLV_OK && src != SYLV_ENOTCONV) {
+        rc = src;
+        break;
+      }
+    }
+  }
+  h->status = rc;
+  if (info) {
+    info->status = rc;
+    info->iters = (int32_t)h->total_iters;
+    info->width = h->total_width;
+    info->true_rel_res = h->true_rel;
+    info->refinements = h->refinements;
+    info->solve_ms = (now_s() - t0) * 1e3;
+    info->kernel_launches = h->launches;
+  }
+  return rc;
+}
+
 int solve(sylv_handle* h, int method, double tol, int32_t maxit, sylv_info* info) {
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
   if (info) std::memset(info, 0, sizeof(*info));
@@ -619,6 +1012,13 @@ int unpack_to_host(sylv_handle* h, const Side& sd, int nb, double* out) {
 
 }  // namespace
 
+namespace {
+void free_subs(sylv_handle* h) {
+  for (sylv_handle* sb : h->subs) sylv_destroy(sb);
+  h->subs.clear();
+}
+}  // namespace
+
 extern "C" {
 
 void sylv_default_options(sylv_options* opt) {
@@ -626,7 +1026,7 @@ void sylv_default_options(sylv_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = SYLV_FP64;
   opt->poll_every = 8;
-  opt->refine_max = 4;
+  opt->refine_max = 8;
   opt->timeout_s = 3600.0;
 }
 
@@ -682,6 +1082,7 @@ int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const do
   if (!rc) rc = upload_rhs(h, h->side[0], C1);
   if (!rc && !lyap) rc = upload_operator(h, h->side[1], B, true);
   if (!rc && !lyap) rc = upload_rhs(h, h->side[1], C2);
+  if (!rc && (h->mixed || !o.no_true_residual)) rc = prepare_residual_ops(h, A, B);
   if (rc) return bail(rc);
   *out = h;
   return SYLV_OK;
@@ -700,19 +1101,30 @@ int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
 int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t* r) {
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
   if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
-  if (r) *r = h->width;
-  const int s = (int)h->s;
-  const int nb = (int)(h->width / s);
-  if (Xhat && h->width > 0) {
-    CU(cudaMemcpy2DAsync(Xhat, h->width * sizeof(double), h->Xh, h->lds * sizeof(double), h->width * sizeof(double),
-                         h->width, cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-  }
-  for (int i = 0; i < 2; ++i) {
-    double* dst = i == 0 ? V : W;
-    if (!dst || nb == 0) continue;
-    const Side& sd = h->side[(i == 1 && !h->lyap) ? 1 : 0];
-    TRY(h->mixed ? unpack_to_host<float>(h, sd, nb, dst) : unpack_to_host<double>(h, sd, nb, dst));
+  const int64_t R = h->total_width;
+  if (r) *r = R;
+  if (R == 0) return SYLV_OK;
+  std::vector<sylv_handle*> rounds{h};
+  for (sylv_handle* sb : h->subs) rounds.push_back(sb);
+  if (Xhat) std::memset(Xhat, 0, (size_t)R * R * sizeof(double));  // block diagonal over the rounds
+  int64_t off = 0;
+  for (sylv_handle* x : rounds) {
+    const int64_t w = x->width;
+    if (w == 0) continue;
+    const int nb = (int)(w / x->s);
+    if (Xhat) {
+      CU(cudaMemcpy2DAsync(Xhat + off + off * R, R * sizeof(double), x->Xh, x->lds * sizeof(double),
+                           w * sizeof(double), w, cudaMemcpyDeviceToHost, x->stream));
+      CU(cudaStreamSynchronize(x->stream));
+    }
+    for (int i = 0; i < 2; ++i) {
+      double* dst = i == 0 ? V : W;
+      if (!dst) continue;
+      const Side& sd = x->side[(i == 1 && !x->lyap) ? 1 : 0];
+      double* at = dst + off * sd.n;
+      TRY(x->mixed ? unpack_to_host<float>(x, sd, nb, at) : unpack_to_host<double>(x, sd, nb, at));
+    }
+    off += w;
   }
   return SYLV_OK;
 }
@@ -825,6 +1237,8 @@ const char* sylv_last_error(void) { return g_err.c_str(); }
 void sylv_destroy(sylv_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  free_subs(h);
+  free_sketch(h);
   free_solve(h);
   for (void* p : h->fixed_allocs) cudaFree(p);
   h->fixed_allocs.clear();

@@ -113,4 +113,27 @@ void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);
 void launch_bicg_update(cudaStream_t, const SmallCtx&, int k, int rp, int rpp);
 void launch_bicg_p(cudaStream_t, const SmallCtx&, int rpp);
 
+// ---------------------------------------------------------------- true residual (float64 accumulation)
+// P (nb*su x k, row-major) = U^T Y with U in block-row-major storage (nb blocks of width su,
+// element TU) and Y n x k row-major float64, k <= 16.  partial: scratch of max_rc * nb*su*k.
+template <typename TU>
+void launch_tsg(cudaStream_t, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* Y, int k,
+                double* partial, int max_rc, double* P);
+// Z = beta Z + alpha U M  (U as above, M nb*su x k row-major, Z n x k row-major).
+template <typename TU>
+void launch_tsu(cudaStream_t, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* M, int k,
+                double alpha, double beta, double* Z);
+// out (r x k row-major) = op(Xh) in, op = Xh or Xh^T (Xh column-major, ld lds).
+void launch_small_apply(cudaStream_t, int r, int k, const double* Xh, int64_t lds, bool trans, const double* in,
+                        double* out);
+// Y = alpha Y + C G (C n x s row-major, G s x k row-major, Y n x k row-major).
+void launch_lowrank_axpy(cudaStream_t, int64_t n, int s, int k, const double* C, const double* G, double alpha,
+                         double* Y);
+// out = -(X1 + X2) element-wise.
+void launch_neg_sum(cudaStream_t, int64_t count, const double* X1, const double* X2, double* out);
+// out[0] = sum of squares of x (deterministic; ticket must be zero).
+void launch_sumsq(cudaStream_t, int64_t count, const double* x, double* partials, unsigned int* ticket, double* out);
+// out[0] = trace(G1 G2) for s x s matrices.
+void launch_trace_prod(cudaStream_t, int s, const double* G1, const double* G2, double* out);
+
 }  // namespace sylv

@@ -152,7 +152,27 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
     for (int u = 0; u < S; ++u)
 #pragma unroll
       for (int t = 0; t < S; ++t) acc[u][t] = 0;
-    for (int64_t row = r0 + (int64_t)sl * 32 + l; row < r1; row += 32 * slices) {
+    // UNR independent rows per lane in flight (more bytes in flight per warp for the
+    // HBM-bound FP32 case; bounded so the S x S accumulators stay in registers)
+    constexpr int RB = S * (int)sizeof(T);
+    constexpr int UNR = RB <= 16 ? 4 : (RB <= 32 ? 2 : 1);
+    const int64_t step = 32 * (int64_t)slices;
+    int64_t row = r0 + (int64_t)sl * 32 + l;
+    for (; row + (UNR - 1) * step < r1; row += UNR * step) {
+      T v[UNR][S], y[UNR][S];
+#pragma unroll
+      for (int q = 0; q < UNR; ++q) {
+        ld_row_ro<T, S>(Vb + (row + q * step) * S, v[q]);
+        ld_row<T, S>(Y + (row + q * step) * S, y[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < UNR; ++q)
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+          for (int t = 0; t < S; ++t) acc[u][t] += (A)v[q][u] * (A)y[q][t];
+    }
+    for (; row < r1; row += step) {
       T v[S], y[S];
       ld_row_ro<T, S>(Vb + row * S, v);
       ld_row<T, S>(Y + row * S, y);
@@ -236,6 +256,7 @@ __global__ void __launch_bounds__(NT) update_kernel(const DevState* st, int64_t 
       for (int e = threadIdx.x; e < cb * S * S; e += NT) hs[e] = (T)Hc[(int64_t)b0 * S * S + e];
       __syncthreads();
       if (row < n) {
+#pragma unroll 4
         for (int b = 0; b < cb; ++b) {
           T v[S];
           ld_row_ro<T, S>(V + (int64_t)(b0 + b) * bstride + row * S, v);
@@ -328,14 +349,24 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
                                                   CholArgs a) {
   if (stopped(st)) return;
   __shared__ double G[64], R[64], Ri[64], sh[32];
-  __shared__ double nu2_sh;
-  __shared__ int exh_sh;
+  __shared__ double gsum[NT];
   const int s = a.s, E = s * s;
-  for (int e = 0; e < E; ++e) {
+  {
+    // thread -> (entry e, group g); each group sums a strided subset of the CTA
+    // partials, then the groups are added in a fixed order (deterministic)
+    const int groups = NT / E;
+    const int e = threadIdx.x % E, g = threadIdx.x / E;
     double v = 0.0;
-    for (int c = threadIdx.x; c < ncta; c += NT) v += partial[(int64_t)c * E + e];
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0) G[e] = v;
+    if (g < groups)
+      for (int c = g; c < ncta; c += groups) v += partial[(int64_t)c * E + e];
+    gsum[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < E) {
+      double t = 0.0;
+      for (int q = 0; q < groups; ++q) t += gsum[q * E + threadIdx.x];
+      G[threadIdx.x] = t;
+    }
+    __syncthreads();
   }
   double hsq = 0.0;
   if (a.pass == 1 && a.Hcol != nullptr) {
@@ -353,7 +384,6 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
     for (int e = 0; e < E; ++e) finite = finite && isfinite(G[e]);
     for (int u = 0; u < s; ++u) tr += G[u * s + u];
     const double nu2 = hsq + tr;
-    nu2_sh = nu2;
     int exh = (a.pass == 2) ? st->exhausted[a.side] : 0;
     int bad = 0;
     if (!finite || !isfinite(hsq)) {
@@ -395,7 +425,6 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
         }
       }
     }
-    exh_sh = exh;
     if (!bad) {
       for (int e = 0; e < E; ++e) {
         a.Rinv[e] = Ri[e];
@@ -473,7 +502,10 @@ void launch_spmm(cudaStream_t strm, const DevState* st, int64_t n, int s, const 
 template <typename T>
 int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T* V, int64_t bstride, int nb,
                 const T* Y, double* partial) {
-  const int grid = grid_for(n, 64, 2 * num_sms());
+  // FP64 is bound by the FP64 pipe: one CTA per SM keeps the per-task warp
+  // reductions (s*s shuffle+add steps) small next to the row loop.  FP32 is bound
+  // by HBM: two CTAs per SM for more loads in flight.
+  const int grid = grid_for(n, 64, (sizeof(T) == 8 ? 1 : 2) * num_sms());
   const int64_t rpc = (n + grid - 1) / grid;
 #define CASE(SV) \
   case SV: gram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, partial); break;

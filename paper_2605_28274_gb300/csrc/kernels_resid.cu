@@ -1,0 +1,221 @@
+// Float64 tall-skinny products for the true residual R = C1 C2^T - A X - X B of a
+// factored iterate X = sum_i V_i X^_i W_i^T (the residual the convergence test
+// of Algorithms 4.1/4.2 stands in for, eq. 3.6), and for the outer refinement of
+// the mixed-precision mode.
+//
+// R is only ever applied to thin blocks (k <= 16 columns): R Omega and R^T Q.
+// Those products cancel to ~1e-8 of their terms near convergence, so every
+// product here accumulates in float64, whatever the precision the basis blocks
+// U are stored in (float or double).  Blocks of k vectors are n x k row-major.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sylv {
+
+namespace {
+
+constexpr int TS_ROWS = 64;   // rows of Y staged in shared memory per tile
+constexpr int TS_COLS = NT;   // basis columns per CTA (one per thread)
+
+// partial[rc][col][t] = sum over the rows of row-chunk rc of U[col][row] * Y[row][t]
+// U: nb blocks of width su (block-row-major, element TU), Y: n x k row-major float64.
+template <typename TU>
+__global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const TU* __restrict__ U, int64_t bstride,
+                                                 int su, int ncol, const double* __restrict__ Y, int k,
+                                                 double* __restrict__ partial) {
+  __shared__ double ys[TS_ROWS * 16];
+  const int col = blockIdx.y * TS_COLS + threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = min(n, r0 + rpc);
+  double acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  const bool active = col < ncol;
+  const int b = active ? col / su : 0, u = active ? col - b * su : 0;
+  const TU* Ub = U + (int64_t)b * bstride + u;
+  for (int64_t base = r0; base < r1; base += TS_ROWS) {
+    const int rows = (int)((r1 - base) < TS_ROWS ? (r1 - base) : TS_ROWS);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * k; e += NT) ys[e] = Y[base * k + e];
+    __syncthreads();
+    if (active) {
+      for (int i = 0; i < rows; ++i) {
+        const double uv = (double)Ub[(base + i) * su];
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t < k) acc[t] += uv * ys[i * k + t];
+      }
+    }
+  }
+  if (active) {
+    double* out = partial + ((int64_t)blockIdx.x * ncol + col) * k;
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (t < k) out[t] = acc[t];
+  }
+}
+
+__global__ void tsg_reduce_kernel(const double* __restrict__ partial, int nrc, int64_t E, double* __restrict__ P) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= E) return;
+  double v = 0.0;
+  for (int c = 0; c < nrc; ++c) v += partial[(int64_t)c * E + e];
+  P[e] = v;
+}
+
+// Z[row][t] = beta * Z[row][t] + alpha * sum_col U[col][row] M[col][t]   (M: ncol x k row-major)
+template <typename TU>
+__global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict__ U, int64_t bstride, int su,
+                                                 int ncol, const double* __restrict__ M, int k, double alpha,
+                                                 double beta, double* __restrict__ Z) {
+  __shared__ double ms[64 * 16];
+  const int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int c0 = 0; c0 < ncol; c0 += 64) {
+    const int cc = min(64, ncol - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cc * k; e += NT) ms[e] = M[(int64_t)c0 * k + e];
+    __syncthreads();
+    if (row < n) {
+      for (int c = 0; c < cc; ++c) {
+        const int col = c0 + c, b = col / su, u = col - b * su;
+        const double uv = (double)U[(int64_t)b * bstride + row * su + u];
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t < k) acc[t] += uv * ms[c * k + t];
+      }
+    }
+  }
+  if (row < n) {
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (t < k) {
+        double* z = Z + row * k + t;
+        *z = (beta == 0.0 ? 0.0 : beta * *z) + alpha * acc[t];
+      }
+  }
+}
+
+// out (r x k, row-major) = op(Xh) * in (r x k row-major), op = identity or transpose; Xh ld lds.
+__global__ void small_apply_kernel(int r, int k, const double* __restrict__ Xh, int64_t lds, int trans,
+                                   const double* __restrict__ in, double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= (int64_t)r * k) return;
+  const int i = (int)(e / k), t = (int)(e - (int64_t)i * k);
+  double acc = 0.0;
+  if (!trans)
+    for (int c = 0; c < r; ++c) acc += Xh[i + (int64_t)c * lds] * in[(int64_t)c * k + t];
+  else
+    for (int c = 0; c < r; ++c) acc += Xh[c + (int64_t)i * lds] * in[(int64_t)c * k + t];
+  out[e] = acc;
+}
+
+// Y (n x k row-major) = alpha * Y + C (n x s row-major) * G (s x k row-major)
+__global__ void lowrank_axpy_kernel(int64_t n, int s, int k, const double* __restrict__ C,
+                                    const double* __restrict__ G, double alpha, double* __restrict__ Y) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= n * k) return;
+  const int64_t row = e / k;
+  const int t = (int)(e - row * k);
+  double acc = 0.0;
+  for (int c = 0; c < s; ++c) acc += C[row * s + c] * G[c * k + t];
+  Y[e] = alpha * Y[e] + acc;
+}
+
+// out = -(X1 + X2), element-wise
+__global__ void neg_sum_kernel(int64_t count, const double* __restrict__ X1, const double* __restrict__ X2,
+                               double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e < count) out[e] = -(X1[e] + X2[e]);
+}
+
+// sum of squares of x[0..count) -> partial per CTA (deterministic), then out[0] by the last CTA
+__global__ void sumsq_kernel(int64_t count, const double* __restrict__ x, double* __restrict__ partials,
+                             unsigned int* ticket, double* __restrict__ out) {
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  double v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < count; i += (int64_t)gridDim.x * NT) v += x[i] * x[i];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  if (last_cta(ticket, &last_sh) && threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(partials + i);
+    *out = t;
+  }
+}
+
+// out = trace(G1 G2) for symmetric s x s G1, G2 (row-major): ||C1 C2^T||_F^2 from the two Grams.
+__global__ void trace_prod_kernel(int s, const double* __restrict__ G1, const double* __restrict__ G2,
+                                  double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < s; ++i)
+    for (int j = 0; j < s; ++j) t += G1[i * s + j] * G2[j * s + i];
+  *out = t;
+}
+
+}  // namespace
+
+template <typename TU>
+void launch_tsg(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* Y, int k,
+                double* partial, int max_rc, double* P) {
+  const int ncol = nb * su;
+  if (ncol == 0) return;
+  int rc = (int)std::min<int64_t>(max_rc, std::max<int64_t>(1, (n + 1023) / 1024));
+  const int64_t rpc = (n + rc - 1) / rc;
+  rc = (int)((n + rpc - 1) / rpc);
+  const dim3 g((unsigned)rc, (unsigned)((ncol + TS_COLS - 1) / TS_COLS));
+  tsg_kernel<TU><<<g, NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, partial);
+  const int64_t E = (int64_t)ncol * k;
+  tsg_reduce_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(partial, rc, E, P);
+}
+
+template <typename TU>
+void launch_tsu(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* M, int k,
+                double alpha, double beta, double* Z) {
+  const int ncol = nb * su;  // ncol = 0: Z = beta Z
+  if (n == 0) return;
+  tsu_kernel<TU><<<(unsigned)((n + NT - 1) / NT), NT, 0, strm>>>(n, U, bstride, su, ncol, M, k, alpha, beta, Z);
+}
+
+void launch_small_apply(cudaStream_t strm, int r, int k, const double* Xh, int64_t lds, bool trans, const double* in,
+                        double* out) {
+  const int64_t E = (int64_t)r * k;
+  if (E == 0) return;
+  small_apply_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(r, k, Xh, lds, trans ? 1 : 0, in, out);
+}
+
+void launch_lowrank_axpy(cudaStream_t strm, int64_t n, int s, int k, const double* C, const double* G, double alpha,
+                         double* Y) {
+  lowrank_axpy_kernel<<<(unsigned)((n * k + NT - 1) / NT), NT, 0, strm>>>(n, s, k, C, G, alpha, Y);
+}
+
+void launch_neg_sum(cudaStream_t strm, int64_t count, const double* X1, const double* X2, double* out) {
+  if (count == 0) return;
+  neg_sum_kernel<<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, X1, X2, out);
+}
+
+void launch_sumsq(cudaStream_t strm, int64_t count, const double* x, double* partials, unsigned int* ticket,
+                  double* out) {
+  const int grid = (int)std::min<int64_t>(256, std::max<int64_t>(1, (count + NT - 1) / NT));
+  sumsq_kernel<<<grid, NT, 0, strm>>>(count, x, partials, ticket, out);
+}
+
+void launch_trace_prod(cudaStream_t strm, int s, const double* G1, const double* G2, double* out) {
+  trace_prod_kernel<<<1, 32, 0, strm>>>(s, G1, G2, out);
+}
+
+template void launch_tsg<float>(cudaStream_t, int64_t, const float*, int64_t, int, int, const double*, int, double*,
+                                int, double*);
+template void launch_tsg<double>(cudaStream_t, int64_t, const double*, int64_t, int, int, const double*, int, double*,
+                                 int, double*);
+template void launch_tsu<float>(cudaStream_t, int64_t, const float*, int64_t, int, int, const double*, int, double,
+                                double, double*);
+template void launch_tsu<double>(cudaStream_t, int64_t, const double*, int64_t, int, int, const double*, int, double,
+                                 double, double*);
+
+}  // namespace sylv

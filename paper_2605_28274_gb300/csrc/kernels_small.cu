@@ -162,11 +162,13 @@ __global__ void __launch_bounds__(NT) cg_p_kernel(const DevState* st, int rp, do
 
 // ---------------------------------------------------------------- BiCGSTAB: dense factored operator
 // Out = [H Z, 0] + [Z G^T; 0] for Z with extent r (H, G block upper Hessenberg,
-// (r+s) x r).  64 x 64 output tiles, 16-deep k-slices in shared memory, 4 x 4
+// (r+s) x r).  32 x 32 output tiles, 32-deep k-slices in shared memory, 2 x 2
 // outputs per thread; k-slices left of the Hessenberg band of a tile are skipped.
+// The skipping makes tiles unequal (the top-left tile does the most work), so the
+// tiles are small enough that the block scheduler keeps every SM busy.
 // With OMEGA, the tile also reduces <Out(1:r,1:r), Z> and <Out, Out> and the last
 // CTA sets omega (Algorithm 4.2).
-constexpr int GBM = 64, GBK = 16;
+constexpr int GBM = 32, GBK = 32;
 
 template <bool OMEGA>
 __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int s, const double* __restrict__ H,
@@ -181,11 +183,7 @@ __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int 
   const int rp = r + s;
   const int a0 = blockIdx.x * GBM, b0 = blockIdx.y * GBM;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 
   // term 1: (H Z)[a][b] for b < r
   if (b0 < r) {
@@ -200,17 +198,14 @@ __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int 
         Bs[kk2][bb] = (c2 < r && b < r) ? Z[c2 + (int64_t)b * lds] : 0.0;
       }
       __syncthreads();
-#pragma unroll
+#pragma unroll 8
       for (int kk = 0; kk < GBK; ++kk) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        const double a_0 = As[kk][tx], a_1 = As[kk][tx + 16];
+        const double b_0 = Bs[kk][ty], b_1 = Bs[kk][ty + 16];
+        acc[0][0] += a_0 * b_0;
+        acc[0][1] += a_0 * b_1;
+        acc[1][0] += a_1 * b_0;
+        acc[1][1] += a_1 * b_1;
       }
       __syncthreads();
     }
@@ -227,26 +222,23 @@ __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int 
         Bs[kk][aa] = (b < rp && c < r) ? G[b + (int64_t)c * ldh] : 0.0;
       }
       __syncthreads();
-#pragma unroll
+#pragma unroll 8
       for (int kk = 0; kk < GBK; ++kk) {
-        double av[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        const double a_0 = As[kk][tx], a_1 = As[kk][tx + 16];
+        const double b_0 = Bs[kk][ty], b_1 = Bs[kk][ty + 16];
+        acc[0][0] += a_0 * b_0;
+        acc[0][1] += a_0 * b_1;
+        acc[1][0] += a_1 * b_0;
+        acc[1][1] += a_1 * b_1;
       }
       __syncthreads();
     }
   }
   double ts = 0.0, tt = 0.0;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
       const int a = a0 + tx + 16 * i, b = b0 + ty + 16 * j;
       if (a < rp && b < rp) {
         Out[a + (int64_t)b * lds] = acc[i][j];
