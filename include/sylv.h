@@ -117,6 +117,31 @@ int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const do
                 const sylv_options* opt, sylv_handle** out);
 
 /*
+ * Batched Lyapunov equations A_i X_i + X_i A_i^T = C_i C_i^T, i = 0..count-1, of
+ * uneven sizes n_i and block widths s_i (1..8), solved together by factorized CG
+ * (Algorithm 4.1 in the one-basis form of Sec. 4.3): every phase of an iteration
+ * is one persistent launch over all running instances, and one iteration is a
+ * CUDA graph replayed until every instance has converged.  Row-chunk size and
+ * grid size of the streaming phases are picked by a built-in autotuner on the
+ * first solve.
+ *   A[i]   n_i x n_i CSR (host);  C1[i]  n_i x s[i] column-major (host)
+ *   B, C2  must be NULL;  opt->lyapunov must be 1; float64 only (SYLV_FP64)
+ * sylv_cg(h, ...) then solves all instances (sylv_bicgstab is EINVAL); its info
+ * aggregates: status OK only if every instance converged (else the first failing
+ * status), iters = max, matvecs / width = sums, rel_res / true_rel_res = max.
+ * Per-instance results: sylv_batch_instance + the single-instance calls.
+ */
+int sylv_create_batch(int32_t count, const sylv_csr* A, const sylv_csr* B, const double* const* C1,
+                      const double* const* C2, const int64_t* s, const sylv_options* opt, sylv_handle** out);
+
+/*
+ * The internal handle of instance `inst` of a batched handle (owned by the batch:
+ * do not destroy it).  sylv_get_factors / sylv_get_history / sylv_get_hessenberg
+ * on it return that instance's results of the last batched solve.
+ */
+int sylv_batch_instance(sylv_handle* h, int32_t inst, sylv_handle** out);
+
+/*
  * Factorized CG, Algorithm 4.1 (A, B symmetric positive definite; block
  * Lanczos bases).  Runs at most maxit iterations from X_0 = 0 and stops at the
  * first k with ||R^_{k+1}|| <= tol ||R^_0||.  The factors V_{k+1}, X^_{k+1},

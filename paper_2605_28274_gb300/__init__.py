@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_get_factors",
            "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
-           "sylv_strerror", "sylv_last_error", "sylv_destroy"]
+           "sylv_create_batch", "sylv_batch_instance", "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
 
 class sylv_csr(ctypes.Structure):
@@ -104,6 +104,11 @@ def load(path: Optional[str] = None):
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p]
     lib.sylv_spmm_noalloc.restype = ctypes.c_int
+    lib.sylv_create_batch.argtypes = [ctypes.c_int32, P(sylv_csr), P(sylv_csr), P(dp), P(dp), P(ctypes.c_int64),
+                                      P(sylv_options), P(ctypes.c_void_p)]
+    lib.sylv_create_batch.restype = ctypes.c_int
+    lib.sylv_batch_instance.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_void_p)]
+    lib.sylv_batch_instance.restype = ctypes.c_int
     lib.sylv_strerror.argtypes = [ctypes.c_int]
     lib.sylv_strerror.restype = ctypes.c_char_p
     lib.sylv_last_error.argtypes = []
@@ -265,9 +270,85 @@ def sylv_spmm_noalloc(n: int, nnz: int, row_ptr: int, col_idx: int, val: int, X:
     return load().sylv_spmm_noalloc(n, nnz, row_ptr, col_idx, val, X, Y, k, stream or None)
 
 
+def sylv_create_batch(As, C1s, opt: Optional[sylv_options] = None):
+    """Batched Lyapunov handle for instances (A_i, C1_i); opt.lyapunov must be 1."""
+    lib = load()
+    count = len(As)
+    arr = (sylv_csr * count)()
+    keep = []
+    for i, A in enumerate(As):
+        c, k = _make_csr(A)
+        arr[i] = c
+        keep.append(k)
+    cs = [np.asfortranarray(C, dtype=np.float64) for C in C1s]
+    ptrs = (ctypes.POINTER(ctypes.c_double) * count)(*[_dptr(C) for C in cs])
+    svec = (ctypes.c_int64 * count)(*[C.shape[1] for C in cs])
+    h = ctypes.c_void_p()
+    rc = lib.sylv_create_batch(count, arr, None, ptrs, None, svec, None if opt is None else ctypes.byref(opt),
+                               ctypes.byref(h))
+    if rc != SYLV_OK:
+        raise SylvError(rc, "sylv_create_batch")
+    return h
+
+
+def sylv_batch_instance(h, inst: int):
+    out = ctypes.c_void_p()
+    rc = load().sylv_batch_instance(h, inst, ctypes.byref(out))
+    if rc != SYLV_OK:
+        raise SylvError(rc, "sylv_batch_instance")
+    return out
+
+
 def sylv_destroy(h) -> None:
     if h is not None and h.value:
         load().sylv_destroy(h)
+
+
+class BatchSolver:
+    """Many Lyapunov equations A_i X_i + X_i A_i^T = C_i C_i^T solved together by
+    batched factorized CG: ``BatchSolver([A_0, ...], [C_0, ...]).cg(tol, maxit)``."""
+
+    def __init__(self, As, C1s, poll_every: int = 0, cuda_stream: int = 0, timeout_s: float = 0.0,
+                 no_true_residual: bool = False):
+        o = sylv_default_options()
+        o.lyapunov = 1
+        if poll_every:
+            o.poll_every = poll_every
+        o.cuda_stream = cuda_stream or None
+        o.timeout_s = timeout_s or 3600.0
+        o.no_true_residual = 1 if no_true_residual else 0
+        self.ns = [_csr_arrays(A)[0] for A in As]
+        self.h = sylv_create_batch(As, C1s, o)
+
+    def cg(self, tol: float, maxit: int) -> dict:
+        return sylv_cg(self.h, tol, maxit).as_dict()
+
+    def instance(self, i: int):
+        return sylv_batch_instance(self.h, i)
+
+    def factors(self, i: int):
+        n = self.ns[i]
+        return sylv_get_factors(self.instance(i), n, n)
+
+    def history(self, i: int) -> np.ndarray:
+        return sylv_get_history(self.instance(i))
+
+    def close(self) -> None:
+        sylv_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -140,6 +140,17 @@ struct sylv_handle {
   std::vector<std::pair<void*, size_t>> sk;  // sketch scratch buffers (pointer, bytes)
   std::vector<sylv_handle*> subs;  // correction solves of the last mixed solve
   bool is_sub = false;
+  // batched Lyapunov CG: one internal handle per instance
+  std::vector<sylv_handle*> batch;
+  sylv::BatchInst* d_insts = nullptr;
+  int2* d_items = nullptr;
+  double *b_gpart = nullptr, *b_spart = nullptr;
+  int* d_running = nullptr;
+  int* h_running = nullptr;  // pinned, 2 slots
+  size_t items_cap = 0;
+  int tuned_chunk = 0, tuned_grid = 0;
+  double tune_ms = 0.0;
+  cudaGraphExec_t graph = nullptr;
   double true_rel = -1.0;
   int refinements = 0;
   int64_t total_iters = 0, total_width = 0;
@@ -700,9 +711,9 @@ std::vector<RoundView> round_views(const sylv_handle* h) {
 
 constexpr int SKK = 8;  // columns of the sketch blocks
 
-// Yout (rows x 8) = X Min (trans = false; Min is m x 8) or X^T Min (trans = true; Min is n x 8).
+// Yout (rows x k) = X Min (trans = false; Min is m x k) or X^T Min (trans = true; Min is n x k).
 template <typename T>
-int apply_X(sylv_handle* h, bool trans, const double* Min, double* Yout) {
+int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) {
   int rc = SYLV_OK;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
@@ -710,9 +721,9 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, double* Yout) {
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
   const int max_rc = 32;
-  double* P = sk_buf(h, 0, (size_t)maxw * SKK * sizeof(double), &rc);
-  double* P2 = sk_buf(h, 1, (size_t)maxw * SKK * sizeof(double), &rc);
-  double* part = sk_buf(h, 2, (size_t)max_rc * maxw * SKK * sizeof(double), &rc);
+  double* P = sk_buf(h, 0, (size_t)maxw * k * sizeof(double), &rc);
+  double* P2 = sk_buf(h, 1, (size_t)maxw * k * sizeof(double), &rc);
+  double* part = sk_buf(h, 2, (size_t)max_rc * maxw * k * sizeof(double), &rc);
   if (rc) return rc;
   bool first = true;
   for (auto& v : views) {
@@ -720,17 +731,17 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, double* Yout) {
     const T* Uout = (const T*)(trans ? v.W : v.V);
     const int64_t bsin = trans ? v.bsV : v.bsW, bsout = trans ? v.bsW : v.bsV;
     const int r = v.nb * v.s;
-    sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, SKK, part, max_rc, P);
-    sylv::launch_small_apply(h->stream, r, SKK, v.Xh, v.lds, trans, P, P2);
-    sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, SKK, 1.0, first ? 0.0 : 1.0, Yout);
+    sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, k, part, max_rc, P);
+    sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2);
+    sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, k, 1.0, first ? 0.0 : 1.0, Yout);
     h->launches += 4;
     first = false;
   }
-  if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * SKK * sizeof(double), h->stream));
+  if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
   return SYLV_OK;
 }
 
-// Y (n x 8) = R Om (Om m x 8)
+// Y (n x 8) = R Om (Om m x 8); X is applied once to the 16 columns [Om | B Om].
 template <typename T>
 int sketch_R(sylv_handle* h, const double* Om, double* Y) {
   int rc = SYLV_OK;
@@ -741,21 +752,24 @@ int sketch_R(sylv_handle* h, const double* Om, double* Y) {
   double* Tm = sk_buf(h, 5, (size_t)m * SKK * sizeof(double), &rc);
   double* Xa = sk_buf(h, 6, (size_t)n * SKK * sizeof(double), &rc);
   double* Xb = sk_buf(h, 7, (size_t)n * SKK * sizeof(double), &rc);
+  double* M16 = sk_buf(h, 20, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
+  double* X16 = sk_buf(h, 21, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
   if (rc) return rc;
   const Side& Aop = h->side[0];
   sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, Om, SKK, part, 32, G);       // C2^T Om
   sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, h->opB.rp, h->opB.ci, h->opB.vald, Om, Tm, nullptr,
                             nullptr, 0);                                                     // B Om
-  TRY(apply_X<T>(h, false, Om, Xa));                                                         // X Om
-  TRY(apply_X<T>(h, false, Tm, Xb));                                                         // X B Om
+  sylv::launch_interleave(h->stream, m, Om, Tm, M16);
+  TRY(apply_X<T>(h, false, M16, 16, X16));                                                   // X [Om | B Om]
+  sylv::launch_deinterleave(h->stream, n, X16, Xa, Xb);
   sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, Aop.rp, Aop.ci, Aop.vald, Xa, Y, nullptr, nullptr, 0);
   sylv::launch_neg_sum(h->stream, n * SKK, Y, Xb, Y);                                        // -(A X Om + X B Om)
   sylv::launch_lowrank_axpy(h->stream, n, s, SKK, h->C1rm, G, 1.0, Y);                       // + C1 (C2^T Om)
-  h->launches += 6;
+  h->launches += 8;
   return SYLV_OK;
 }
 
-// Z (m x 8) = R^T Q (Q n x 8)
+// Z (m x 8) = R^T Q (Q n x 8); X^T is applied once to the 16 columns [A^T Q | Q].
 template <typename T>
 int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
   int rc = SYLV_OK;
@@ -766,17 +780,20 @@ int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
   double* Tn = sk_buf(h, 8, (size_t)n * SKK * sizeof(double), &rc);
   double* Za = sk_buf(h, 9, (size_t)m * SKK * sizeof(double), &rc);
   double* Zb = sk_buf(h, 10, (size_t)m * SKK * sizeof(double), &rc);
+  double* M16 = sk_buf(h, 20, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
+  double* X16 = sk_buf(h, 21, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
   if (rc) return rc;
   const Side& Bt = h->side[h->lyap ? 0 : 1];  // B^T
   sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, Q, SKK, part, 32, G);        // C1^T Q
   sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, h->opAt.rp, h->opAt.ci, h->opAt.vald, Q, Tn, nullptr,
                             nullptr, 0);                                                     // A^T Q
-  TRY(apply_X<T>(h, true, Tn, Za));                                                          // X^T A^T Q
-  TRY(apply_X<T>(h, true, Q, Zb));                                                           // X^T Q
+  sylv::launch_interleave(h->stream, n, Tn, Q, M16);
+  TRY(apply_X<T>(h, true, M16, 16, X16));                                                    // X^T [A^T Q | Q]
+  sylv::launch_deinterleave(h->stream, m, X16, Za, Zb);
   sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, Bt.rp, Bt.ci, Bt.vald, Zb, Z, nullptr, nullptr, 0);
   sylv::launch_neg_sum(h->stream, m * SKK, Z, Za, Z);
   sylv::launch_lowrank_axpy(h->stream, m, s, SKK, h->C2rm, G, 1.0, Z);
-  h->launches += 6;
+  h->launches += 8;
   return SYLV_OK;
 }
 
@@ -837,8 +854,8 @@ int sketch(sylv_handle* h, double* est, bool* ok) {
   TRY(sketch_R<T>(h, Om1, Q));  // Y = R Om1
   qr8(h, n, Q, Rk);
   TRY(sketch_Rt<T>(h, Q, Z));   // Z1 = R^T Q1
-  TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1
-  qr8(h, n, Q, Rk);
+  TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1 (a rank-8 range without it is too
+  qr8(h, n, Q, Rk);             // poor for the refinement rounds to converge)
   TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
   TRY(sketch_R<T>(h, Om2, Y3)); // tail probe
   sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 32, P);
@@ -984,9 +1001,227 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   return rc;
 }
 
+
+// ------------------------------------------------------------------ batched Lyapunov CG
+int batch_items(sylv_handle* h, int chunk, std::vector<int2>& items, std::vector<sylv::BatchInst>& insts) {
+  items.clear();
+  for (size_t i = 0; i < h->batch.size(); ++i) {
+    const int64_t n = h->batch[i]->side[0].n;
+    insts[i].item_begin = (int)items.size();
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) items.push_back(make_int2((int)i, (int)r0));
+    insts[i].item_end = (int)items.size();
+  }
+  if (items.size() > h->items_cap) {
+    const size_t cap = items.size() * 2;
+    if (h->d_items) cudaFree(h->d_items);
+    if (h->b_gpart) cudaFree(h->b_gpart);
+    if (h->b_spart) cudaFree(h->b_spart);
+    h->d_items = nullptr;
+    h->b_gpart = h->b_spart = nullptr;
+    h->items_cap = 0;
+    CU(cudaMalloc(&h->d_items, cap * sizeof(int2)));
+    CU(cudaMalloc(&h->b_gpart, cap * 64 * sizeof(double)));
+    CU(cudaMalloc(&h->b_spart, cap * 64 * sizeof(double)));
+    h->items_cap = cap;
+  }
+  CU(cudaMemcpyAsync(h->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->d_insts, insts.data(), insts.size() * sizeof(sylv::BatchInst), cudaMemcpyHostToDevice,
+                     h->stream));
+  CU(cudaStreamSynchronize(h->stream));  // the host vectors may change after return
+  return SYLV_OK;
+}
+
+int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
+  const double t0 = now_s();
+  const double deadline = t0 + (h->opt.timeout_s > 0 ? h->opt.timeout_s : 3600.0);
+  if (!(tol >= 0.0) || maxit < 0) return fail(SYLV_EINVAL, "tol must be >= 0 and maxit >= 0");
+  const int count = (int)h->batch.size();
+  cudaStream_t strm = h->stream;
+  h->launches = 0;
+  std::vector<sylv::BatchInst> insts(count);
+  int maxs = 1;
+  for (int i = 0; i < count; ++i) {
+    sylv_handle* x = h->batch[i];
+    TRY(ensure_capacity(x, M_CG, std::max(2, maxit + 1), maxit + 1));
+    CU(cudaMemsetAsync(x->st, 0, sizeof(DevState), strm));
+    const size_t l2 = (size_t)(x->lds * x->lds) * sizeof(double);
+    for (double* p : {x->Xh, x->Rh, x->Ph, x->Qh, x->Th}) CU(cudaMemsetAsync(p, 0, l2, strm));
+    CU(cudaMemsetAsync(x->side[0].H, 0, l2, strm));
+    setup_qr<double>(x, 0);
+    sylv::SmallCtx c = small_ctx(x);
+    sylv::launch_init_small(strm, c, x->side[0].RQR, x->side[0].RQR, tol, 0);
+    h->launches += 7;
+    sylv::BatchInst& I = insts[i];
+    std::memset(&I, 0, sizeof(I));
+    I.n = x->side[0].n;
+    I.s = (int)x->s;
+    I.k = 0;
+    I.rp = x->side[0].rp;
+    I.ci = x->side[0].ci;
+    I.val = x->side[0].vald;
+    I.V = (double*)x->side[0].V;
+    I.H = x->side[0].H;
+    I.ldh = x->lds;
+    I.X = x->Xh;
+    I.R = x->Rh;
+    I.P = x->Ph;
+    I.Q = x->Qh;
+    I.M = x->Th;
+    I.lds = x->lds;
+    I.st = x->st;
+    I.hist = x->hist;
+    I.R1 = x->side[0].R1;
+    I.Rinv = x->side[0].Rinv;
+    I.psm = x->psmall;
+    maxs = std::max(maxs, I.s);
+  }
+  CU(cudaGetLastError());
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sylv::BatchCtx bc{};
+  bc.insts = h->d_insts;
+  bc.count = count;
+  bc.delta = deflate_tol(h);
+  bc.running = h->d_running;
+  bc.sgrid = 4 * sms;
+  std::vector<int2> items;
+  // autotuner: rows per work item x persistent grid size, timed on the batch itself
+  // (sparse apply + Gram phases of the first iteration; the real iteration rewrites
+  // everything they write)
+  if (h->tuned_chunk == 0) {
+    const int chunks[] = {512, 1024, 2048, 4096};
+    const int mults[] = {1, 2, 4, 8};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    const double tt0 = now_s();
+    for (int ch : chunks)
+      for (int mu : mults) {
+        TRY(batch_items(h, ch, items, insts));
+        bc.items = h->d_items;
+        bc.nitems = (int)items.size();
+        bc.chunk = ch;
+        bc.grid = mu * sms;
+        bc.gpart = h->b_gpart;
+        bc.spart = h->b_spart;
+        sylv::launch_batch_spmm_gram(strm, bc);
+        CU(cudaEventRecord(e0, strm));
+        for (int rep = 0; rep < 3; ++rep) sylv::launch_batch_spmm_gram(strm, bc);
+        CU(cudaEventRecord(e1, strm));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        h->launches += 8;
+        if (ms < best) {
+          best = ms;
+          h->tuned_chunk = ch;
+          h->tuned_grid = mu * sms;
+        }
+      }
+    h->tune_ms = (now_s() - tt0) * 1e3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  TRY(batch_items(h, h->tuned_chunk, items, insts));
+  bc.items = h->d_items;
+  bc.nitems = (int)items.size();
+  bc.chunk = h->tuned_chunk;
+  bc.grid = h->tuned_grid;
+  bc.gpart = h->b_gpart;
+  bc.spart = h->b_spart;
+  // one iteration of all instances as a CUDA graph (15 phase kernels)
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal));
+  sylv::launch_batch_iteration(strm, bc);
+  CU(cudaStreamEndCapture(strm, &g));
+  cudaError_t ge = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ge != cudaSuccess) return fail(SYLV_ECUDA, std::string("graph: ") + cudaGetErrorString(ge));
+  const int poll = h->opt.poll_every > 0 ? h->opt.poll_every : 8;
+  int slot = 0, pending = -1, k = 0;
+  bool done = false;
+  while (k < maxit && !done) {
+    const int nrep = std::min(poll, maxit - k);
+    for (int r = 0; r < nrep; ++r) CU(cudaGraphLaunch(h->graph, strm));
+    k += nrep;
+    h->launches += 15 * nrep;
+    CU(cudaMemcpyAsync(&h->h_running[slot], h->d_running, sizeof(int), cudaMemcpyDeviceToHost, strm));
+    CU(cudaEventRecord(h->ev[slot], strm));
+    if (pending >= 0) {
+      TRY(wait_status(h, pending, deadline));
+      if (h->h_running[pending] == 0) done = true;
+    }
+    pending = slot;
+    slot ^= 1;
+  }
+  CU(cudaStreamSynchronize(strm));
+  // per-instance results, then the aggregate
+  int agg = SYLV_OK;
+  double worst = 0.0;
+  int64_t width = 0, matvecs = 0;
+  int maxk = 0;
+  for (int i = 0; i < count; ++i) {
+    sylv_handle* x = h->batch[i];
+    DevState ds;
+    CU(cudaMemcpy(&ds, x->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    x->method = M_CG;
+    x->iters = ds.iters;
+    x->width = (int64_t)ds.iters * x->s;
+    x->total_iters = x->iters;
+    x->total_width = x->width;
+    x->nblocks = ds.iters + 1;
+    int rc = ds.status == sylv::ST_CONVERGED ? SYLV_OK
+             : ds.status == sylv::ST_RUNNING ? SYLV_ENOTCONV
+             : ds.status == sylv::ST_BREAKDOWN ? SYLV_EBREAKDOWN : SYLV_ENONFINITE;
+    x->status = rc;
+    x->true_rel = -1.0;
+    if (agg == SYLV_OK && rc != SYLV_OK) agg = rc;
+    worst = std::max(worst, ds.r0 > 0 ? ds.rnorm / ds.r0 : 0.0);
+    width += x->width;
+    matvecs += ds.iters;
+    maxk = std::max(maxk, ds.iters);
+  }
+  // float64 true residual of every instance (unless disabled)
+  double worst_true = -1.0;
+  if (!h->opt.no_true_residual) {
+    for (sylv_handle* x : h->batch) {
+      if (x->width == 0 || x->C1rm == nullptr) continue;
+      double est = 0.0;
+      bool ok = false;
+      TRY(sketch<double>(x, &est, &ok));
+      x->true_rel = x->cnorm > 0 ? est / x->cnorm : 0.0;
+      worst_true = std::max(worst_true, x->true_rel);
+    }
+  }
+  h->method = M_CG;
+  h->status = agg;
+  h->iters = maxk;
+  if (info) {
+    info->status = agg;
+    info->iters = maxk;
+    info->matvecs = matvecs;
+    info->width = width;
+    info->rel_res = worst;
+    info->true_rel_res = worst_true;
+    info->solve_ms = (now_s() - t0) * 1e3;
+    info->kernel_launches = h->launches;
+  }
+  return agg;
+}
+
 int solve(sylv_handle* h, int method, double tol, int32_t maxit, sylv_info* info) {
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
   if (info) std::memset(info, 0, sizeof(*info));
+  if (!h->batch.empty()) {
+    if (method != M_CG) return fail(SYLV_EINVAL, "batched handles run factorized CG (Lyapunov) only");
+    return batch_cg(h, tol, maxit, info);
+  }
   return h->mixed ? run_solve<float>(h, method, tol, maxit, info) : run_solve<double>(h, method, tol, maxit, info);
 }
 
@@ -1098,8 +1333,75 @@ int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
   return solve(h, M_BICG, tol, maxit, info);
 }
 
+int sylv_create_batch(int32_t count, const sylv_csr* A, const sylv_csr* B, const double* const* C1,
+                      const double* const* C2, const int64_t* s, const sylv_options* opt, sylv_handle** out) {
+  g_err.clear();
+  if (!out) return fail(SYLV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !A || !C1 || !s) return fail(SYLV_EINVAL, "need count >= 1 and A, C1, s arrays");
+  sylv_options o;
+  sylv_default_options(&o);
+  if (opt) o = *opt;
+  if (!o.lyapunov || B != nullptr || C2 != nullptr)
+    return fail(SYLV_EINVAL, "batched mode solves Lyapunov equations: set lyapunov = 1, B = C2 = NULL");
+  if (o.precision != SYLV_FP64) return fail(SYLV_EINVAL, "batched mode runs in SYLV_FP64");
+  sylv_handle* h = new sylv_handle();
+  h->opt = o;
+  h->lyap = true;
+  h->s = 0;
+  auto bail = [&](int rc) {
+    std::string msg = g_err;
+    sylv_destroy(h);
+    g_err = msg;
+    return rc;
+  };
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    delete h;
+    return fail(SYLV_ECUDA, "no CUDA device");
+  }
+  if (o.cuda_stream) {
+    h->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(SYLV_ECUDA, "stream"));
+    h->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(SYLV_ECUDA, "event"));
+  if (cudaMallocHost(&h->h_running, 2 * sizeof(int)) != cudaSuccess) return bail(fail(SYLV_ECUDA, "pinned"));
+  int rc = alloc_fixed(h, &h->d_running, 1);
+  if (!rc) rc = alloc_fixed(h, &h->d_insts, (size_t)count);
+  if (rc) return bail(rc);
+  sylv_options io = o;
+  io.cuda_stream = h->stream;
+  io.profile = 0;
+  for (int i = 0; i < count; ++i) {
+    sylv_handle* x = nullptr;
+    rc = sylv_create(&A[i], nullptr, C1[i], nullptr, s[i], &io, &x);
+    if (rc) {
+      g_err = "instance " + std::to_string(i) + ": " + g_err;
+      return bail(rc);
+    }
+    h->batch.push_back(x);
+  }
+  *out = h;
+  return SYLV_OK;
+}
+
+int sylv_batch_instance(sylv_handle* h, int32_t inst, sylv_handle** out) {
+  if (!h || !out) return fail(SYLV_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (h->batch.empty()) return fail(SYLV_EINVAL, "not a batched handle");
+  if (inst < 0 || inst >= (int32_t)h->batch.size()) return fail(SYLV_EINVAL, "instance index out of range");
+  *out = h->batch[inst];
+  return SYLV_OK;
+}
+
 int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t* r) {
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (!h->batch.empty()) return fail(SYLV_EINVAL, "batched handle: use sylv_batch_instance");
   if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
   const int64_t R = h->total_width;
   if (r) *r = R;
@@ -1237,6 +1539,10 @@ const char* sylv_last_error(void) { return g_err.c_str(); }
 void sylv_destroy(sylv_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (sylv_handle* x : h->batch) sylv_destroy(x);
+  h->batch.clear();
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->h_running) cudaFreeHost(h->h_running);
   free_subs(h);
   free_sketch(h);
   free_solve(h);

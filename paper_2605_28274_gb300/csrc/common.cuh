@@ -79,4 +79,35 @@ __device__ __forceinline__ bool last_cta(unsigned int* ticket, int* flag_sh) {
   return last;
 }
 
+// Cholesky G = R^T R of a symmetric s x s matrix (G[u*s+t], s <= 8) with upper R
+// (column-major R[i + j*s]) and its inverse Ri.  A pivot <= thr is a failure
+// (returns 1).  Single thread.
+__device__ __forceinline__ int chol_small(const double* G, int s, double thr, double* R, double* Ri) {
+  for (int e = 0; e < 64; ++e) {
+    R[e] = 0.0;
+    Ri[e] = 0.0;
+  }
+  for (int j = 0; j < s; ++j) {
+    double d = G[j * s + j];
+    for (int k = 0; k < j; ++k) d -= R[k + j * s] * R[k + j * s];
+    if (!(d > thr)) return 1;
+    const double rjj = sqrt(d);
+    R[j + j * s] = rjj;
+    for (int i = j + 1; i < s; ++i) {
+      double g = G[j * s + i];
+      for (int k = 0; k < j; ++k) g -= R[k + j * s] * R[k + i * s];
+      R[j + i * s] = g / rjj;
+    }
+  }
+  for (int j = 0; j < s; ++j) {
+    Ri[j + j * s] = 1.0 / R[j + j * s];
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int k = i; k < j; ++k) acc += Ri[i + k * s] * R[k + j * s];
+      Ri[i + j * s] = -acc / R[j + j * s];
+    }
+  }
+  return 0;
+}
+
 }  // namespace sylv

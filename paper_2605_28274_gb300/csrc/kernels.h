@@ -129,11 +129,55 @@ void launch_small_apply(cudaStream_t, int r, int k, const double* Xh, int64_t ld
 // Y = alpha Y + C G (C n x s row-major, G s x k row-major, Y n x k row-major).
 void launch_lowrank_axpy(cudaStream_t, int64_t n, int s, int k, const double* C, const double* G, double alpha,
                          double* Y);
+// out (rows x 16) = [a | b], and back (a, b rows x 8; all row-major).
+void launch_interleave(cudaStream_t, int64_t rows, const double* a, const double* b, double* out);
+void launch_deinterleave(cudaStream_t, int64_t rows, const double* in, double* a, double* b);
 // out = -(X1 + X2) element-wise.
 void launch_neg_sum(cudaStream_t, int64_t count, const double* X1, const double* X2, double* out);
 // out[0] = sum of squares of x (deterministic; ticket must be zero).
 void launch_sumsq(cudaStream_t, int64_t count, const double* x, double* partials, unsigned int* ticket, double* out);
 // out[0] = trace(G1 G2) for s x s matrices.
 void launch_trace_prod(cudaStream_t, int s, const double* G1, const double* G2, double* out);
+
+// ---------------------------------------------------------------- batched Lyapunov CG
+// One entry per instance (device array).  All buffers belong to the instance's own
+// handle; the batched phase kernels below walk every active instance in one launch
+// and read the iteration index k from here, so one CUDA graph serves every iteration.
+struct BatchInst {
+  int64_t n;
+  int s, k;             // block width; current iteration (advanced on the device)
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* val;    // CSR of A (float64)
+  double* V;            // basis blocks (n x s row-major each)
+  double* H;            // block tridiagonal Lanczos matrix, dense column-major (ld ldh)
+  int64_t ldh;
+  double *X, *R, *P, *Q, *M;  // small matrices (ld lds); M = [H P^, 0]
+  int64_t lds;
+  DevState* st;
+  double* hist;
+  double *R1, *Rinv;    // CholQR scratch (s x s)
+  double* psm;          // per-tile partial sums of the small phases
+  int item_begin, item_end;  // this instance's (row chunk) work items
+};
+
+struct BatchCtx {
+  BatchInst* insts;     // device array
+  int count;
+  const int2* items;    // (instance, first row) per row-chunk work item
+  int nitems;
+  int chunk;            // rows per work item (autotuned)
+  int grid;             // CTAs of the persistent row phases (autotuned)
+  double* gpart;        // [nitems][64] Gram partials
+  double* spart;        // [nitems][64] self-Gram partials
+  double delta;
+  int* running;         // device counter of instances still running
+  int sgrid;            // CTAs of the persistent small-matrix phases
+};
+
+// The 15 phases of one factorized-CG (Lyapunov) iteration over all instances.
+void launch_batch_iteration(cudaStream_t, const BatchCtx&);
+// Only the sparse-apply and Gram phases (for the autotuner).
+void launch_batch_spmm_gram(cudaStream_t, const BatchCtx&);
 
 }  // namespace sylv

@@ -207,15 +207,29 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
   }
 }
 
-__global__ void reduce_H_kernel(const DevState* st, const double* __restrict__ partial, int ncta, int nb, int s,
-                                double* __restrict__ H, int64_t ldh, int64_t row0, int64_t col0,
-                                double* __restrict__ Hc, int add) {
+// Fixed-order sum of the per-CTA partials: 64-thread CTAs (more SMs busy for small
+// nb*s*s) and four independent accumulators over interleaved CTAs (loads in flight
+// instead of one dependent add chain), combined in a fixed order.
+constexpr int RED_NT = 64;
+
+__global__ void __launch_bounds__(RED_NT) reduce_H_kernel(const DevState* st, const double* __restrict__ partial,
+                                                          int ncta, int nb, int s, double* __restrict__ H,
+                                                          int64_t ldh, int64_t row0, int64_t col0,
+                                                          double* __restrict__ Hc, int add) {
   if (stopped(st)) return;
   const int E = nb * s * s;
-  const int e = blockIdx.x * NT + threadIdx.x;
+  const int e = blockIdx.x * RED_NT + threadIdx.x;
   if (e >= E) return;
-  double v = 0.0;
-  for (int c = 0; c < ncta; ++c) v += partial[(int64_t)c * E + e];
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+  int c = 0;
+  for (; c + 3 < ncta; c += 4) {
+    v0 += partial[(int64_t)c * E + e];
+    v1 += partial[(int64_t)(c + 1) * E + e];
+    v2 += partial[(int64_t)(c + 2) * E + e];
+    v3 += partial[(int64_t)(c + 3) * E + e];
+  }
+  for (; c < ncta; ++c) v0 += partial[(int64_t)c * E + e];
+  const double v = (v0 + v1) + (v2 + v3);
   Hc[e] = v;
   const int b = e / (s * s), r = e - b * s * s, u = r / s, t = r - u * s;
   double* h = H + (row0 + (int64_t)b * s + u) + (col0 + t) * ldh;
@@ -357,8 +371,18 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
     const int groups = NT / E;
     const int e = threadIdx.x % E, g = threadIdx.x / E;
     double v = 0.0;
-    if (g < groups)
-      for (int c = g; c < ncta; c += groups) v += partial[(int64_t)c * E + e];
+    if (g < groups) {
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int c = g;
+      for (; c + 3 * groups < ncta; c += 4 * groups) {
+        v0 += partial[(int64_t)c * E + e];
+        v1 += partial[(int64_t)(c + groups) * E + e];
+        v2 += partial[(int64_t)(c + 2 * groups) * E + e];
+        v3 += partial[(int64_t)(c + 3 * groups) * E + e];
+      }
+      for (; c < ncta; c += groups) v0 += partial[(int64_t)c * E + e];
+      v = (v0 + v1) + (v2 + v3);
+    }
     gsum[threadIdx.x] = v;
     __syncthreads();
     if (threadIdx.x < E) {
@@ -517,7 +541,8 @@ int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T
 void launch_reduce_H(cudaStream_t strm, const DevState* st, const double* partial, int ncta, int nb, int s, double* H,
                      int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add) {
   const int E = nb * s * s;
-  reduce_H_kernel<<<(E + NT - 1) / NT, NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc, add ? 1 : 0);
+  reduce_H_kernel<<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc,
+                                                                  add ? 1 : 0);
 }
 
 template <typename T>

@@ -125,6 +125,27 @@ __global__ void lowrank_axpy_kernel(int64_t n, int s, int k, const double* __res
   Y[e] = alpha * Y[e] + acc;
 }
 
+// out (rows x 16) = [a | b] with a, b rows x 8 (all row-major)
+__global__ void interleave_kernel(int64_t rows, const double* __restrict__ a, const double* __restrict__ b,
+                                  double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= rows * 16) return;
+  const int64_t r = e >> 4;
+  const int c = (int)(e & 15);
+  out[e] = c < 8 ? a[r * 8 + c] : b[r * 8 + c - 8];
+}
+
+// a, b (rows x 8) = columns 0..7 and 8..15 of in (rows x 16)
+__global__ void deinterleave_kernel(int64_t rows, const double* __restrict__ in, double* __restrict__ a,
+                                    double* __restrict__ b) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= rows * 16) return;
+  const int64_t r = e >> 4;
+  const int c = (int)(e & 15);
+  if (c < 8) a[r * 8 + c] = in[e];
+  else b[r * 8 + c - 8] = in[e];
+}
+
 // out = -(X1 + X2), element-wise
 __global__ void neg_sum_kernel(int64_t count, const double* __restrict__ X1, const double* __restrict__ X2,
                                double* __restrict__ out) {
@@ -192,6 +213,16 @@ void launch_small_apply(cudaStream_t strm, int r, int k, const double* Xh, int64
 void launch_lowrank_axpy(cudaStream_t strm, int64_t n, int s, int k, const double* C, const double* G, double alpha,
                          double* Y) {
   lowrank_axpy_kernel<<<(unsigned)((n * k + NT - 1) / NT), NT, 0, strm>>>(n, s, k, C, G, alpha, Y);
+}
+
+void launch_interleave(cudaStream_t strm, int64_t rows, const double* a, const double* b, double* out) {
+  if (rows == 0) return;
+  interleave_kernel<<<(unsigned)((rows * 16 + NT - 1) / NT), NT, 0, strm>>>(rows, a, b, out);
+}
+
+void launch_deinterleave(cudaStream_t strm, int64_t rows, const double* in, double* a, double* b) {
+  if (rows == 0) return;
+  deinterleave_kernel<<<(unsigned)((rows * 16 + NT - 1) / NT), NT, 0, strm>>>(rows, in, a, b);
 }
 
 void launch_neg_sum(cudaStream_t strm, int64_t count, const double* X1, const double* X2, double* out) {
