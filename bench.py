@@ -229,6 +229,82 @@ def cpu_baseline(p, iters):
             "details": det}
 
 
+# ----------------------------------------------------------------------------- variants
+def measure_mixed(p, stream, steps, warmup):
+    """Same operators and tolerance in the mixed mode (FP32 factors, FP64 small side,
+    FP64 true-residual refinement): time to a TRUE relative residual of p.tol."""
+    import torch
+
+    import paper_2605_28274_gb300 as ps
+
+    with ps.Solver(p.A, p.B, p.C1, p.C2, precision="mixed", profile=True, cuda_stream=stream.cuda_stream) as sv:
+        for _ in range(warmup):
+            sv.bicgstab(p.tol, p.maxit)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        prof = {}
+        e0.record(stream)
+        for _ in range(steps):
+            info = sv.bicgstab(p.tol, p.maxit)
+            for e in sv.profile():
+                d = prof.setdefault(e["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+                for key in ("launches", "ms", "bytes", "flops"):
+                    d[key] += e[key]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pk = peaks()
+    hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
+    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
+    gbs = hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None
+    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_mixed", "value": ms / 1e3, "unit": "s",
+            "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
+            "true_rel_res": info["true_rel_res"], "width": info["width"],
+            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if gbs else None,
+            "kernel_ms_per_solve": {k: round(v["ms"] / steps, 2) for k, v in
+                                    sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+
+
+def measure_batched(stream, steps, warmup):
+    """64 Lyapunov instances (2D Laplacian + U[0,1] shift, N ~ U{64..256}, s ~ {1,2,4}),
+    batched factorized CG to 1e-8 vs the plain FP64 path looping over the instances."""
+    import torch
+
+    import paper_2605_28274_gb300 as ps
+
+    probs = wl.cfg_batched_lyapunov(count=64)
+    As, Cs = [q.A for q in probs], [q.C1 for q in probs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ps.BatchSolver(As, Cs, cuda_stream=stream.cuda_stream) as bs:
+        for _ in range(warmup):
+            bs.cg(1e-8, 1000)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            info = bs.cg(1e-8, 1000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        its = [len(bs.history(i)) - 1 for i in range(len(probs))]
+    t_batch = e0.elapsed_time(e1) / steps / 1e3
+    svs = [ps.Solver(q.A, None, q.C1, None, lyapunov=True, cuda_stream=stream.cuda_stream) for q in probs]
+    for sv in svs:
+        sv.cg(1e-8, 1000)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for sv in svs:
+        sv.cg(1e-8, 1000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for sv in svs:
+        sv.close()
+    return {"workload": "batched_lyapunov_64x_laplace2d_N64-256_s124_cg_fp64", "value": t_batch, "unit": "s",
+            "status": info["status_name"], "instances": len(probs), "sum_n": int(sum(q.A.nrows for q in probs)),
+            "iters_min_median_max": [int(min(its)), int(np.median(its)), int(max(its))],
+            "true_rel_res_max": info["true_rel_res"], "kernel_launches": info["kernel_launches"],
+            "plain_fp64_sequential_s": t_seq, "speedup_vs_plain_fp64": t_seq / t_batch}
+
+
 # ----------------------------------------------------------------------------- our arm
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -356,14 +432,21 @@ def run_ours(args):
         e2e_s = float(t.item())
     sv.close()
 
+    variants = {}
+    if not args.no_variants:
+        variants["mixed"] = measure_mixed(p, stream, args.steps, 2)
+        variants["mixed"]["speedup_vs_fp64"] = (ms_step / 1e3) / variants["mixed"]["value"]
+        variants["batched"] = measure_batched(stream, args.steps, 2)
+
     line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(p),
             "iters": iters, "status": status, "rel_res": infos[-1]["rel_res"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "status": STATUS(inf2)},
+            "true_rel_res": infos[-1]["true_rel_res"],
             "roofline": roof, "spmm_gram_hbm": spmm_gram, "kernel_breakdown": breakdown,
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks, "variants": variants}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(p, iters)
     if rank == 0:
@@ -414,6 +497,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--maxit", type=int, default=0, help="override maxit (a short solve, e.g. for ncu captures)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed and batched variant timings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -73,11 +73,11 @@ enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2 };
 // Kernel classes timed by the optional profiler.
 enum KClass {
   KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_SCALE, KC_SETUP,
-  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_NUM
+  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_RESID_TSG, KC_RESID_TSU, KC_NUM
 };
 const char* const kKcNames[KC_NUM] = {"spmm",         "gram",  "reduce_h",   "update",           "cholqr_chol",
                                       "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise",
-                                      "true_residual"};
+                                      "true_residual", "resid_tsg", "resid_tsu"};
 
 struct Prof {
   struct Rec {
@@ -93,6 +93,7 @@ struct Prof {
   double ms[KC_NUM] = {}, bytes[KC_NUM] = {}, flops[KC_NUM] = {};
   int cur_k = -1;
   bool valid = false;
+  size_t flushed = 0;  // records already summed
 };
 
 }  // namespace
@@ -137,6 +138,7 @@ struct sylv_handle {
   double* Om = nullptr;            // two m x 8 Gaussian probe blocks (row-major)
   double cnorm = -1.0;             // ||C1 C2^T||_F
   DevState* st_sk = nullptr;       // status word of the sketch's CholQR
+  double* sk_host = nullptr;       // pinned: 3 sums + the sketch's DevState
   std::vector<std::pair<void*, size_t>> sk;  // sketch scratch buffers (pointer, bytes)
   std::vector<sylv_handle*> subs;  // correction solves of the last mixed solve
   bool is_sub = false;
@@ -149,6 +151,7 @@ struct sylv_handle {
   int* h_running = nullptr;  // pinned, 2 slots
   size_t items_cap = 0;
   int tuned_chunk = 0, tuned_grid = 0;
+  std::vector<cudaStream_t> pool;  // streams for the per-instance true-residual sketches
   double tune_ms = 0.0;
   cudaGraphExec_t graph = nullptr;
   double true_rel = -1.0;
@@ -297,6 +300,7 @@ void prof_reset(sylv_handle* h) {
   p.on = h->opt.profile != 0;
   p.used = 0;
   p.recs.clear();
+  p.flushed = 0;
   p.cur_k = -1;
   p.valid = false;
   for (int i = 0; i < KC_NUM; ++i) {
@@ -309,7 +313,8 @@ void prof_reset(sylv_handle* h) {
 void prof_finish(sylv_handle* h, int iters) {
   Prof& p = h->prof;
   if (!p.on) return;
-  for (const auto& r : p.recs) {
+  for (size_t i = p.flushed; i < p.recs.size(); ++i) {
+    const auto& r = p.recs[i];
     if (r.k >= iters) continue;  // enqueued after the stop: no-op launches
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
@@ -321,6 +326,7 @@ void prof_finish(sylv_handle* h, int iters) {
     p.bytes[r.cls] += r.bytes;
     p.flops[r.cls] += r.flops;
   }
+  p.flushed = p.recs.size();
   p.valid = true;
 }
 
@@ -683,6 +689,7 @@ int prepare_residual_ops(sylv_handle* h, const sylv_csr* A, const sylv_csr* B) {
   TRY(alloc_fixed(h, &h->Om, om.size()));
   CU(cudaMemcpyAsync(h->Om, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   TRY(alloc_fixed(h, &h->st_sk, 1));
+  CU(cudaMallocHost(&h->sk_host, 4 * sizeof(double) + sizeof(DevState)));
   CU(cudaStreamSynchronize(h->stream));
   return SYLV_OK;
 }
@@ -720,10 +727,10 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) 
   auto views = round_views(h);
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
-  const int max_rc = 32;
+  const int max_rc = 0;  // launch_tsg picks the row chunks
   double* P = sk_buf(h, 0, (size_t)maxw * k * sizeof(double), &rc);
   double* P2 = sk_buf(h, 1, (size_t)maxw * k * sizeof(double), &rc);
-  double* part = sk_buf(h, 2, (size_t)max_rc * maxw * k * sizeof(double), &rc);
+  double* part = sk_buf(h, 2, (size_t)sylv::tsg_partial_elems(maxw, k) * sizeof(double), &rc);
   if (rc) return rc;
   bool first = true;
   for (auto& v : views) {
@@ -731,10 +738,13 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) 
     const T* Uout = (const T*)(trans ? v.W : v.V);
     const int64_t bsin = trans ? v.bsV : v.bsW, bsout = trans ? v.bsW : v.bsV;
     const int r = v.nb * v.s;
-    sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, k, part, max_rc, P);
+    const double fl = 2.0 * (double)r * k;
+    PROF(h, KC_RESID_TSG, (double)rows_in * (r * sizeof(T) + k * 8.0), fl * rows_in,
+         sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, k, part, max_rc, P));
     sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2);
-    sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, k, 1.0, first ? 0.0 : 1.0, Yout);
-    h->launches += 4;
+    PROF(h, KC_RESID_TSU, (double)rows_out * (r * sizeof(T) + 2.0 * k * 8.0), fl * rows_out,
+         sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, k, 1.0, first ? 0.0 : 1.0, Yout));
+    h->launches += 2;
     first = false;
   }
   if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
@@ -822,9 +832,10 @@ void qr8(sylv_handle* h, int64_t n, double* Y, double* Rout) {
   h->launches += 5;
 }
 
-// ||R||_F estimate; leaves Q (n x 8, buffer 11) and Z (m x 8, buffer 12) with R ~ Q Z^T.
+// Enqueues the ||R||_F estimate on h->stream; leaves Q (n x 8, buffer 11) and Z
+// (m x 8, buffer 12) with R ~ Q Z^T.  sketch_finish waits and reads the result.
 template <typename T>
-int sketch(sylv_handle* h, double* est, bool* ok) {
+int sketch_enqueue(sylv_handle* h) {
   int rc = SYLV_OK;
   const int s = (int)h->s;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
@@ -863,16 +874,27 @@ int sketch(sylv_handle* h, double* est, bool* ok) {
   sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
   sylv::launch_sumsq(h->stream, n * SKK, Y3, part, ticket + 1, sums + 1);
   h->launches += 6;
-  double hs[3] = {0, 0, 0};
-  CU(cudaMemcpyAsync(hs, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  DevState dst;
-  CU(cudaMemcpyAsync(&dst, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(h->sk_host, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(h->sk_host + 4, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  return SYLV_OK;
+}
+
+int sketch_finish(sylv_handle* h, double* est, bool* ok) {
   CU(cudaStreamSynchronize(h->stream));
+  const double* hs = h->sk_host;
+  DevState dst;
+  std::memcpy(&dst, h->sk_host + 4, sizeof(DevState));
   if (h->cnorm < 0) h->cnorm = std::sqrt(std::max(0.0, hs[2]));
   *ok = dst.status == sylv::ST_RUNNING;
   // with a rank-deficient sketch (R of rank < 8) the probe estimate alone is used
   *est = *ok ? std::sqrt(hs[0] + hs[1] / SKK) : std::sqrt(hs[1] / SKK);
   return SYLV_OK;
+}
+
+template <typename T>
+int sketch(sylv_handle* h, double* est, bool* ok) {
+  TRY(sketch_enqueue<T>(h));
+  return sketch_finish(h, est, ok);
 }
 
 // A correction solve A dX + dX B = Q Z^T on the same operators (s = 8).
@@ -963,6 +985,8 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
           }
         }
       }
+      h->prof.cur_k = -1;
+      prof_finish(h, 1 << 30);
       h->true_rel = h->cnorm > 0 ? est / h->cnorm : 0.0;
       if (!h->mixed) break;
       if (h->true_rel <= tol) {
@@ -1187,17 +1211,33 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     matvecs += ds.iters;
     maxk = std::max(maxk, ds.iters);
   }
-  // float64 true residual of every instance (unless disabled)
+  // float64 true residual of every instance (unless disabled), instances spread
+  // over a pool of streams so the small ones run side by side
   double worst_true = -1.0;
   if (!h->opt.no_true_residual) {
-    for (sylv_handle* x : h->batch) {
-      if (x->width == 0 || x->C1rm == nullptr) continue;
+    if (h->pool.empty()) {
+      h->pool.resize(16, nullptr);
+      for (auto& ps : h->pool) CU(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+    }
+    std::vector<sylv_handle*> todo;
+    for (sylv_handle* x : h->batch)
+      if (x->width > 0 && x->C1rm != nullptr) todo.push_back(x);
+    for (size_t i = 0; i < todo.size(); ++i) {
+      todo[i]->stream = h->pool[i % h->pool.size()];
+      TRY(sketch_enqueue<double>(todo[i]));
+      h->launches += 60;
+    }
+    int rc_all = SYLV_OK;
+    for (sylv_handle* x : todo) {
       double est = 0.0;
       bool ok = false;
-      TRY(sketch<double>(x, &est, &ok));
+      const int rc = sketch_finish(x, &est, &ok);
+      x->stream = h->stream;
+      if (rc != SYLV_OK && rc_all == SYLV_OK) rc_all = rc;
       x->true_rel = x->cnorm > 0 ? est / x->cnorm : 0.0;
       worst_true = std::max(worst_true, x->true_rel);
     }
+    if (rc_all != SYLV_OK) return rc_all;
   }
   h->method = M_CG;
   h->status = agg;
@@ -1543,6 +1583,9 @@ void sylv_destroy(sylv_handle* h) {
   h->batch.clear();
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->h_running) cudaFreeHost(h->h_running);
+  for (auto& ps : h->pool)
+    if (ps) cudaStreamDestroy(ps);
+  if (h->sk_host) cudaFreeHost(h->sk_host);
   free_subs(h);
   free_sketch(h);
   free_solve(h);

@@ -115,7 +115,9 @@ void launch_bicg_p(cudaStream_t, const SmallCtx&, int rpp);
 
 // ---------------------------------------------------------------- true residual (float64 accumulation)
 // P (nb*su x k, row-major) = U^T Y with U in block-row-major storage (nb blocks of width su,
-// element TU) and Y n x k row-major float64, k <= 16.  partial: scratch of max_rc * nb*su*k.
+// element TU) and Y n x k row-major float64, k <= 16.  partial: scratch of at least
+// tsg_partial_elems(nb*su, k) doubles (max_rc > 0 caps the row chunks).
+int64_t tsg_partial_elems(int64_t ncol, int k);
 template <typename TU>
 void launch_tsg(cudaStream_t, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* Y, int k,
                 double* partial, int max_rc, double* P);

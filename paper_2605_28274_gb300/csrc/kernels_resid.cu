@@ -4,9 +4,14 @@
 // the mixed-precision mode.
 //
 // R is only ever applied to thin blocks (k <= 16 columns): R Omega and R^T Q.
-// Those products cancel to ~1e-8 of their terms near convergence, so every
-// product here accumulates in float64, whatever the precision the basis blocks
-// U are stored in (float or double).  Blocks of k vectors are n x k row-major.
+// Those products cancel to ~1e-8 of their terms near convergence, so the tall
+// products with the basis (tsg, tsu) accumulate in double-float arithmetic on
+// the FP32 pipes: each float64 operand is split into hi + lo floats, products
+// are formed with the error-free FMA product, sums with the error-free two-sum
+// (Dekker 1971; Knuth TAOCP vol. 2), giving a unit roundoff of about 2^-48 at a
+// fraction of the cost of float64 FMAs on this GPU (whose FP64 rate is 1/64 of
+// its FP32 rate).  All explicit-rounding intrinsics, so nothing is contracted.
+// Blocks of k vectors are n x k row-major.
 #include <algorithm>
 
 #include "common.cuh"
@@ -19,32 +24,58 @@ namespace {
 constexpr int TS_ROWS = 64;   // rows of Y staged in shared memory per tile
 constexpr int TS_COLS = NT;   // basis columns per CTA (one per thread)
 
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl split(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ dfl split(float x) { return {x, 0.0f}; }
+
+// acc += u * y for double-float u, y (the lo * lo term, ~2^-48 relative, is dropped)
+__device__ __forceinline__ void df_fma(dfl& acc, dfl u, dfl y) {
+  const float ph = __fmul_rn(u.hi, y.hi);
+  float pl = __fmaf_rn(u.hi, y.hi, -ph);  // exact error of the product
+  pl = __fmaf_rn(u.hi, y.lo, pl);
+  pl = __fmaf_rn(u.lo, y.hi, pl);
+  const float s = __fadd_rn(acc.hi, ph);  // two-sum of acc.hi + ph
+  const float bb = __fsub_rn(s, acc.hi);
+  const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  const float t = __fadd_rn(__fadd_rn(e, acc.lo), pl);
+  acc.hi = __fadd_rn(s, t);  // renormalise
+  acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
+}
+
+__device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
 // partial[rc][col][t] = sum over the rows of row-chunk rc of U[col][row] * Y[row][t]
 // U: nb blocks of width su (block-row-major, element TU), Y: n x k row-major float64.
 template <typename TU>
 __global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const TU* __restrict__ U, int64_t bstride,
                                                  int su, int ncol, const double* __restrict__ Y, int k,
                                                  double* __restrict__ partial) {
-  __shared__ double ys[TS_ROWS * 16];
+  __shared__ dfl ys[TS_ROWS * 16];
   const int col = blockIdx.y * TS_COLS + threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = min(n, r0 + rpc);
-  double acc[16];
+  dfl acc[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int t = 0; t < 16; ++t) acc[t] = {0.0f, 0.0f};
   const bool active = col < ncol;
   const int b = active ? col / su : 0, u = active ? col - b * su : 0;
   const TU* Ub = U + (int64_t)b * bstride + u;
   for (int64_t base = r0; base < r1; base += TS_ROWS) {
     const int rows = (int)((r1 - base) < TS_ROWS ? (r1 - base) : TS_ROWS);
     __syncthreads();
-    for (int e = threadIdx.x; e < rows * k; e += NT) ys[e] = Y[base * k + e];
+    for (int e = threadIdx.x; e < rows * k; e += NT) ys[e] = split(Y[base * k + e]);
     __syncthreads();
     if (active) {
       for (int i = 0; i < rows; ++i) {
-        const double uv = (double)Ub[(base + i) * su];
+        const dfl uv = split(Ub[(base + i) * su]);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
-          if (t < k) acc[t] += uv * ys[i * k + t];
+          if (t < k) df_fma(acc[t], uv, ys[i * k + t]);
       }
     }
   }
@@ -52,16 +83,23 @@ __global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const T
     double* out = partial + ((int64_t)blockIdx.x * ncol + col) * k;
 #pragma unroll
     for (int t = 0; t < 16; ++t)
-      if (t < k) out[t] = acc[t];
+      if (t < k) out[t] = to_double(acc[t]);
   }
 }
 
 __global__ void tsg_reduce_kernel(const double* __restrict__ partial, int nrc, int64_t E, double* __restrict__ P) {
   const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (e >= E) return;
-  double v = 0.0;
-  for (int c = 0; c < nrc; ++c) v += partial[(int64_t)c * E + e];
-  P[e] = v;
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads in flight, fixed order
+  int c = 0;
+  for (; c + 3 < nrc; c += 4) {
+    v0 += partial[(int64_t)c * E + e];
+    v1 += partial[(int64_t)(c + 1) * E + e];
+    v2 += partial[(int64_t)(c + 2) * E + e];
+    v3 += partial[(int64_t)(c + 3) * E + e];
+  }
+  for (; c < nrc; ++c) v0 += partial[(int64_t)c * E + e];
+  P[e] = (v0 + v1) + (v2 + v3);
 }
 
 // Z[row][t] = beta * Z[row][t] + alpha * sum_col U[col][row] M[col][t]   (M: ncol x k row-major)
@@ -69,23 +107,23 @@ template <typename TU>
 __global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict__ U, int64_t bstride, int su,
                                                  int ncol, const double* __restrict__ M, int k, double alpha,
                                                  double beta, double* __restrict__ Z) {
-  __shared__ double ms[64 * 16];
+  __shared__ dfl ms[64 * 16];
   const int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x;
-  double acc[16];
+  dfl acc[16];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = 0.0;
+  for (int t = 0; t < 16; ++t) acc[t] = {0.0f, 0.0f};
   for (int c0 = 0; c0 < ncol; c0 += 64) {
     const int cc = min(64, ncol - c0);
     __syncthreads();
-    for (int e = threadIdx.x; e < cc * k; e += NT) ms[e] = M[(int64_t)c0 * k + e];
+    for (int e = threadIdx.x; e < cc * k; e += NT) ms[e] = split(M[(int64_t)c0 * k + e]);
     __syncthreads();
     if (row < n) {
       for (int c = 0; c < cc; ++c) {
         const int col = c0 + c, b = col / su, u = col - b * su;
-        const double uv = (double)U[(int64_t)b * bstride + row * su + u];
+        const dfl uv = split(U[(int64_t)b * bstride + row * su + u]);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
-          if (t < k) acc[t] += uv * ms[c * k + t];
+          if (t < k) df_fma(acc[t], uv, ms[c * k + t]);
       }
     }
   }
@@ -94,7 +132,7 @@ __global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict
     for (int t = 0; t < 16; ++t)
       if (t < k) {
         double* z = Z + row * k + t;
-        *z = (beta == 0.0 ? 0.0 : beta * *z) + alpha * acc[t];
+        *z = (beta == 0.0 ? 0.0 : beta * *z) + alpha * to_double(acc[t]);
       }
   }
 }
@@ -181,15 +219,34 @@ __global__ void trace_prod_kernel(int s, const double* __restrict__ G1, const do
 
 }  // namespace
 
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+int64_t tsg_partial_elems(int64_t ncol, int k) {
+  return ((int64_t)4 * sm_count() + ncol / TS_COLS + 2) * TS_COLS * k;
+}
+
 template <typename TU>
 void launch_tsg(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int su, int nb, const double* Y, int k,
                 double* partial, int max_rc, double* P) {
   const int ncol = nb * su;
   if (ncol == 0) return;
-  int rc = (int)std::min<int64_t>(max_rc, std::max<int64_t>(1, (n + 1023) / 1024));
+  // about four CTAs per SM over (row chunk, column chunk); at least 256 rows per chunk
+  const int cchunks = (ncol + TS_COLS - 1) / TS_COLS;
+  int rc = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256),
+                                  std::max(1, (4 * sm_count() + cchunks - 1) / cchunks));
+  if (max_rc > 0) rc = std::min(rc, max_rc);
   const int64_t rpc = (n + rc - 1) / rc;
   rc = (int)((n + rpc - 1) / rpc);
-  const dim3 g((unsigned)rc, (unsigned)((ncol + TS_COLS - 1) / TS_COLS));
+  const dim3 g((unsigned)rc, (unsigned)cchunks);
   tsg_kernel<TU><<<g, NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, partial);
   const int64_t E = (int64_t)ncol * k;
   tsg_reduce_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(partial, rc, E, P);
