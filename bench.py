@@ -71,8 +71,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/sylv_clocks_{os.getpid()}.csv"
+        out_dir = os.environ.get("SYLV_BENCH_OUT", "/tmp")
+        self.path = os.path.join(out_dir, f"sylv_clocks_{os.getpid()}_{index}.csv")
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -313,6 +313,18 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Max of x over all ranks (replicas: the job is as slow as its slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
 
@@ -354,11 +366,7 @@ def run_ours(args):
     barrier()
     ms_total = e0.elapsed_time(e1)
     clocks = clk.stop()
-    ms_step = ms_total / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_total / args.steps, dist)
     iters = infos[-1]["iters"]
     status = infos[-1]["status_name"]
     launches = int(sum(i["kernel_launches"] for i in infos))
@@ -425,11 +433,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
         d2h = V.nbytes + X.nbytes + W.nbytes
-    e2e_s = statistics.mean(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), dist)
     sv.close()
 
     variants = {}

@@ -40,7 +40,7 @@ def test_convdiff_structure(N, seed):
     assert np.isclose(D[0, 0], 6 + h * 10 * np.abs(w).sum())
 
 
-def test_cfg_sizes():
+def test_convdiff_workload_sizes():
     A = wl.convdiff_3d(64, 1)
     assert A.nrows == 262144 and A.nnz == 1810432
     B = wl.convdiff_3d(48, 2)
@@ -58,7 +58,7 @@ def test_transpose_and_rhs():
     assert np.array_equal(E1, E2)
 
 
-def test_batched_cfg_draws():
+def test_batched_lyapunov_workload_draws():
     probs = wl.cfg_batched_lyapunov(count=64)
     assert len(probs) == 64
     for p in probs:
