@@ -305,6 +305,36 @@ def measure_batched(stream, steps, warmup):
             "plain_fp64_sequential_s": t_seq, "speedup_vs_plain_fp64": t_seq / t_batch}
 
 
+def measure_large(stream, steps, warmup):
+    """Large mixed-precision BiCGSTAB: A = CD 128^3 (n = 2,097,152), B = CD 96^3
+    (m = 884,736), s = 8, tol 1e-8 on the true residual."""
+    import torch
+
+    import paper_2605_28274_gb300 as ps
+
+    p = wl.cfg_convdiff_bicgstab(128, 96, 8, tol=1e-8, maxit=400, precision="mixed")
+    with ps.Solver(p.A, p.B, p.C1, p.C2, precision="mixed", profile=True, cuda_stream=stream.cuda_stream) as sv:
+        for _ in range(warmup):
+            sv.bicgstab(p.tol, p.maxit)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            info = sv.bicgstab(p.tol, p.maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = sv.profile()
+    pk = peaks()
+    hb = [e for e in prof if e["name"] in ("spmm", "gram", "update")]
+    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
+    gbs = hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None
+    return {"workload": "convdiff3d_128^3_x_96^3_s8_bicgstab_mixed", "value": e0.elapsed_time(e1) / steps / 1e3,
+            "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
+            "refinements": info["refinements"], "true_rel_res": info["true_rel_res"], "width": info["width"],
+            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if gbs else None,
+            "kernel_ms_last_solve": {e["name"]: round(e["ms"], 1) for e in sorted(prof, key=lambda e: -e["ms"])}}
+
+
 # ----------------------------------------------------------------------------- our arm
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -441,6 +471,8 @@ def run_ours(args):
         variants["mixed"] = measure_mixed(p, stream, args.steps, 2)
         variants["mixed"]["speedup_vs_fp64"] = (ms_step / 1e3) / variants["mixed"]["value"]
         variants["batched"] = measure_batched(stream, args.steps, 2)
+    if args.large:
+        variants["large_mixed"] = measure_large(stream, 1, 1)
 
     line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -502,6 +534,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--maxit", type=int, default=0, help="override maxit (a short solve, e.g. for ncu captures)")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed and batched variant timings")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the large mixed-precision workload (CD 128^3 x 96^3, s = 8; ~60 GB of HBM)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -496,6 +496,7 @@ sylv::SmallCtx small_ctx(sylv_handle* h) {
   c.ldh = h->lds;
   c.partials = h->psmall;
   c.lyapunov = h->lyap ? 1 : 0;
+  c.df_small = h->mixed ? 1 : 0;  // mixed mode: double-float small products (2^-48), FP64 mode: FP64
   return c;
 }
 
@@ -705,8 +706,7 @@ struct RoundView {
 
 std::vector<RoundView> round_views(const sylv_handle* h) {
   std::vector<RoundView> out;
-  auto add = [&out](const sylv_handle* x) {
-    if (x->width <= 0) return;
+  auto add = [&out](const sylv_handle* x) {  // empty rounds stay (nb = 0) so indices match h->subs
     const Side& a = x->side[0];
     const Side& b = x->side[x->lyap ? 0 : 1];
     out.push_back({a.V, b.V, a.n * x->s, b.n * x->s, (int)x->s, (int)(x->width / x->s), x->Xh, x->lds});
@@ -720,11 +720,12 @@ constexpr int SKK = 8;  // columns of the sketch blocks
 
 // Yout (rows x k) = X Min (trans = false; Min is m x k) or X^T Min (trans = true; Min is n x k).
 template <typename T>
-int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) {
+int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, size_t from_round = 0) {
   int rc = SYLV_OK;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
   auto views = round_views(h);
+  if (from_round > 0) views.erase(views.begin(), views.begin() + std::min(from_round, views.size()));
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
   const int max_rc = 0;  // launch_tsg picks the row chunks
@@ -734,6 +735,7 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) 
   if (rc) return rc;
   bool first = true;
   for (auto& v : views) {
+    if (v.nb <= 0) continue;
     const T* Uin = (const T*)(trans ? v.V : v.W);
     const T* Uout = (const T*)(trans ? v.W : v.V);
     const int64_t bsin = trans ? v.bsV : v.bsW, bsout = trans ? v.bsW : v.bsV;
@@ -752,8 +754,10 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout) 
 }
 
 // Y (n x 8) = R Om (Om m x 8); X is applied once to the 16 columns [Om | B Om].
+// With from_round > 0, Y already holds R_old Om and only the rounds >= from_round
+// (the newest correction dX) are applied: R_new Om = R_old Om - (A dX Om + dX B Om).
 template <typename T>
-int sketch_R(sylv_handle* h, const double* Om, double* Y) {
+int sketch_R(sylv_handle* h, const double* Om, double* Y, size_t from_round = 0) {
   int rc = SYLV_OK;
   const int s = (int)h->s;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
@@ -770,11 +774,17 @@ int sketch_R(sylv_handle* h, const double* Om, double* Y) {
   sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, h->opB.rp, h->opB.ci, h->opB.vald, Om, Tm, nullptr,
                             nullptr, 0);                                                     // B Om
   sylv::launch_interleave(h->stream, m, Om, Tm, M16);
-  TRY(apply_X<T>(h, false, M16, 16, X16));                                                   // X [Om | B Om]
+  TRY(apply_X<T>(h, false, M16, 16, X16, from_round));                                       // X [Om | B Om]
   sylv::launch_deinterleave(h->stream, n, X16, Xa, Xb);
-  sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, Aop.rp, Aop.ci, Aop.vald, Xa, Y, nullptr, nullptr, 0);
-  sylv::launch_neg_sum(h->stream, n * SKK, Y, Xb, Y);                                        // -(A X Om + X B Om)
-  sylv::launch_lowrank_axpy(h->stream, n, s, SKK, h->C1rm, G, 1.0, Y);                       // + C1 (C2^T Om)
+  if (from_round == 0) {
+    sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, Aop.rp, Aop.ci, Aop.vald, Xa, Y, nullptr, nullptr, 0);
+    sylv::launch_neg_sum(h->stream, n * SKK, Y, Xb, Y);                                      // -(A X Om + X B Om)
+    sylv::launch_lowrank_axpy(h->stream, n, s, SKK, h->C1rm, G, 1.0, Y);                     // + C1 (C2^T Om)
+  } else {
+    sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, Aop.rp, Aop.ci, Aop.vald, Xa, X16, nullptr, nullptr, 0);
+    sylv::launch_neg_sum(h->stream, n * SKK, X16, Xb, X16);                                  // -(A dX Om + dX B Om)
+    sylv::launch_axpy(h->stream, n * SKK, 1.0, X16, Y);
+  }
   h->launches += 8;
   return SYLV_OK;
 }
@@ -862,13 +872,21 @@ int sketch_enqueue(sylv_handle* h) {
   }
   const double* Om1 = h->Om;
   const double* Om2 = h->Om + m * SKK;
-  TRY(sketch_R<T>(h, Om1, Q));  // Y = R Om1
+  // R Om1 and R Om2 persist across the refinement rounds of one solve and are updated
+  // with the newest correction only
+  double* RO1 = sk_buf(h, 22, (size_t)n * SKK * sizeof(double), &rc);
+  double* RO2 = sk_buf(h, 23, (size_t)n * SKK * sizeof(double), &rc);
+  if (rc) return rc;
+  const size_t newest = h->subs.size();  // round index of the newest correction (0: none)
+  TRY(sketch_R<T>(h, Om1, RO1, newest));
+  TRY(sketch_R<T>(h, Om2, RO2, newest));
+  CU(cudaMemcpyAsync(Q, RO1, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   qr8(h, n, Q, Rk);
   TRY(sketch_Rt<T>(h, Q, Z));   // Z1 = R^T Q1
   TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1 (a rank-8 range without it is too
   qr8(h, n, Q, Rk);             // poor for the refinement rounds to converge)
   TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
-  TRY(sketch_R<T>(h, Om2, Y3)); // tail probe
+  CU(cudaMemcpyAsync(Y3, RO2, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));  // tail probe
   sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 32, P);
   sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Y3);
   sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
@@ -999,7 +1017,8 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       TRY(make_sub(h, &sub));
       h->subs.push_back(sub);
       sylv_info si;
-      const int src = run_inner<T>(sub, method, tol_c, maxit, &si);
+      // a correction only has to reach tol_c; its basis is sized for at most 100 iterations
+      const int src = run_inner<T>(sub, method, tol_c, std::min(maxit, 100), &si);
       prof_add(h, sub);
       h->launches += sub->launches;
       h->total_iters += sub->iters;

@@ -91,6 +91,7 @@ struct SmallCtx {
   int64_t ldh;
   double* partials;  // per-CTA scratch for the fused reductions
   int lyapunov;
+  int df_small;      // 1: the dense factored operator runs in double-float on the FP32 pipes
 };
 
 // R^_0 = R_L R_R^T, P^_0 = R^_0, R~_0 = R^_0, rho_0, ||R^_0||, history[0] = 1.
@@ -134,6 +135,8 @@ void launch_lowrank_axpy(cudaStream_t, int64_t n, int s, int k, const double* C,
 // out (rows x 16) = [a | b], and back (a, b rows x 8; all row-major).
 void launch_interleave(cudaStream_t, int64_t rows, const double* a, const double* b, double* out);
 void launch_deinterleave(cudaStream_t, int64_t rows, const double* in, double* a, double* b);
+// y += a x element-wise.
+void launch_axpy(cudaStream_t, int64_t count, double a, const double* x, double* y);
 // out = -(X1 + X2) element-wise.
 void launch_neg_sum(cudaStream_t, int64_t count, const double* X1, const double* X2, double* out);
 // out[0] = sum of squares of x (deterministic; ticket must be zero).

@@ -184,6 +184,12 @@ __global__ void deinterleave_kernel(int64_t rows, const double* __restrict__ in,
   else b[r * 8 + c - 8] = in[e];
 }
 
+// y += a * x, element-wise
+__global__ void axpy_kernel(int64_t count, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e < count) y[e] += a * x[e];
+}
+
 // out = -(X1 + X2), element-wise
 __global__ void neg_sum_kernel(int64_t count, const double* __restrict__ X1, const double* __restrict__ X2,
                                double* __restrict__ out) {
@@ -280,6 +286,11 @@ void launch_interleave(cudaStream_t strm, int64_t rows, const double* a, const d
 void launch_deinterleave(cudaStream_t strm, int64_t rows, const double* in, double* a, double* b) {
   if (rows == 0) return;
   deinterleave_kernel<<<(unsigned)((rows * 16 + NT - 1) / NT), NT, 0, strm>>>(rows, in, a, b);
+}
+
+void launch_axpy(cudaStream_t strm, int64_t count, double a, const double* x, double* y) {
+  if (count == 0) return;
+  axpy_kernel<<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, a, x, y);
 }
 
 void launch_neg_sum(cudaStream_t strm, int64_t count, const double* X1, const double* X2, double* out) {

@@ -275,6 +275,137 @@ __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int 
   }
 }
 
+// Double-float variant of sylv_gemm_kernel for the mixed-precision mode: operands are
+// split into hi + lo floats as they are staged in shared memory, products use the
+// error-free FMA product and sums the error-free two-sum (Dekker 1971), so the
+// accumulation runs on the FP32 pipes with a unit roundoff of about 2^-48 (the
+// mixed mode's factors are FP32, 2^-24).  Same tiling, Hessenberg skipping and
+// omega reduction as the float64 kernel.
+struct dfp {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfp dsplit(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ void dfma2(dfp& acc, dfp u, dfp y) {
+  const float ph = __fmul_rn(u.hi, y.hi);
+  float pl = __fmaf_rn(u.hi, y.hi, -ph);
+  pl = __fmaf_rn(u.hi, y.lo, pl);
+  pl = __fmaf_rn(u.lo, y.hi, pl);
+  const float s = __fadd_rn(acc.hi, ph);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  const float t = __fadd_rn(__fadd_rn(e, acc.lo), pl);
+  acc.hi = __fadd_rn(s, t);
+  acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
+}
+
+template <bool OMEGA>
+__global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, int s, const double* __restrict__ H,
+                                                          const double* __restrict__ G, int64_t ldh,
+                                                          const double* __restrict__ Z, double* __restrict__ Out,
+                                                          int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ dfp As[GBK][GBM + 1];
+  __shared__ dfp Bs[GBK][GBM + 1];
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int rp = r + s;
+  const int a0 = blockIdx.x * GBM, b0 = blockIdx.y * GBM;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  dfp acc[2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+  if (b0 < r) {  // (H Z)[a][b], b < r
+    const int clo = max(0, (a0 / s - 1) * s);
+    for (int c0 = clo; c0 < r; c0 += GBK) {
+      for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
+        const int aa = e % GBM, kk = e / GBM;
+        const int a = a0 + aa, c = c0 + kk;
+        As[kk][aa] = dsplit((a < rp && c < r) ? H[a + (int64_t)c * ldh] : 0.0);
+        const int kk2 = e % GBK, bb = e / GBK;
+        const int c2 = c0 + kk2, b = b0 + bb;
+        Bs[kk2][bb] = dsplit((c2 < r && b < r) ? Z[c2 + (int64_t)b * lds] : 0.0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < GBK; ++kk) {
+        const dfp a_0 = As[kk][tx], a_1 = As[kk][tx + 16];
+        const dfp b_0 = Bs[kk][ty], b_1 = Bs[kk][ty + 16];
+        dfma2(acc[0][0], a_0, b_0);
+        dfma2(acc[0][1], a_0, b_1);
+        dfma2(acc[1][0], a_1, b_0);
+        dfma2(acc[1][1], a_1, b_1);
+      }
+      __syncthreads();
+    }
+  }
+  if (a0 < r) {  // (Z G^T)[a][b], a < r
+    const int clo = max(0, (b0 / s - 1) * s);
+    for (int c0 = clo; c0 < r; c0 += GBK) {
+      for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
+        const int aa = e % GBM, kk = e / GBM;
+        const int a = a0 + aa, c = c0 + kk;
+        As[kk][aa] = dsplit((a < r && c < r) ? Z[a + (int64_t)c * lds] : 0.0);
+        const int b = b0 + aa;
+        Bs[kk][aa] = dsplit((b < rp && c < r) ? G[b + (int64_t)c * ldh] : 0.0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < GBK; ++kk) {
+        const dfp a_0 = As[kk][tx], a_1 = As[kk][tx + 16];
+        const dfp b_0 = Bs[kk][ty], b_1 = Bs[kk][ty + 16];
+        dfma2(acc[0][0], a_0, b_0);
+        dfma2(acc[0][1], a_0, b_1);
+        dfma2(acc[1][0], a_1, b_0);
+        dfma2(acc[1][1], a_1, b_1);
+      }
+      __syncthreads();
+    }
+  }
+  double ts = 0.0, tt = 0.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a0 + tx + 16 * i, b = b0 + ty + 16 * j;
+      if (a < rp && b < rp) {
+        const double v = (double)acc[i][j].hi + (double)acc[i][j].lo;
+        Out[a + (int64_t)b * lds] = v;
+        if (OMEGA) {
+          tt += v * v;
+          if (a < r && b < r) ts += v * Z[a + (int64_t)b * lds];
+        }
+      }
+    }
+  if (!OMEGA) return;
+  ts = block_sum(ts, sh);
+  tt = block_sum(tt, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) {
+    partials[2 * bid] = ts;
+    partials[2 * bid + 1] = tt;
+  }
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      s1 += __ldcg(partials + 2 * i);
+      s2 += __ldcg(partials + 2 * i + 1);
+    }
+    if (!isfinite(s1) || !isfinite(s2)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 4;
+    } else if (s2 == 0.0 || s1 == 0.0) {
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 5;
+    } else {
+      st->omega = s1 / s2;
+    }
+  }
+}
+
 // alpha_k = rho_k / <R~_0, Q^(1:s,1:s)>  (one CTA)
 __global__ void bicg_alpha_kernel(DevState* st, int s, const double* __restrict__ Rt, const double* __restrict__ Q,
                                   int64_t lds) {
@@ -400,6 +531,13 @@ void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
 void launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
   const int rp = r + c.s;
   const dim3 gg((rp + GBM - 1) / GBM, (rp + GBM - 1) / GBM);
+  if (c.df_small) {
+    if (omega)
+      sylv_gemm_df_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
+    else
+      sylv_gemm_df_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
+    return;
+  }
   if (omega)
     sylv_gemm_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
   else
