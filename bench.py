@@ -52,15 +52,16 @@ def peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def workload(maxit: int = 0):
-    p = wl.cfg_convdiff_bicgstab(64, 48, 4, tol=1e-8, maxit=maxit or 300)
+def workload(maxit: int = 0, precision: str = "fp64"):
+    p = wl.cfg_convdiff_bicgstab(64, 48, 4, tol=1e-8, maxit=maxit or 300, precision=precision)
     return p
 
 
 def config_of(p):
-    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_fp64", "method": "factorized BiCGSTAB (Algorithm 4.2)",
+    return {"workload": f"convdiff3d_64^3_x_48^3_s4_bicgstab_{p.precision}",
+            "method": "factorized BiCGSTAB (Algorithm 4.2)",
             "n": p.A.nrows, "m": p.B.nrows, "nnzA": p.A.nnz, "nnzB": p.B.nnz, "s": p.s, "tol": p.tol,
-            "maxit": p.maxit, "precision": "fp64",
+            "maxit": p.maxit, "precision": p.precision,
             "l2": "inputs larger than L2: the basis grows to ~2 GB per side per solve (L2 = 126 MB)"}
 
 
@@ -230,39 +231,53 @@ def cpu_baseline(p, iters):
 
 
 # ----------------------------------------------------------------------------- variants
-def measure_mixed(p, stream, steps, warmup):
-    """Same operators and tolerance in the mixed mode (FP32 factors, FP64 small side,
-    FP64 true-residual refinement): time to a TRUE relative residual of p.tol."""
+def profiled_breakdown(p, stream, precision, maxit):
+    """One extra solve with every basis kernel on one stream and CUDA-event timing of
+    each launch (clean per-kernel durations; the timed runs overlap the bases)."""
+    import paper_2605_28274_gb300 as ps
+
+    with ps.Solver(p.A, p.B, p.C1, p.C2, precision=precision, profile=True, stream_mode=1,
+                   cuda_stream=stream.cuda_stream) as sv:
+        sv.bicgstab(p.tol, maxit)
+        prof = sv.profile()
+    pk = peaks()
+    hb = [e for e in prof if e["name"] in ("spmm", "gram", "update")]
+    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
+    gbs = hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None
+    per = {e["name"]: {"ms": round(e["ms"], 2), "launches": e["launches"],
+                       "gbs": round(e["bytes"] / (e["ms"] * 1e-3) / 1e9, 1) if e["ms"] and e["bytes"] else None}
+           for e in sorted(prof, key=lambda e: -e["ms"])}
+    return gbs, (gbs / pk["hbm_gbs"] if gbs else None), per
+
+
+def timed_solves(p, stream, precision, steps, warmup):
     import torch
 
     import paper_2605_28274_gb300 as ps
 
-    with ps.Solver(p.A, p.B, p.C1, p.C2, precision="mixed", profile=True, cuda_stream=stream.cuda_stream) as sv:
+    with ps.Solver(p.A, p.B, p.C1, p.C2, precision=precision, cuda_stream=stream.cuda_stream) as sv:
         for _ in range(warmup):
             sv.bicgstab(p.tol, p.maxit)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        prof = {}
         e0.record(stream)
         for _ in range(steps):
             info = sv.bicgstab(p.tol, p.maxit)
-            for e in sv.profile():
-                d = prof.setdefault(e["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
-                for key in ("launches", "ms", "bytes", "flops"):
-                    d[key] += e[key]
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    pk = peaks()
-    hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
-    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
-    gbs = hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None
-    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_mixed", "value": ms / 1e3, "unit": "s",
+    return e0.elapsed_time(e1) / steps / 1e3, info
+
+
+def measure_mixed(p, stream, steps, warmup):
+    """Same operators and tolerance in the mixed mode (FP32 factors, FP64 small side,
+    FP64 true-residual refinement): time to a TRUE relative residual of p.tol."""
+    t, info = timed_solves(p, stream, "mixed", steps, warmup)
+    gbs, frac, per = profiled_breakdown(p, stream, "mixed", p.maxit)
+    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_mixed", "value": t, "unit": "s",
             "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
             "true_rel_res": info["true_rel_res"], "width": info["width"],
-            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if gbs else None,
-            "kernel_ms_per_solve": {k: round(v["ms"] / steps, 2) for k, v in
-                                    sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
+            "kernel_profile_one_stream": per}
 
 
 def measure_batched(stream, steps, warmup):
@@ -308,31 +323,14 @@ def measure_batched(stream, steps, warmup):
 def measure_large(stream, steps, warmup):
     """Large mixed-precision BiCGSTAB: A = CD 128^3 (n = 2,097,152), B = CD 96^3
     (m = 884,736), s = 8, tol 1e-8 on the true residual."""
-    import torch
-
-    import paper_2605_28274_gb300 as ps
-
     p = wl.cfg_convdiff_bicgstab(128, 96, 8, tol=1e-8, maxit=400, precision="mixed")
-    with ps.Solver(p.A, p.B, p.C1, p.C2, precision="mixed", profile=True, cuda_stream=stream.cuda_stream) as sv:
-        for _ in range(warmup):
-            sv.bicgstab(p.tol, p.maxit)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            info = sv.bicgstab(p.tol, p.maxit)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        prof = sv.profile()
-    pk = peaks()
-    hb = [e for e in prof if e["name"] in ("spmm", "gram", "update")]
-    hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
-    gbs = hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None
-    return {"workload": "convdiff3d_128^3_x_96^3_s8_bicgstab_mixed", "value": e0.elapsed_time(e1) / steps / 1e3,
-            "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
-            "refinements": info["refinements"], "true_rel_res": info["true_rel_res"], "width": info["width"],
-            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": gbs / pk["hbm_gbs"] if gbs else None,
-            "kernel_ms_last_solve": {e["name"]: round(e["ms"], 1) for e in sorted(prof, key=lambda e: -e["ms"])}}
+    t, info = timed_solves(p, stream, "mixed", steps, warmup)
+    gbs, frac, per = profiled_breakdown(p, stream, "mixed", p.maxit)
+    return {"workload": "convdiff3d_128^3_x_96^3_s8_bicgstab_mixed", "value": t, "unit": "s",
+            "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
+            "true_rel_res": info["true_rel_res"], "width": info["width"],
+            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
+            "kernel_profile_one_stream": per}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -367,9 +365,9 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    p = workload(args.maxit)
+    p = workload(args.maxit, args.precision)
     stream = torch.cuda.Stream()
-    sv = ps.Solver(p.A, p.B, p.C1, p.C2, precision="fp64", profile=True, cuda_stream=stream.cuda_stream)
+    sv = ps.Solver(p.A, p.B, p.C1, p.C2, precision=args.precision, profile=True, cuda_stream=stream.cuda_stream)
 
     def barrier():
         if dist is not None:
@@ -403,7 +401,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel class (live CUDA-event timing inside the library)
     pk = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    # dominant kernel class (the residual wrapper and setup are not single kernels)
+    dom = max(((k, v) for k, v in prof.items() if k not in ("true_residual", "setup")), key=lambda kv: kv[1]["ms"])
     dname, d = dom
     ai = d["flops"] / max(d["bytes"], 1.0)
     ridge = FP64_NOMINAL_TFLOPS * 1e12 / (pk["hbm_gbs"] * 1e9)
@@ -457,7 +456,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with ps.Solver(Ap, Bp, C1p, C2p, precision="fp64", cuda_stream=stream.cuda_stream) as sv2:
+        with ps.Solver(Ap, Bp, C1p, C2p, precision=args.precision, cuda_stream=stream.cuda_stream) as sv2:
             inf2 = sv2.bicgstab(p.tol, p.maxit)
             V, X, W = sv2.factors(out={"V": outV, "X": outX, "W": outW})
         torch.cuda.synchronize()
@@ -476,7 +475,7 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(p),
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic", "config": config_of(p),
             "iters": iters, "status": status, "rel_res": infos[-1]["rel_res"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "status": STATUS(inf2)},
@@ -533,6 +532,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--maxit", type=int, default=0, help="override maxit (a short solve, e.g. for ncu captures)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="precision of the timed line (the variants are always measured)")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed and batched variant timings")
     ap.add_argument("--large", action="store_true",
                     help="also time the large mixed-precision workload (CD 128^3 x 96^3, s = 8; ~60 GB of HBM)")

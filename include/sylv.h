@@ -68,6 +68,10 @@ typedef struct {
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a stream owned by the handle */
   int32_t profile;     /* 1: time every kernel launch with CUDA events (see sylv_get_profile) */
   int32_t no_true_residual; /* SYLV_FP64 only: 1 skips the float64 true-residual estimate after the solve */
+  int32_t stream_mode; /* 0: auto (SYLV_MIXED runs the two bases on their own streams, ahead of the small
+                          side; SYLV_FP64 uses one stream, where FP64-bound kernels gain nothing from
+                          overlap); 1: everything on one stream (clean per-kernel profiles); 2: concurrent */
+  int32_t reserved;
 } sylv_options;
 
 typedef struct {

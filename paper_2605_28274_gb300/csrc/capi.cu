@@ -118,13 +118,16 @@ struct sylv_handle {
   DevState* st_host = nullptr;  // pinned, 2 slots
   double* hist = nullptr;
   int hist_cap = 0;
-  double* gpart = nullptr;  // Gram partials
   double* spart = nullptr;  // self-Gram partials
-  double* Hc = nullptr;
   double* psmall = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   Prof prof;
+  cudaStream_t prof_stream = nullptr;  // stream the profiler records on (null: h->stream)
   int64_t launches = 0;  // kernels enqueued by the current solve
+  // the two block Krylov bases run on their own streams, ahead of the small side
+  cudaStream_t sbas[2] = {nullptr, nullptr};
+  double *gpart_s[2] = {nullptr, nullptr}, *spart_s[2] = {nullptr, nullptr}, *Hc_s[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_bas[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, ev_small[8] = {};
   // last solve
   int method = M_NONE;
   int iters = 0;
@@ -283,7 +286,7 @@ cudaEvent_t prof_event(sylv_handle* h) {
 cudaEvent_t prof_begin(sylv_handle* h) {
   if (!h->prof.on) return nullptr;
   cudaEvent_t a = prof_event(h);
-  if (a) cudaEventRecord(a, h->stream);
+  if (a) cudaEventRecord(a, h->prof_stream ? h->prof_stream : h->stream);
   return a;
 }
 
@@ -291,7 +294,7 @@ void prof_end(sylv_handle* h, int cls, double bytes, double flops, cudaEvent_t a
   if (!h->prof.on || !a) return;
   cudaEvent_t b = prof_event(h);
   if (!b) return;
-  cudaEventRecord(b, h->stream);
+  cudaEventRecord(b, h->prof_stream ? h->prof_stream : h->stream);
   h->prof.recs.push_back({cls, h->prof.cur_k, a, b, bytes, flops});
 }
 
@@ -364,9 +367,12 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  TRY(alloc_solve(h, &h->gpart, (size_t)(2 * sms) * maxb * s * s));
   TRY(alloc_solve(h, &h->spart, (size_t)(4 * sms) * 64));
-  TRY(alloc_solve(h, &h->Hc, (size_t)maxb * s * s));
+  for (int i = 0; i < nsides(h); ++i) {
+    TRY(alloc_solve(h, &h->gpart_s[i], (size_t)(4 * sms) * maxb * s * s));
+    TRY(alloc_solve(h, &h->spart_s[i], (size_t)(4 * sms) * 64));
+    TRY(alloc_solve(h, &h->Hc_s[i], (size_t)maxb * s * s));
+  }
   const int64_t gtiles = (h->lds + 31) / 32;
   const size_t psz = std::max<size_t>((size_t)((h->lds + sylv::NT - 1) / sylv::NT) * h->lds, 2 * gtiles * gtiles) + 64;
   TRY(alloc_solve(h, &h->psmall, psz));
@@ -428,7 +434,11 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   T* V = (T*)sd.V;
   T* Vq = V + (int64_t)q * bstride;
   T* Y = V + (int64_t)(q + 1) * bstride;
-  cudaStream_t st = h->stream;
+  cudaStream_t st = h->sbas[si];
+  h->prof_stream = st;
+  double* gpart = h->gpart_s[si];
+  double* spart = h->spart_s[si];
+  double* Hc = h->Hc_s[si];
   int nc;
   // algorithmic bytes: CSR once, gathered block once, result once (+ V_{j-1} for Lanczos)
   const double spmm_bytes = (double)sd.nnz * (4.0 + b) + 4.0 * (n + 1) + 2.0 * ns * b + (lanczos && q >= 1 ? ns * b : 0.0);
@@ -448,13 +458,13 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   }
   const int passes = lanczos ? 1 : 2;  // block Lanczos: one projection; Arnoldi: BCGS2
   for (int pass = 0; pass < passes; ++pass) {
-    PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, h->gpart));
+    PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));
     PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
-         sylv::launch_reduce_H(st, h->st, h->gpart, nc, nb, s, sd.H, ldh, lanczos ? (int64_t)q * s : 0,
-                               (int64_t)q * s, h->Hc, pass == 1));
+         sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, lanczos ? (int64_t)q * s : 0,
+                               (int64_t)q * s, Hc, pass == 1, sizeof(T) == 4));
     const bool last = pass == passes - 1;
     PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
-         nc = sylv::launch_update<T>(st, h->st, n, s, Vfirst, bstride, nb, h->Hc, Y, last ? h->spart : nullptr));
+         nc = sylv::launch_update<T>(st, h->st, n, s, Vfirst, bstride, nb, Hc, Y, last ? spart : nullptr));
   }
   sylv::CholArgs a{};
   a.side = si;
@@ -468,14 +478,15 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   a.RinvT = sd.RinvT;
   a.factor_is_float = h->mixed ? 1 : 0;
   a.pass = 1;
-  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, h->spart, nc, a));
+  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1) + ns * s,
-       nc = sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, h->spart));
+       nc = sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, spart));
   a.pass = 2;
   a.Hsub = sd.H + (int64_t)(q + 1) * s + (int64_t)q * s * ldh;
   a.Hsup = lanczos ? sd.H + (int64_t)q * s + (int64_t)(q + 1) * s * ldh : nullptr;
-  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, h->spart, nc, a));
+  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1), sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr));
+  h->prof_stream = nullptr;
 }
 
 sylv::SmallCtx small_ctx(sylv_handle* h) {
@@ -517,6 +528,19 @@ int wait_status(sylv_handle* h, int slot, double deadline) {
   }
 }
 
+int ensure_streams(sylv_handle* h) {
+  if (h->sbas[0]) return SYLV_OK;
+  for (auto& sb : h->sbas) CU(cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  for (auto& pr : h->ev_bas)
+    for (auto& e : pr) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto& e : h->ev_small) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return SYLV_OK;
+}
+
+// The bases run at most this many iterations ahead of the small side.
+constexpr int kBasisLag = 2;
+
 template <typename T>
 int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
   const double t0 = now_s();
@@ -546,12 +570,44 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   const int poll = h->opt.poll_every > 0 ? h->opt.poll_every : 8;
   int slot = 0, pending = -1;
   bool stopped = false;
+  TRY(ensure_streams(h));
+  const int ns_ = nsides(h);
+  // concurrent bases only where they pay (measured): the mixed mode's memory-bound
+  // basis sweeps overlap the small side; FP64 kernels all compete for the FP64 pipe
+  const int mode = h->opt.stream_mode;
+  const bool concurrent = mode == 2 || (mode == 0 && h->mixed);
+  struct RestoreBasisStreams {  // the handle keeps owning its two streams on every exit path
+    sylv_handle* h;
+    cudaStream_t a, b;
+    ~RestoreBasisStreams() {
+      h->sbas[0] = a;
+      h->sbas[1] = b;
+    }
+  } restore{h, h->sbas[0], h->sbas[1]};
+  if (!concurrent) h->sbas[0] = h->sbas[1] = strm;
+  // fork: the basis streams start after the setup on the main stream
+  CU(cudaEventRecord(h->ev_fork, strm));
+  for (int i = 0; i < ns_; ++i) CU(cudaStreamWaitEvent(h->sbas[i], h->ev_fork, 0));
   const double e8 = 8.0;
+  auto basis_wait_small = [&](int k) -> int {  // throttle: basis of iteration k after small side of k - lag
+    if (k < kBasisLag) return SYLV_OK;
+    for (int i = 0; i < ns_; ++i) CU(cudaStreamWaitEvent(h->sbas[i], h->ev_small[(k - kBasisLag) % 8], 0));
+    return SYLV_OK;
+  };
+  auto small_wait_basis = [&](int which) -> int {  // small side after basis event `which` of every side
+    for (int i = 0; i < ns_; ++i) {
+      CU(cudaEventRecord(h->ev_bas[i][which], h->sbas[i]));
+      CU(cudaStreamWaitEvent(strm, h->ev_bas[i][which], 0));
+    }
+    return SYLV_OK;
+  };
   for (int k = 0; k < maxit && !stopped; ++k) {
     h->prof.cur_k = k;
+    TRY(basis_wait_small(k));
     if (method == M_CG) {
       basis_step<T>(h, 0, k, true);
       if (!h->lyap) basis_step<T>(h, 1, k, true);
+      TRY(small_wait_basis(0));
       const int r = (k + 1) * s, rp = r + s;
       const double r2 = (double)rp * rp;
       const double opflops = 2.0 * 2.0 * r2 * 3.0 * s;
@@ -568,18 +624,21 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
       basis_step<T>(h, 0, 2 * k, false);
       basis_step<T>(h, 1, 2 * k, false);
+      TRY(small_wait_basis(0));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * (double)r1 * r1 + q2), sylv::sylv_gemm_flops(r1, s),
            sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false));
       PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
       PROF(h, KC_SMALL_ELEM, e8 * 3.0 * q2, 2.0 * q2, sylv::launch_bicg_s(strm, c, rp));
       basis_step<T>(h, 0, 2 * k + 1, false);
       basis_step<T>(h, 1, 2 * k + 1, false);
+      TRY(small_wait_basis(1));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + t2), sylv::sylv_gemm_flops(rp, s) + 4.0 * t2,
            sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true));
       PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
            sylv::launch_bicg_update(strm, c, k, rp, rpp));
       PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));
     }
+    CU(cudaEventRecord(h->ev_small[k % 8], strm));
     if ((k + 1) % poll == 0 && k + 1 < maxit) {
       CU(cudaGetLastError());
       TRY(post_status(h, slot));
@@ -592,6 +651,11 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     }
   }
   CU(cudaGetLastError());
+  for (int i = 0; i < ns_; ++i) {  // join the basis streams
+    CU(cudaEventRecord(h->ev_bas[i][0], h->sbas[i]));
+    CU(cudaStreamWaitEvent(strm, h->ev_bas[i][0], 0));
+  }
+
   TRY(post_status(h, slot));
   TRY(wait_status(h, slot, deadline));
   const DevState& ds = h->st_host[slot];
@@ -1614,6 +1678,14 @@ void sylv_destroy(sylv_handle* h) {
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->prof.pool) cudaEventDestroy(e);
+  for (auto& sb : h->sbas)
+    if (sb) cudaStreamDestroy(sb);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  for (auto& pr : h->ev_bas)
+    for (auto& e : pr)
+      if (e) cudaEventDestroy(e);
+  for (auto& e : h->ev_small)
+    if (e) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

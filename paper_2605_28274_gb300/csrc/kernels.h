@@ -23,7 +23,8 @@ void launch_spmm(cudaStream_t, const DevState*, int64_t n, int s, const int32_t*
                  const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm);
 
 // Per-CTA partial Gram products  P_c = sum over the CTA's rows of V_b^T Y  for
-// blocks b = 0..nb-1 (V points at the first block).  Returns the number of CTAs.
+// blocks b = 0..nb-1 (V points at the first block), written in the factor precision T
+// into the (double-sized) partial buffer.  Returns the number of CTAs.
 template <typename T>
 int launch_gram(cudaStream_t, const DevState*, int64_t n, int s, const T* V, int64_t bstride, int nb,
                 const T* Y, double* partial);
@@ -31,7 +32,7 @@ int launch_gram(cudaStream_t, const DevState*, int64_t n, int s, const T* V, int
 // Sum the partials in a fixed order: Hc[e] = sum_c partial[c][e], e < nb*s*s, and
 // store (add) the nb*s x s result into H at (row0, col0) (column-major, ld ldh).
 void launch_reduce_H(cudaStream_t, const DevState*, const double* partial, int ncta, int nb, int s, double* H,
-                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add);
+                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add, bool float_partials);
 
 // Y -= [V_0 .. V_{nb-1}] Hc  (Hc: nb*s x s row-major).  With self_partial != NULL also
 // writes per-CTA partials of Y^T Y.  Returns the number of CTAs.

@@ -134,16 +134,18 @@ __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n,
 template <typename T, int S>
 __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n, int64_t rpc, const T* __restrict__ V,
                                                   int64_t bstride, int nb, const T* __restrict__ Y,
-                                                  double* __restrict__ partial) {
+                                                  T* __restrict__ partial) {
   if (stopped(st)) return;
-  __shared__ double sh[(NT / 32) * S * S];
+  // partials stay in the factor precision (float in the mixed mode): converting them
+  // to double here would occupy GB300's narrow FP64 pipe; the reduce kernel does it
+  __shared__ T sh[(NT / 32) * S * S];
   using A = typename AccOf<T>::type;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = NT / 32;
   const int64_t r0 = (int64_t)blockIdx.x * rpc;
   const int64_t r1 = min(n, r0 + rpc);
   const int slices = nb >= nw ? 1 : nw / nb;
   const int ntasks = nb * slices;
-  double* out = partial + (int64_t)blockIdx.x * nb * S * S;
+  T* out = partial + (int64_t)blockIdx.x * nb * S * S;
   for (int task = w; task < ntasks; task += nw) {
     const int b = task / slices, sl = task - b * slices;
     const T* Vb = V + (int64_t)b * bstride;
@@ -190,9 +192,9 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int e = u * S + t;
         if (slices == 1) {
-          if (l == (e & 31)) out[b * S * S + e] = (double)v;
+          if (l == (e & 31)) out[b * S * S + e] = (T)v;
         } else {
-          if (l == (e & 31)) sh[task * S * S + e] = (double)v;
+          if (l == (e & 31)) sh[task * S * S + e] = (T)v;
         }
       }
   }
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
     __syncthreads();
     for (int e = threadIdx.x; e < nb * S * S; e += NT) {
       const int b = e / (S * S), r = e - b * S * S;
-      double s = 0.0;
+      T s = 0;
       for (int sl = 0; sl < slices; ++sl) s += sh[(b * slices + sl) * S * S + r];
       out[e] = s;
     }
@@ -212,7 +214,8 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
 // instead of one dependent add chain), combined in a fixed order.
 constexpr int RED_NT = 64;
 
-__global__ void __launch_bounds__(RED_NT) reduce_H_kernel(const DevState* st, const double* __restrict__ partial,
+template <typename P>
+__global__ void __launch_bounds__(RED_NT) reduce_H_kernel(const DevState* st, const P* __restrict__ partial,
                                                           int ncta, int nb, int s, double* __restrict__ H,
                                                           int64_t ldh, int64_t row0, int64_t col0,
                                                           double* __restrict__ Hc, int add) {
@@ -223,12 +226,12 @@ __global__ void __launch_bounds__(RED_NT) reduce_H_kernel(const DevState* st, co
   double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
   int c = 0;
   for (; c + 3 < ncta; c += 4) {
-    v0 += partial[(int64_t)c * E + e];
-    v1 += partial[(int64_t)(c + 1) * E + e];
-    v2 += partial[(int64_t)(c + 2) * E + e];
-    v3 += partial[(int64_t)(c + 3) * E + e];
+    v0 += (double)partial[(int64_t)c * E + e];
+    v1 += (double)partial[(int64_t)(c + 1) * E + e];
+    v2 += (double)partial[(int64_t)(c + 2) * E + e];
+    v3 += (double)partial[(int64_t)(c + 3) * E + e];
   }
-  for (; c < ncta; ++c) v0 += partial[(int64_t)c * E + e];
+  for (; c < ncta; ++c) v0 += (double)partial[(int64_t)c * E + e];
   const double v = (v0 + v1) + (v2 + v3);
   Hc[e] = v;
   const int b = e / (s * s), r = e - b * s * s, u = r / s, t = r - u * s;
@@ -528,21 +531,27 @@ int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T
                 const T* Y, double* partial) {
   // FP64 is bound by the FP64 pipe: one CTA per SM keeps the per-task warp
   // reductions (s*s shuffle+add steps) small next to the row loop.  FP32 is bound
-  // by HBM: two CTAs per SM for more loads in flight.
-  const int grid = grid_for(n, 64, (sizeof(T) == 8 ? 1 : 2) * num_sms());
+  // by HBM latency: four CTAs per SM for more loads in flight.  The partials are
+  // written in the factor precision (T), read by launch_reduce_H<T>.
+  const int grid = grid_for(n, 64, (sizeof(T) == 8 ? 1 : 4) * num_sms());
   const int64_t rpc = (n + grid - 1) / grid;
+  T* tpart = reinterpret_cast<T*>(partial);
 #define CASE(SV) \
-  case SV: gram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, partial); break;
+  case SV: gram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, tpart); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
   return grid;
 }
 
 void launch_reduce_H(cudaStream_t strm, const DevState* st, const double* partial, int ncta, int nb, int s, double* H,
-                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add) {
+                     int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add, bool float_partials) {
   const int E = nb * s * s;
-  reduce_H_kernel<<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc,
-                                                                  add ? 1 : 0);
+  if (float_partials)
+    reduce_H_kernel<float><<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(
+        st, reinterpret_cast<const float*>(partial), ncta, nb, s, H, ldh, row0, col0, Hc, add ? 1 : 0);
+  else
+    reduce_H_kernel<double><<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0,
+                                                                            col0, Hc, add ? 1 : 0);
 }
 
 template <typename T>
