@@ -702,9 +702,12 @@ double* sk_buf(sylv_handle* h, size_t idx, size_t bytes, int* rc) {
   if (h->sk.size() <= idx) h->sk.resize(idx + 1, {nullptr, 0});
   auto& b = h->sk[idx];
   if (b.second < bytes) {
+    // grow geometrically: every cudaFree synchronises the device
     if (b.first) cudaFree(b.first);
     b.first = nullptr;
     b.second = 0;
+    bytes = std::max(bytes, (size_t)(1.5 * (double)bytes));
+    if (bytes < (1u << 20)) bytes = 1u << 20;
     cudaError_t e = cudaMalloc(&b.first, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();

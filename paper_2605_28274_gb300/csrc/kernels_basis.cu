@@ -209,34 +209,39 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
   }
 }
 
-// Fixed-order sum of the per-CTA partials: 64-thread CTAs (more SMs busy for small
-// nb*s*s) and four independent accumulators over interleaved CTAs (loads in flight
-// instead of one dependent add chain), combined in a fixed order.
-constexpr int RED_NT = 64;
+// Fixed-order sum of the per-CTA partials.  A CTA covers 32 outputs; its 8 warps
+// split each output's partials (warp g takes CTAs g, g+8, ...), so every thread has
+// only ncta/8 loads in its chain, and the 8 group sums are added in a fixed order.
+constexpr int RED_E = 32, RED_G = 8;
 
 template <typename P>
-__global__ void __launch_bounds__(RED_NT) reduce_H_kernel(const DevState* st, const P* __restrict__ partial,
-                                                          int ncta, int nb, int s, double* __restrict__ H,
-                                                          int64_t ldh, int64_t row0, int64_t col0,
-                                                          double* __restrict__ Hc, int add) {
+__global__ void __launch_bounds__(RED_E * RED_G) reduce_H_kernel(const DevState* st, const P* __restrict__ partial,
+                                                                 int ncta, int nb, int s, double* __restrict__ H,
+                                                                 int64_t ldh, int64_t row0, int64_t col0,
+                                                                 double* __restrict__ Hc, int add) {
   if (stopped(st)) return;
+  __shared__ double part[RED_G][RED_E];
   const int E = nb * s * s;
-  const int e = blockIdx.x * RED_NT + threadIdx.x;
-  if (e >= E) return;
-  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-  int c = 0;
-  for (; c + 3 < ncta; c += 4) {
-    v0 += (double)partial[(int64_t)c * E + e];
-    v1 += (double)partial[(int64_t)(c + 1) * E + e];
-    v2 += (double)partial[(int64_t)(c + 2) * E + e];
-    v3 += (double)partial[(int64_t)(c + 3) * E + e];
+  const int el = threadIdx.x % RED_E, g = threadIdx.x / RED_E;
+  const int e = blockIdx.x * RED_E + el;
+  double v0 = 0.0, v1 = 0.0;
+  if (e < E) {
+    int c = g;
+    for (; c + RED_G < ncta; c += 2 * RED_G) {
+      v0 += (double)partial[(int64_t)c * E + e];
+      v1 += (double)partial[(int64_t)(c + RED_G) * E + e];
+    }
+    if (c < ncta) v0 += (double)partial[(int64_t)c * E + e];
   }
-  for (; c < ncta; ++c) v0 += (double)partial[(int64_t)c * E + e];
-  const double v = (v0 + v1) + (v2 + v3);
-  Hc[e] = v;
+  part[g][el] = v0 + v1;
+  __syncthreads();
+  if (g != 0 || e >= E) return;
+  double vs = 0.0;
+  for (int q = 0; q < RED_G; ++q) vs += part[q][el];
+  Hc[e] = vs;
   const int b = e / (s * s), r = e - b * s * s, u = r / s, t = r - u * s;
   double* h = H + (row0 + (int64_t)b * s + u) + (col0 + t) * ldh;
-  *h = add ? (*h + v) : v;
+  *h = add ? (*h + vs) : vs;
 }
 
 // ---------------------------------------------------------------- block update
@@ -396,12 +401,25 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
     __syncthreads();
   }
   double hsq = 0.0;
-  if (a.pass == 1 && a.Hcol != nullptr) {
-    for (int64_t i = threadIdx.x; i < a.hrows * s; i += NT) {
-      const int64_t rr = i % a.hrows, cc = i / a.hrows;
-      const double h = a.Hcol[rr + cc * a.ldh];
-      hsq += h * h;
+  if (a.pass == 1 && a.Hcol != nullptr) {  // ||H_{1:j,j}||^2, four independent chains per thread
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
+    const int64_t tot = a.hrows * s;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * NT < tot; i += 4 * NT) {
+      const double x0 = a.Hcol[(i % a.hrows) + (i / a.hrows) * a.ldh];
+      const double x1 = a.Hcol[((i + NT) % a.hrows) + ((i + NT) / a.hrows) * a.ldh];
+      const double x2 = a.Hcol[((i + 2 * NT) % a.hrows) + ((i + 2 * NT) / a.hrows) * a.ldh];
+      const double x3 = a.Hcol[((i + 3 * NT) % a.hrows) + ((i + 3 * NT) / a.hrows) * a.ldh];
+      h0 += x0 * x0;
+      h1 += x1 * x1;
+      h2 += x2 * x2;
+      h3 += x3 * x3;
     }
+    for (; i < tot; i += NT) {
+      const double x = a.Hcol[(i % a.hrows) + (i / a.hrows) * a.ldh];
+      h0 += x * x;
+    }
+    hsq = (h0 + h1) + (h2 + h3);
   }
   hsq = block_sum(hsq, sh);
   if (threadIdx.x == 0) {
@@ -546,12 +564,13 @@ int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T
 void launch_reduce_H(cudaStream_t strm, const DevState* st, const double* partial, int ncta, int nb, int s, double* H,
                      int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add, bool float_partials) {
   const int E = nb * s * s;
+  const int grid = (E + RED_E - 1) / RED_E;
   if (float_partials)
-    reduce_H_kernel<float><<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(
-        st, reinterpret_cast<const float*>(partial), ncta, nb, s, H, ldh, row0, col0, Hc, add ? 1 : 0);
+    reduce_H_kernel<float><<<grid, RED_E * RED_G, 0, strm>>>(st, reinterpret_cast<const float*>(partial), ncta, nb, s,
+                                                             H, ldh, row0, col0, Hc, add ? 1 : 0);
   else
-    reduce_H_kernel<double><<<(E + RED_NT - 1) / RED_NT, RED_NT, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0,
-                                                                            col0, Hc, add ? 1 : 0);
+    reduce_H_kernel<double><<<grid, RED_E * RED_G, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc,
+                                                              add ? 1 : 0);
 }
 
 template <typename T>
