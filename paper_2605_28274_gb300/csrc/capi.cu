@@ -73,11 +73,13 @@ enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2 };
 // Kernel classes timed by the optional profiler.
 enum KClass {
   KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_SCALE, KC_SETUP,
-  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_RESID_TSG, KC_RESID_TSU, KC_NUM
+  KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_RESID_TSG, KC_RESID_TSU, KC_RESID_SMALL,
+  KC_RESID_SPMM, KC_RESID_QR, KC_RESID_MISC, KC_NUM
 };
 const char* const kKcNames[KC_NUM] = {"spmm",         "gram",  "reduce_h",   "update",           "cholqr_chol",
                                       "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise",
-                                      "true_residual", "resid_tsg", "resid_tsu"};
+                                      "true_residual", "resid_tsg", "resid_tsu", "resid_small", "resid_spmm",
+                                      "resid_qr", "resid_misc"};
 
 struct Prof {
   struct Rec {
@@ -810,7 +812,7 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
     const double fl = 2.0 * (double)r * k;
     PROF(h, KC_RESID_TSG, (double)rows_in * (r * sizeof(T) + k * 8.0), fl * rows_in,
          sylv::launch_tsg<T>(h->stream, rows_in, Uin, bsin, v.s, v.nb, Min, k, part, max_rc, P));
-    sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2);
+    PROF(h, KC_RESID_SMALL, 0.0, 2.0 * r * r * k, sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2));
     PROF(h, KC_RESID_TSU, (double)rows_out * (r * sizeof(T) + 2.0 * k * 8.0), fl * rows_out,
          sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, k, 1.0, first ? 0.0 : 1.0, Yout));
     h->launches += 2;
@@ -829,7 +831,7 @@ int sketch_R(sylv_handle* h, const double* Om, double* Y, size_t from_round = 0)
   const int s = (int)h->s;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
   double* G = sk_buf(h, 3, 64 * SKK * sizeof(double), &rc);
-  double* part = sk_buf(h, 4, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  double* part = sk_buf(h, 4, (size_t)sylv::tsg_partial_elems(64, 16) * sizeof(double), &rc);
   double* Tm = sk_buf(h, 5, (size_t)m * SKK * sizeof(double), &rc);
   double* Xa = sk_buf(h, 6, (size_t)n * SKK * sizeof(double), &rc);
   double* Xb = sk_buf(h, 7, (size_t)n * SKK * sizeof(double), &rc);
@@ -837,10 +839,11 @@ int sketch_R(sylv_handle* h, const double* Om, double* Y, size_t from_round = 0)
   double* X16 = sk_buf(h, 21, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
   if (rc) return rc;
   const Side& Aop = h->side[0];
-  sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, Om, SKK, part, 32, G);       // C2^T Om
-  sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, h->opB.rp, h->opB.ci, h->opB.vald, Om, Tm, nullptr,
-                            nullptr, 0);                                                     // B Om
-  sylv::launch_interleave(h->stream, m, Om, Tm, M16);
+  sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, Om, SKK, part, 0, G);       // C2^T Om
+  PROF(h, KC_RESID_SPMM, 0.0, 0.0,
+       sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, h->opB.rp, h->opB.ci, h->opB.vald, Om, Tm, nullptr,
+                                 nullptr, 0));                                               // B Om
+  PROF(h, KC_RESID_MISC, 0.0, 0.0, sylv::launch_interleave(h->stream, m, Om, Tm, M16));
   TRY(apply_X<T>(h, false, M16, 16, X16, from_round));                                       // X [Om | B Om]
   sylv::launch_deinterleave(h->stream, n, X16, Xa, Xb);
   if (from_round == 0) {
@@ -863,7 +866,7 @@ int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
   const int s = (int)h->s;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
   double* G = sk_buf(h, 3, 64 * SKK * sizeof(double), &rc);
-  double* part = sk_buf(h, 4, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  double* part = sk_buf(h, 4, (size_t)sylv::tsg_partial_elems(64, 16) * sizeof(double), &rc);
   double* Tn = sk_buf(h, 8, (size_t)n * SKK * sizeof(double), &rc);
   double* Za = sk_buf(h, 9, (size_t)m * SKK * sizeof(double), &rc);
   double* Zb = sk_buf(h, 10, (size_t)m * SKK * sizeof(double), &rc);
@@ -871,10 +874,11 @@ int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
   double* X16 = sk_buf(h, 21, (size_t)std::max(n, m) * 16 * sizeof(double), &rc);
   if (rc) return rc;
   const Side& Bt = h->side[h->lyap ? 0 : 1];  // B^T
-  sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, Q, SKK, part, 32, G);        // C1^T Q
-  sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, h->opAt.rp, h->opAt.ci, h->opAt.vald, Q, Tn, nullptr,
-                            nullptr, 0);                                                     // A^T Q
-  sylv::launch_interleave(h->stream, n, Tn, Q, M16);
+  sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, Q, SKK, part, 0, G);        // C1^T Q
+  PROF(h, KC_RESID_SPMM, 0.0, 0.0,
+       sylv::launch_spmm<double>(h->stream, nullptr, n, SKK, h->opAt.rp, h->opAt.ci, h->opAt.vald, Q, Tn, nullptr,
+                                 nullptr, 0));                                               // A^T Q
+  PROF(h, KC_RESID_MISC, 0.0, 0.0, sylv::launch_interleave(h->stream, n, Tn, Q, M16));
   TRY(apply_X<T>(h, true, M16, 16, X16));                                                    // X^T [A^T Q | Q]
   sylv::launch_deinterleave(h->stream, m, X16, Za, Zb);
   sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, Bt.rp, Bt.ci, Bt.vald, Zb, Z, nullptr, nullptr, 0);
@@ -885,7 +889,11 @@ int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
 }
 
 // In-place CholQR2 of an n x 8 float64 block (status in st_sk).
+void qr8_impl(sylv_handle* h, int64_t n, double* Y, double* Rout);
 void qr8(sylv_handle* h, int64_t n, double* Y, double* Rout) {
+  PROF(h, KC_RESID_QR, 0.0, 0.0, qr8_impl(h, n, Y, Rout));
+}
+void qr8_impl(sylv_handle* h, int64_t n, double* Y, double* Rout) {
   double* R1 = Rout + 64;
   double* Rinv = Rout + 128;
   double* RinvT = Rout + 192;
@@ -923,7 +931,7 @@ int sketch_enqueue(sylv_handle* h) {
   double* sums = sk_buf(h, 15, 8 * sizeof(double), &rc);
   double* part = sk_buf(h, 16, (size_t)256 * sizeof(double) + 64, &rc);
   double* P = sk_buf(h, 17, 64 * sizeof(double), &rc);
-  double* part2 = sk_buf(h, 18, (size_t)32 * 64 * SKK * sizeof(double), &rc);
+  double* part2 = sk_buf(h, 18, (size_t)sylv::tsg_partial_elems(64, 16) * sizeof(double), &rc);
   if (rc) return rc;
   unsigned int* ticket = (unsigned int*)(part + 256);
   CU(cudaMemsetAsync(h->st_sk, 0, sizeof(DevState), h->stream));
@@ -932,8 +940,8 @@ int sketch_enqueue(sylv_handle* h) {
     // ||C1 C2^T||_F^2 = tr((C1^T C1)(C2^T C2))
     double* G1 = sk_buf(h, 19, 128 * sizeof(double), &rc);
     if (rc) return rc;
-    sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, h->C1rm, s, part2, 32, G1);
-    sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, h->C2rm, s, part2, 32, G1 + 64);
+    sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, h->C1rm, s, part2, 0, G1);
+    sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, h->C2rm, s, part2, 0, G1 + 64);
     sylv::launch_trace_prod(h->stream, s, G1, G1 + 64, sums + 2);
     h->launches += 5;
   }
@@ -954,7 +962,7 @@ int sketch_enqueue(sylv_handle* h) {
   qr8(h, n, Q, Rk);             // poor for the refinement rounds to converge)
   TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
   CU(cudaMemcpyAsync(Y3, RO2, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));  // tail probe
-  sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 32, P);
+  sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 0, P);
   sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Y3);
   sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
   sylv::launch_sumsq(h->stream, n * SKK, Y3, part, ticket + 1, sums + 1);

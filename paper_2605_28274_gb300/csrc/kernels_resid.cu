@@ -35,11 +35,7 @@ __device__ __forceinline__ dfl split(double x) {
 __device__ __forceinline__ dfl split(float x) { return {x, 0.0f}; }
 
 // acc += u * y for double-float u, y (the lo * lo term, ~2^-48 relative, is dropped)
-__device__ __forceinline__ void df_fma(dfl& acc, dfl u, dfl y) {
-  const float ph = __fmul_rn(u.hi, y.hi);
-  float pl = __fmaf_rn(u.hi, y.hi, -ph);  // exact error of the product
-  pl = __fmaf_rn(u.hi, y.lo, pl);
-  pl = __fmaf_rn(u.lo, y.hi, pl);
+__device__ __forceinline__ void df_acc(dfl& acc, float ph, float pl) {
   const float s = __fadd_rn(acc.hi, ph);  // two-sum of acc.hi + ph
   const float bb = __fsub_rn(s, acc.hi);
   const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
@@ -47,17 +43,38 @@ __device__ __forceinline__ void df_fma(dfl& acc, dfl u, dfl y) {
   acc.hi = __fadd_rn(s, t);  // renormalise
   acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
 }
+__device__ __forceinline__ void df_fma(dfl& acc, dfl u, dfl y) {
+  const float ph = __fmul_rn(u.hi, y.hi);
+  float pl = __fmaf_rn(u.hi, y.hi, -ph);  // exact error of the product
+  pl = __fmaf_rn(u.hi, y.lo, pl);
+  pl = __fmaf_rn(u.lo, y.hi, pl);
+  df_acc(acc, ph, pl);
+}
+// a float u is exact in one word: no u.lo term
+__device__ __forceinline__ void df_fma(dfl& acc, float u, dfl y) {
+  const float ph = __fmul_rn(u, y.hi);
+  float pl = __fmaf_rn(u, y.hi, -ph);
+  pl = __fmaf_rn(u, y.lo, pl);
+  df_acc(acc, ph, pl);
+}
+
+__device__ __forceinline__ dfl load_df(const double* p) { return split(*p); }
+__device__ __forceinline__ float load_df(const float* p) { return *p; }
 
 __device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 
 // partial[rc][col][t] = sum over the rows of row-chunk rc of U[col][row] * Y[row][t]
 // U: nb blocks of width su (block-row-major, element TU), Y: n x k row-major float64.
+// A CTA covers cw columns (a power of two); with cw < NT its NT / cw thread slots split
+// the rows of each tile (row i goes to slot i mod nslot) and are summed in slot order.
 template <typename TU>
 __global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const TU* __restrict__ U, int64_t bstride,
-                                                 int su, int ncol, const double* __restrict__ Y, int k,
+                                                 int su, int ncol, const double* __restrict__ Y, int k, int cw,
                                                  double* __restrict__ partial) {
   __shared__ dfl ys[TS_ROWS * 16];
-  const int col = blockIdx.y * TS_COLS + threadIdx.x;
+  __shared__ double red[NT * 16];
+  const int nslot = NT / cw, cl = threadIdx.x % cw, slot = threadIdx.x / cw;
+  const int col = blockIdx.y * cw + cl;
   const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = min(n, r0 + rpc);
   dfl acc[16];
 #pragma unroll
@@ -71,19 +88,33 @@ __global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const T
     for (int e = threadIdx.x; e < rows * k; e += NT) ys[e] = split(Y[base * k + e]);
     __syncthreads();
     if (active) {
-      for (int i = 0; i < rows; ++i) {
-        const dfl uv = split(Ub[(base + i) * su]);
+      for (int i = slot; i < rows; i += nslot) {
+        const auto uv = load_df(Ub + (base + i) * su);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
           if (t < k) df_fma(acc[t], uv, ys[i * k + t]);
       }
     }
   }
-  if (active) {
-    double* out = partial + ((int64_t)blockIdx.x * ncol + col) * k;
+  if (nslot == 1) {
+    if (active) {
+      double* out = partial + ((int64_t)blockIdx.x * ncol + col) * k;
 #pragma unroll
-    for (int t = 0; t < 16; ++t)
-      if (t < k) out[t] = to_double(acc[t]);
+      for (int t = 0; t < 16; ++t)
+        if (t < k) out[t] = to_double(acc[t]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 16; ++t) red[threadIdx.x * 16 + t] = to_double(acc[t]);
+  __syncthreads();
+  if (slot == 0 && active) {
+    double* out = partial + ((int64_t)blockIdx.x * ncol + col) * k;
+    for (int t = 0; t < k; ++t) {
+      double v = 0.0;
+      for (int q = 0; q < nslot; ++q) v += red[(q * cw + cl) * 16 + t];
+      out[t] = v;
+    }
   }
 }
 
@@ -120,7 +151,7 @@ __global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict
     if (row < n) {
       for (int c = 0; c < cc; ++c) {
         const int col = c0 + c, b = col / su, u = col - b * su;
-        const dfl uv = split(U[(int64_t)b * bstride + row * su + u]);
+        const auto uv = load_df(U + (int64_t)b * bstride + row * su + u);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
           if (t < k) df_fma(acc[t], uv, ms[c * k + t]);
@@ -138,17 +169,42 @@ __global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict
 }
 
 // out (r x k, row-major) = op(Xh) * in (r x k row-major), op = identity or transpose; Xh ld lds.
-__global__ void small_apply_kernel(int r, int k, const double* __restrict__ Xh, int64_t lds, int trans,
-                                   const double* __restrict__ in, double* __restrict__ out) {
-  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
-  if (e >= (int64_t)r * k) return;
-  const int i = (int)(e / k), t = (int)(e - (int64_t)i * k);
+// A CTA owns 16 output rows x 16 columns; tiles of op(Xh) (16 x 64) and of in (64 x 16)
+// are staged in shared memory, so the dependent chain per output runs on shared loads.
+__global__ void __launch_bounds__(NT) small_apply_kernel(int r, int k, const double* __restrict__ Xh, int64_t lds,
+                                                         int trans, const double* __restrict__ in,
+                                                         double* __restrict__ out) {
+  __shared__ double xs[16][65];
+  __shared__ double is[64][17];
+  const int ti = threadIdx.x >> 4, tt = threadIdx.x & 15;
+  const int i0 = blockIdx.x * 16;
+  const int i = i0 + ti;
   double acc = 0.0;
-  if (!trans)
-    for (int c = 0; c < r; ++c) acc += Xh[i + (int64_t)c * lds] * in[(int64_t)c * k + t];
-  else
-    for (int c = 0; c < r; ++c) acc += Xh[c + (int64_t)i * lds] * in[(int64_t)c * k + t];
-  out[e] = acc;
+  for (int c0 = 0; c0 < r; c0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * 64; e += NT) {
+      int a, cc;
+      if (!trans) {  // Xh[i + c*lds]: contiguous in i
+        a = e % 16;
+        cc = e / 16;
+      } else {       // Xh[c + i*lds]: contiguous in c
+        cc = e % 64;
+        a = e / 64;
+      }
+      const int ii = i0 + a, c = c0 + cc;
+      double x = 0.0;
+      if (ii < r && c < r) x = trans ? Xh[c + (int64_t)ii * lds] : Xh[ii + (int64_t)c * lds];
+      xs[a][cc] = x;
+    }
+    for (int e = threadIdx.x; e < 64 * 16; e += NT) {
+      const int cc = e / 16, t = e % 16, c = c0 + cc;
+      is[cc][t] = (c < r && t < k) ? in[(int64_t)c * k + t] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int cc = 0; cc < 64; ++cc) acc += xs[ti][cc] * is[cc][tt];
+  }
+  if (i < r && tt < k) out[(int64_t)i * k + tt] = acc;
 }
 
 // Y (n x k row-major) = alpha * Y + C (n x s row-major) * G (s x k row-major)
@@ -245,15 +301,18 @@ void launch_tsg(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int 
                 double* partial, int max_rc, double* P) {
   const int ncol = nb * su;
   if (ncol == 0) return;
-  // about four CTAs per SM over (row chunk, column chunk); at least 256 rows per chunk
-  const int cchunks = (ncol + TS_COLS - 1) / TS_COLS;
+  // cw columns per CTA (narrow blocks: fewer columns, more row slots); about four CTAs
+  // per SM over (row chunk, column chunk); at least 256 rows per chunk
+  int cw = 1;
+  while (cw < ncol && cw < TS_COLS) cw <<= 1;
+  const int cchunks = (ncol + cw - 1) / cw;
   int rc = (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256),
                                   std::max(1, (4 * sm_count() + cchunks - 1) / cchunks));
   if (max_rc > 0) rc = std::min(rc, max_rc);
   const int64_t rpc = (n + rc - 1) / rc;
   rc = (int)((n + rpc - 1) / rpc);
   const dim3 g((unsigned)rc, (unsigned)cchunks);
-  tsg_kernel<TU><<<g, NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, partial);
+  tsg_kernel<TU><<<g, NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, cw, partial);
   const int64_t E = (int64_t)ncol * k;
   tsg_reduce_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(partial, rc, E, P);
 }
@@ -268,9 +327,8 @@ void launch_tsu(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int 
 
 void launch_small_apply(cudaStream_t strm, int r, int k, const double* Xh, int64_t lds, bool trans, const double* in,
                         double* out) {
-  const int64_t E = (int64_t)r * k;
-  if (E == 0) return;
-  small_apply_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(r, k, Xh, lds, trans ? 1 : 0, in, out);
+  if (r == 0 || k == 0) return;
+  small_apply_kernel<<<(unsigned)((r + 15) / 16), NT, 0, strm>>>(r, k, Xh, lds, trans ? 1 : 0, in, out);
 }
 
 void launch_lowrank_axpy(cudaStream_t strm, int64_t n, int s, int k, const double* C, const double* G, double alpha,
