@@ -353,6 +353,24 @@ def max_over_ranks(x: float, dist=None) -> float:
     return float(t.item())
 
 
+def nvtx_push(name):
+    try:
+        import torch
+
+        torch.cuda.nvtx.range_push(name)
+    except Exception:  # NVTX is a profiling aid only
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def run_ours(args):
     import torch
 
@@ -381,6 +399,7 @@ def run_ours(args):
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos, prof = [], {}
+    nvtx_push("timed")  # lets a profiler restrict its launch list to the timed solves
     e0.record(stream)
     for _ in range(args.steps):
         info = sv.bicgstab(p.tol, p.maxit)
@@ -391,6 +410,7 @@ def run_ours(args):
                 d[key] += e[key]
     e1.record(stream)
     torch.cuda.synchronize()
+    nvtx_pop()
     barrier()
     ms_total = e0.elapsed_time(e1)
     clocks = clk.stop()

@@ -122,6 +122,9 @@ struct sylv_handle {
   int hist_cap = 0;
   double* spart = nullptr;  // self-Gram partials
   double* psmall = nullptr;
+  // mixed mode: hi/lo float pairs of H, G and of the small operand (8 bytes per entry)
+  double *Hs = nullptr, *Gs = nullptr, *Zs = nullptr;
+  int split_cols = 0;  // columns of H, G split so far in this solve
   cudaEvent_t ev[2] = {nullptr, nullptr};
   Prof prof;
   cudaStream_t prof_stream = nullptr;  // stream the profiler records on (null: h->stream)
@@ -198,6 +201,7 @@ void free_solve(sylv_handle* h) {
     sd.V = nullptr;
     sd.H = nullptr;
   }
+  h->Hs = h->Gs = h->Zs = nullptr;
 }
 
 int check_csr(const sylv_csr* M, const char* name, int64_t expect_n) {
@@ -378,6 +382,11 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   const int64_t gtiles = (h->lds + 31) / 32;
   const size_t psz = std::max<size_t>((size_t)((h->lds + sylv::NT - 1) / sylv::NT) * h->lds, 2 * gtiles * gtiles) + 64;
   TRY(alloc_solve(h, &h->psmall, psz));
+  if (h->mixed) {
+    TRY(alloc_solve(h, &h->Hs, l2));
+    if (!h->lyap) TRY(alloc_solve(h, &h->Gs, l2));
+    TRY(alloc_solve(h, &h->Zs, l2));
+  }
   h->maxb = maxb;
   h->hist_cap = hist_need;
   h->cap_method = method;
@@ -510,6 +519,10 @@ sylv::SmallCtx small_ctx(sylv_handle* h) {
   c.partials = h->psmall;
   c.lyapunov = h->lyap ? 1 : 0;
   c.df_small = h->mixed ? 1 : 0;  // mixed mode: double-float small products (2^-48), FP64 mode: FP64
+  c.Hs = h->Hs;
+  c.Gs = h->lyap ? h->Hs : h->Gs;
+  c.Zs = h->Zs;
+  c.split_cols = &h->split_cols;
   return c;
 }
 
@@ -555,9 +568,12 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), strm));
   const size_t l2 = (size_t)(h->lds * h->lds) * sizeof(double);
   for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th}) CU(cudaMemsetAsync(p, 0, l2, strm));
-  for (int i = 0; i < nsides(h); ++i) {
-    CU(cudaMemsetAsync(h->side[i].H, 0, l2, strm));
-    }
+  for (int i = 0; i < nsides(h); ++i) CU(cudaMemsetAsync(h->side[i].H, 0, l2, strm));
+  if (h->mixed) {  // split copies of H, G follow H's zero fill
+    CU(cudaMemsetAsync(h->Hs, 0, l2, strm));
+    if (!h->lyap) CU(cudaMemsetAsync(h->Gs, 0, l2, strm));
+  }
+  h->split_cols = 0;
   prof_reset(h);
   h->launches = 0;
   for (int i = 0; i < nsides(h); ++i) {
@@ -628,14 +644,14 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       basis_step<T>(h, 1, 2 * k, false);
       TRY(small_wait_basis(0));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * (double)r1 * r1 + q2), sylv::sylv_gemm_flops(r1, s),
-           sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false));
+           h->launches += sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false) - 1);
       PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
       PROF(h, KC_SMALL_ELEM, e8 * 3.0 * q2, 2.0 * q2, sylv::launch_bicg_s(strm, c, rp));
       basis_step<T>(h, 0, 2 * k + 1, false);
       basis_step<T>(h, 1, 2 * k + 1, false);
       TRY(small_wait_basis(1));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + t2), sylv::sylv_gemm_flops(rp, s) + 4.0 * t2,
-           sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true));
+           h->launches += sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true) - 1);
       PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
            sylv::launch_bicg_update(strm, c, k, rp, rpp));
       PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));

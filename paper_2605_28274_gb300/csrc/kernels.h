@@ -93,6 +93,10 @@ struct SmallCtx {
   double* partials;  // per-CTA scratch for the fused reductions
   int lyapunov;
   int df_small;      // 1: the dense factored operator runs in double-float on the FP32 pipes
+  // df_small only: hi/lo float pairs of H, G (ld ldh; Gs == Hs in the Lyapunov case) and of
+  // the operand Z (ld lds); *split_cols = columns of H and G already split in this solve
+  void *Hs, *Gs, *Zs;
+  int* split_cols;
 };
 
 // R^_0 = R_L R_R^T, P^_0 = R^_0, R~_0 = R^_0, rho_0, ||R^_0||, history[0] = 1.
@@ -108,7 +112,8 @@ void launch_cg_p(cudaStream_t, const SmallCtx&, int rp);
 
 // Algorithm 4.2 pieces.  Out = [H Z, 0] + [Z G^T; 0] with Z of extent r (block upper
 // Hessenberg H, G); with omega also reduces <Out(1:r,1:r), Z>, <Out, Out> and sets omega.
-void launch_sylv_gemm(cudaStream_t, const SmallCtx&, int r, const double* Z, double* Out, bool omega);
+// Returns the number of kernels launched.
+int launch_sylv_gemm(cudaStream_t, const SmallCtx&, int r, const double* Z, double* Out, bool omega);
 double sylv_gemm_flops(int r, int s);
 void launch_bicg_alpha(cudaStream_t, const SmallCtx&);
 void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);

@@ -303,11 +303,25 @@ __device__ __forceinline__ void dfma2(dfp& acc, dfp u, dfp y) {
   acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
 }
 
+// Hi/lo split of the columns [c0, c1) of a column-major matrix (rows 0..rows-1, ld ld).
+__global__ void __launch_bounds__(NT) split_cols_kernel(const DevState* st, int rows, int c0, int c1,
+                                                        const double* __restrict__ M, int64_t ld,
+                                                        dfp* __restrict__ out) {
+  if (stopped(st)) return;
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (e >= (int64_t)rows * (c1 - c0)) return;
+  const int a = (int)(e % rows);
+  const int64_t c = c0 + e / rows;
+  out[a + c * ld] = dsplit(M[a + c * ld]);
+}
+
+// The operands arrive split (Hs, Gs, Zs: the hi/lo pairs of H, G, Z, same layouts), so
+// the inner loop runs on the FP32 pipes only; Z itself is read for the omega sums.
 template <bool OMEGA>
-__global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, int s, const double* __restrict__ H,
-                                                          const double* __restrict__ G, int64_t ldh,
-                                                          const double* __restrict__ Z, double* __restrict__ Out,
-                                                          int64_t lds, double* partials) {
+__global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, int s, const dfp* __restrict__ Hs,
+                                                          const dfp* __restrict__ Gs, int64_t ldh,
+                                                          const dfp* __restrict__ Zs, const double* __restrict__ Z,
+                                                          double* __restrict__ Out, int64_t lds, double* partials) {
   if (stopped(st)) return;
   __shared__ dfp As[GBK][GBM + 1];
   __shared__ dfp Bs[GBK][GBM + 1];
@@ -323,10 +337,10 @@ __global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, i
       for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
         const int aa = e % GBM, kk = e / GBM;
         const int a = a0 + aa, c = c0 + kk;
-        As[kk][aa] = dsplit((a < rp && c < r) ? H[a + (int64_t)c * ldh] : 0.0);
+        As[kk][aa] = (a < rp && c < r) ? Hs[a + (int64_t)c * ldh] : dfp{0.0f, 0.0f};
         const int kk2 = e % GBK, bb = e / GBK;
         const int c2 = c0 + kk2, b = b0 + bb;
-        Bs[kk2][bb] = dsplit((c2 < r && b < r) ? Z[c2 + (int64_t)b * lds] : 0.0);
+        Bs[kk2][bb] = (c2 < r && b < r) ? Zs[c2 + (int64_t)b * lds] : dfp{0.0f, 0.0f};
       }
       __syncthreads();
 #pragma unroll 4
@@ -347,9 +361,9 @@ __global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, i
       for (int e = threadIdx.x; e < GBK * GBM; e += NT) {
         const int aa = e % GBM, kk = e / GBM;
         const int a = a0 + aa, c = c0 + kk;
-        As[kk][aa] = dsplit((a < r && c < r) ? Z[a + (int64_t)c * lds] : 0.0);
+        As[kk][aa] = (a < r && c < r) ? Zs[a + (int64_t)c * lds] : dfp{0.0f, 0.0f};
         const int b = b0 + aa;
-        Bs[kk][aa] = dsplit((b < rp && c < r) ? G[b + (int64_t)c * ldh] : 0.0);
+        Bs[kk][aa] = (b < rp && c < r) ? Gs[b + (int64_t)c * ldh] : dfp{0.0f, 0.0f};
       }
       __syncthreads();
 #pragma unroll 4
@@ -528,20 +542,39 @@ void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
   cg_p_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, rp, c.Ph, c.Rh, c.lds);
 }
 
-void launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
+int launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
   const int rp = r + c.s;
   const dim3 gg((rp + GBM - 1) / GBM, (rp + GBM - 1) / GBM);
   if (c.df_small) {
+    dfp* Hs = (dfp*)c.Hs;
+    dfp* Gs = (dfp*)c.Gs;
+    dfp* Zs = (dfp*)c.Zs;
+    // columns of H and G are final once written: split only those added since the last call
+    int launched = 2;
+    if (*c.split_cols < r) {
+      const int c0 = *c.split_cols;
+      const int64_t E = (int64_t)rp * (r - c0);
+      split_cols_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(c.st, rp, c0, r, c.H, c.ldh, Hs);
+      launched += 1;
+      if (c.G != c.H) {
+        split_cols_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(c.st, rp, c0, r, c.G, c.ldh, Gs);
+        launched += 1;
+      }
+      *c.split_cols = r;
+    }
+    const int64_t EZ = (int64_t)r * r;
+    split_cols_kernel<<<(unsigned)((EZ + NT - 1) / NT), NT, 0, strm>>>(c.st, r, 0, r, Z, c.lds, Zs);
     if (omega)
-      sylv_gemm_df_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
+      sylv_gemm_df_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, c.partials);
     else
-      sylv_gemm_df_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
-    return;
+      sylv_gemm_df_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, nullptr);
+    return launched;
   }
   if (omega)
     sylv_gemm_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
   else
     sylv_gemm_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
+  return 1;
 }
 
 double sylv_gemm_flops(int r, int s) {
