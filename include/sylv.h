@@ -71,7 +71,10 @@ typedef struct {
   int32_t stream_mode; /* 0: auto (SYLV_MIXED runs the two bases on their own streams, ahead of the small
                           side; SYLV_FP64 uses one stream, where FP64-bound kernels gain nothing from
                           overlap); 1: everything on one stream (clean per-kernel profiles); 2: concurrent */
-  int32_t reserved;
+  int32_t small_gemm;  /* products of the small Sylvester operator, eq. 3.7, in BiCGSTAB: 0 auto (tensor
+                          cores from order r = 448 on), 1 CUDA cores only (float64, or double-float in
+                          SYLV_MIXED), 2 tensor cores at every order; the tensor-core form splits both
+                          factors into BF16 digits (Ozaki scheme) and keeps float64 accuracy */
 } sylv_options;
 
 typedef struct {

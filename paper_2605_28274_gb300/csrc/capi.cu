@@ -125,6 +125,7 @@ struct sylv_handle {
   // mixed mode: hi/lo float pairs of H, G and of the small operand (8 bytes per entry)
   double *Hs = nullptr, *Gs = nullptr, *Zs = nullptr;
   int split_cols = 0;  // columns of H, G split so far in this solve
+  void* oz_scratch = nullptr;  // digit planes of the tensor-core small products
   cudaEvent_t ev[2] = {nullptr, nullptr};
   Prof prof;
   cudaStream_t prof_stream = nullptr;  // stream the profiler records on (null: h->stream)
@@ -202,6 +203,7 @@ void free_solve(sylv_handle* h) {
     sd.H = nullptr;
   }
   h->Hs = h->Gs = h->Zs = nullptr;
+  h->oz_scratch = nullptr;
 }
 
 int check_csr(const sylv_csr* M, const char* name, int64_t expect_n) {
@@ -348,8 +350,13 @@ void prof_finish(sylv_handle* h, int iters) {
   } while (0)
 
 // Device buffers sized for `maxb` basis blocks per side.
+// Order r from which the small Sylvester operator runs on the tensor cores (option small_gemm = 0).
+constexpr int kOzakiMinR = 448;  // measured crossover with the CUDA-core float64 kernel
+
 int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
-  if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE) return SYLV_OK;
+  const bool want_oz = method == M_BICG && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
+  if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE && (!want_oz || h->oz_scratch))
+    return SYLV_OK;
   free_solve(h);
   const int64_t s = h->s;
   const size_t fsz = h->mixed ? sizeof(float) : sizeof(double);
@@ -386,6 +393,13 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
     TRY(alloc_solve(h, &h->Hs, l2));
     if (!h->lyap) TRY(alloc_solve(h, &h->Gs, l2));
     TRY(alloc_solve(h, &h->Zs, l2));
+  }
+  // tensor-core small products: the dense (Arnoldi) operator only, once it is large enough
+  if (want_oz) {
+    if (!sylv::ozaki_setup()) return fail(SYLV_ECUDA, "tensor-core kernel setup");
+    unsigned char* p = nullptr;
+    TRY(alloc_solve(h, &p, sylv::ozaki_scratch_bytes((int)ldh)));
+    h->oz_scratch = p;
   }
   h->maxb = maxb;
   h->hist_cap = hist_need;
@@ -523,6 +537,8 @@ sylv::SmallCtx small_ctx(sylv_handle* h) {
   c.Gs = h->lyap ? h->Hs : h->Gs;
   c.Zs = h->Zs;
   c.split_cols = &h->split_cols;
+  c.oz_scratch = h->oz_scratch;
+  c.oz_min_r = h->opt.small_gemm == 2 ? 1 : kOzakiMinR;
   return c;
 }
 
@@ -687,6 +703,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     case sylv::ST_CONVERGED: rc = SYLV_OK; break;
     case sylv::ST_RUNNING: rc = SYLV_ENOTCONV; break;
     case sylv::ST_BREAKDOWN: rc = SYLV_EBREAKDOWN; g_err = "breakdown (site " + std::to_string(ds.breakdown_where) + ")"; break;
+    case sylv::ST_WAIT_TIMEOUT: rc = SYLV_ETIMEOUT; g_err = "a device-side wait gave up (site " + std::to_string(ds.breakdown_where) + ")"; break;
     default: rc = SYLV_ENONFINITE; g_err = "non-finite value (site " + std::to_string(ds.breakdown_where) + ")"; break;
   }
   if (maxit == 0 && ds.status == sylv::ST_RUNNING) rc = SYLV_ENOTCONV;
@@ -1312,7 +1329,8 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     x->nblocks = ds.iters + 1;
     int rc = ds.status == sylv::ST_CONVERGED ? SYLV_OK
              : ds.status == sylv::ST_RUNNING ? SYLV_ENOTCONV
-             : ds.status == sylv::ST_BREAKDOWN ? SYLV_EBREAKDOWN : SYLV_ENONFINITE;
+             : ds.status == sylv::ST_BREAKDOWN ? SYLV_EBREAKDOWN
+             : ds.status == sylv::ST_WAIT_TIMEOUT ? SYLV_ETIMEOUT : SYLV_ENONFINITE;
     x->status = rc;
     x->true_rel = -1.0;
     if (agg == SYLV_OK && rc != SYLV_OK) agg = rc;

@@ -12,7 +12,9 @@
 
 namespace sylv {
 
-enum DevStatus : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3 };
+// ST_WAIT_TIMEOUT: a kernel's bounded wait on its own asynchronous copies or tensor-core
+// operations gave up (the kernel returned without its result).
+enum DevStatus : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_NONFINITE = 3, ST_WAIT_TIMEOUT = 4 };
 
 // Tickets for the "last CTA finishes the reduction" pattern, one per kernel kind.
 enum Ticket : int {

@@ -97,6 +97,10 @@ struct SmallCtx {
   // the operand Z (ld lds); *split_cols = columns of H and G already split in this solve
   void *Hs, *Gs, *Zs;
   int* split_cols;
+  // tensor-core products (Ozaki splitting) for operand orders r >= oz_min_r; oz_scratch holds
+  // ozaki_scratch_bytes(ldh) bytes (null: never)
+  void* oz_scratch;
+  int oz_min_r;
 };
 
 // R^_0 = R_L R_R^T, P^_0 = R^_0, R~_0 = R^_0, rho_0, ||R^_0||, history[0] = 1.
@@ -114,6 +118,11 @@ void launch_cg_p(cudaStream_t, const SmallCtx&, int rp);
 // Hessenberg H, G); with omega also reduces <Out(1:r,1:r), Z>, <Out, Out> and sets omega.
 // Returns the number of kernels launched.
 int launch_sylv_gemm(cudaStream_t, const SmallCtx&, int r, const double* Z, double* Out, bool omega);
+// The same operator in float64 accuracy on the tcgen05 tensor cores (kernels_ozaki.cu).
+size_t ozaki_scratch_bytes(int rmax);
+bool ozaki_setup();  // once per device: opt-in to the kernel's shared-memory size
+int launch_sylv_gemm_ozaki(cudaStream_t, DevState* st, int r, int s, const double* H, const double* G, int64_t ldh,
+                           const double* Z, double* Out, int64_t lds, bool omega, void* scratch);
 double sylv_gemm_flops(int r, int s);
 void launch_bicg_alpha(cudaStream_t, const SmallCtx&);
 void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);

@@ -1,0 +1,448 @@
+// Float64 products of the small Sylvester operator on the tensor cores (Ozaki scheme I).
+//
+// The operator Q^ = [H P^, 0] + [P^ G^T; 0] of Algorithms 4.1/4.2 (eq. 3.7) is a dense
+// contraction of order r (block upper Hessenberg H, G).  GB300 runs float64 FMAs at 1/64 of
+// its FP32 rate, so the float64 kernel is bound by the FP64 pipe.  Here both factors are
+// split exactly into BF16 integer digits and multiplied on the tcgen05 tensor cores:
+//
+//   x = 2^e * sum_{p=1..8} d_p 2^{-7p}   (e: exponent of the row's largest |x|; d_1 in
+//                                         [-128, 128], d_p in [-64, 64]: exact in BF16)
+//   (A B)_{ab} = 2^{e_a + f_b} sum_{p+q <= 9} 2^{-7(p+q)} (D^A_p D^B_q)_{ab}
+//
+// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication and its applications", Numer. Algorithms 59, 2012;
+// its tensor-core form: Mukunoki, Ozaki, Ogita, Imamura, ICCS 2020.)  Each digit product is
+// an integer; the products of one level l = p + q over 128 values of k are below 2^23 in
+// magnitude, so the FP32 accumulation in tensor memory is exact.  After every 128 values of
+// k the eight level sums are added, as integers, into two int64 fixed-point accumulators
+// (levels 2..5 in units of 2^-35, levels 6..9 in units of 2^-63; neither can overflow for
+// k <= 2^13): the whole sum is exact, and the only rounding is the epilogue's conversion to
+// float64.  The result differs from the exact product only by the digits dropped with the
+// pairs p + q > 9, below 2^-56 of (max |row of A|)(max |column of B|) per term.
+//
+// Digits are stored in the canonical no-swizzle K-major layout of the tcgen05 shared-memory
+// matrix descriptor (8-row x 16-byte core matrices), one 128 x 64 (A) or 64 x 64 (B) block
+// per (digit, row tile, k chunk), so plain 1-D bulk copies (cp.async.bulk) load each block.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sylv {
+
+namespace {
+
+constexpr int OZ_P = 8;               // digits per operand
+constexpr int OZ_L = OZ_P + 1;        // pairs with p + q <= OZ_L are kept
+constexpr int OZ_NLEV = OZ_L - 1;     // levels 2..OZ_L
+constexpr int OZ_TM = 128;            // output rows per CTA (MMA M)
+constexpr int OZ_TN = 64;             // output columns per CTA (MMA N)
+constexpr int OZ_KC = 64;             // k per loaded chunk
+constexpr int OZ_FOLD = 2;            // chunks per fold (128 values of k)
+constexpr int OZ_ABLK = OZ_TM * OZ_KC;  // BF16 elements of one A digit block (16 KB)
+constexpr int OZ_BBLK = OZ_TN * OZ_KC;  // BF16 elements of one B digit block (8 KB)
+constexpr int OZ_THREADS = 256;     // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; each takes half the columns
+constexpr int OZ_CPT = OZ_TN / 2;    // output columns per thread
+constexpr int OZ_TMEM_COLS = OZ_NLEV * OZ_TN;  // one FP32 accumulator tile per level
+static_assert(OZ_TMEM_COLS == 512, "tensor memory holds 512 columns");
+constexpr int OZ_EXP_BAD = 1 << 20;   // exponent sentinel: the row holds a non-finite value
+constexpr int OZ_OMEGA_CTAS = 1024;  // grid of the omega reduction (its partials live in the scratch)
+constexpr int OZ_WAIT_ITERS = 1 << 20;
+constexpr size_t OZ_SMEM = (size_t)OZ_P * (OZ_ABLK + OZ_BBLK) * 2 + 2048;  // + 1 KB alignment, barriers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices adjacent in k), stride byte offset (between 8-row groups).
+__device__ __forceinline__ uint64_t oz_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture family
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+constexpr uint32_t oz_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Offset (in BF16 elements) of element (i, k) inside one T x 64 digit block.
+__device__ __forceinline__ int oz_in_block(int i, int k) {
+  return (((i >> 3) * (OZ_KC / 8) + (k >> 3)) << 6) + ((i & 7) << 3) + (k & 7);
+}
+
+// mx[i] = max_k |x(i, k)| as IEEE bits (non-negative doubles order like their bit patterns);
+// x(i, k) = X[i * si + k * sk], i < R, k < K.  A CTA covers 32 rows x 64 values of k (8 per
+// thread) and combines into mx (zeroed beforehand) with atomicMax: the result does not depend
+// on the order.
+__global__ void __launch_bounds__(NT) oz_max_kernel(const DevState* st, const double* __restrict__ X, int64_t si,
+                                                    int64_t sk, int R, int K, unsigned long long* __restrict__ mx) {
+  if (stopped(st)) return;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int k0 = blockIdx.y * 64 + (threadIdx.x >> 5) * 8;
+  if (i >= R) return;
+  unsigned long long m = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = k0 + j;
+    if (k < K)
+      m = max(m, (unsigned long long)__double_as_longlong(X[(int64_t)i * si + (int64_t)k * sk]) & 0x7FFFFFFFFFFFFFFFull);
+  }
+  if (m) atomicMax(mx + i, m);
+}
+
+// e = 1 + floor(log2 m) (0 for a zero or subnormal-only row, OZ_EXP_BAD for a non-finite one)
+__device__ __forceinline__ int oz_exponent(unsigned long long m) {
+  if (m >= 0x7FF0000000000000ull) return OZ_EXP_BAD;
+  if (m < 0x0010000000000000ull) return 0;
+  return (int)(m >> 52) - 1023 + 1;
+}
+
+// Digits of x(i, k) for one row i and 8 consecutive k: thread per (i, k group).  Writes the
+// 8 digit planes, each as one 16-byte core-matrix row.  Layout of a plane: blocks
+// [row tile][k chunk] of T x 64, T = rows per tile.
+__global__ void __launch_bounds__(NT) oz_split_kernel(const DevState* st, const double* __restrict__ X, int64_t si,
+                                                      int64_t sk, int R, int K, int Rp, int Kp, int T,
+                                                      const unsigned long long* __restrict__ mx,
+                                                      int* __restrict__ ex, __nv_bfloat16* __restrict__ dig,
+                                                      int64_t plane) {
+  if (stopped(st)) return;
+  const int kg_n = Kp / 8;
+  const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (t >= (int64_t)Rp * kg_n) return;
+  const int i = (int)(t % Rp), kg = (int)(t / Rp);  // consecutive threads: consecutive rows
+  const int e = i < R ? oz_exponent(mx[i]) : 0;
+  if (kg == 0) ex[i] = e;
+  long long Nv[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int k = kg * 8 + j;
+    double x = 0.0;
+    if (i < R && k < K && e != OZ_EXP_BAD) x = X[(int64_t)i * si + (int64_t)k * sk];
+    // |x| < 2^e, so |x 2^{56-e}| < 2^56: an exact integer after rounding
+    Nv[j] = (e == OZ_EXP_BAD) ? 0 : __double2ll_rn(scalbn(x, 56 - e));
+  }
+  const int nkc = Kp / OZ_KC;
+  const int64_t blk = ((int64_t)(i / T) * nkc + (kg * 8) / OZ_KC) * ((int64_t)T * OZ_KC);
+  const int inb = oz_in_block(i % T, (kg * 8) % OZ_KC);
+#pragma unroll
+  for (int p = 1; p <= OZ_P; ++p) {
+    const int sh = 7 * (OZ_P - p);
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      long long d;
+      if (sh > 0) {
+        d = (Nv[j] + (1ll << (sh - 1))) >> sh;  // nearest multiple of 2^sh (ties up)
+        Nv[j] -= d << sh;
+      } else {
+        d = Nv[j];
+      }
+      v[j] = __float2bfloat16_rn((float)d);  // |d| <= 128: exact
+    }
+    *reinterpret_cast<uint4*>(dig + (int64_t)(p - 1) * plane + blk + inb) = *reinterpret_cast<const uint4*>(v);
+  }
+}
+
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t phase) {
+  for (int it = 0; it < OZ_WAIT_ITERS; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// v: an FP32 level sum, an exact integer below 2^22 in magnitude.  Its integer value comes
+// from the bits of v + 1.5 * 2^23 (exact for |v| < 2^22).
+__device__ __forceinline__ int oz_int(float v) {
+  return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000;
+}
+
+// Out[a + b*ldo] (= or +=) 2^{e_a + f_b} sum_k A(a, k) B(b, k) over the tile's k range.
+// A digits: planes of Mp x Kp (tiles of 128 rows), B digits: Np x Kp (tiles of 64 rows).
+// hess: 0 all k chunks; 1 start at the block-Hessenberg bound of the tile's first row
+// (A = H); 2 the same for the tile's first column (B = G^T).  Valid outputs a < Mv, b < Nv.
+// A wait that gives up sets the solve status to ST_WAIT_TIMEOUT.
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
+    DevState* st, const __nv_bfloat16* __restrict__ Ad, int64_t planeA, const __nv_bfloat16* __restrict__ Bd,
+    int64_t planeB, int nkc, const int* __restrict__ ea, const int* __restrict__ fb, int hess, int s, double* Out,
+    int64_t ldo, int Mv, int Nv, int add) {
+  if (stopped(st)) return;
+  extern __shared__ __align__(1024) unsigned char oz_smem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
+  __nv_bfloat16* sA = (__nv_bfloat16*)base;                       // 8 x 16 KB
+  __nv_bfloat16* sB = sA + (size_t)OZ_P * OZ_ABLK;                // 8 x 8 KB
+  uint64_t* bars = (uint64_t*)(sB + (size_t)OZ_P * OZ_BBLK);      // [0] loads, [1] MMAs
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int a0 = mt * OZ_TM, b0 = nt * OZ_TN;
+
+  int kc0 = 0;
+  if (hess == 1) kc0 = max(0, (a0 / s - 1) * s) / OZ_KC;
+  if (hess == 2) kc0 = max(0, (b0 / s - 1) * s) / OZ_KC;
+  // fold periods start at even chunks, so each covers at most OZ_FOLD chunks
+  kc0 -= kc0 % OZ_FOLD;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  const int quarter = warp & 3, col0 = (warp >> 2) * OZ_CPT;  // TMEM lanes 32 quarter .., columns col0 ..
+  long long w1[OZ_CPT], w2[OZ_CPT];  // levels 2..5 (unit 2^-35) and 6..9 (unit 2^-63)
+#pragma unroll
+  for (int j = 0; j < OZ_CPT; ++j) w1[j] = w2[j] = 0;
+
+  const uint32_t id = oz_idesc(OZ_TM, OZ_TN);
+  const uint32_t lbo = 128, sbo = (OZ_KC / 8) * 128;
+  const uint32_t abytes = OZ_ABLK * 2, bbytes = OZ_BBLK * 2;
+  uint32_t phase = 0;
+  bool ok = true;
+  uint32_t stuck_bar = 0;  // barrier whose wait gave up (0: none)
+  for (int kc = kc0; kc < nkc && ok; ++kc) {
+    const bool first_of_fold = ((kc - kc0) % OZ_FOLD) == 0;
+    const bool last_of_fold = ((kc - kc0) % OZ_FOLD) == OZ_FOLD - 1 || kc == nkc - 1;
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
+                   "r"(OZ_P * (abytes + bbytes))
+                   : "memory");
+#pragma unroll 1
+      for (int p = 0; p < OZ_P; ++p) {
+        const __nv_bfloat16* ga = Ad + (int64_t)p * planeA + ((int64_t)mt * nkc + kc) * OZ_ABLK;
+        const __nv_bfloat16* gb = Bd + (int64_t)p * planeB + ((int64_t)nt * nkc + kc) * OZ_BBLK;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sA + (size_t)p * OZ_ABLK)),
+            "l"(ga), "r"(abytes), "r"(bar_ld)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sB + (size_t)p * OZ_BBLK)),
+            "l"(gb), "r"(bbytes), "r"(bar_ld)
+            : "memory");
+      }
+    }
+    ok = __syncthreads_and(oz_wait(bar_ld, phase));
+    if (!ok) {
+      stuck_bar = bar_ld;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      // level l = p + q accumulates in TMEM columns (l - 2) * 64 ..; its first MMA of a fold
+      // period overwrites (p = 1 comes first for every level)
+#pragma unroll 1
+      for (int p = 1; p <= OZ_P; ++p) {
+#pragma unroll 1
+        for (int q = 1; q <= OZ_L - p; ++q) {
+          const uint32_t dcol = tmem + (uint32_t)((p + q - 2) * OZ_TN);
+#pragma unroll 1
+          for (int ks = 0; ks < OZ_KC / 16; ++ks) {
+            const uint64_t da = oz_sdesc(smem_u32(sA + (size_t)(p - 1) * OZ_ABLK) + ks * 256, lbo, sbo);
+            const uint64_t db = oz_sdesc(smem_u32(sB + (size_t)(q - 1) * OZ_BBLK) + ks * 256, lbo, sbo);
+            const uint32_t acc = (first_of_fold && p == 1 && ks == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(dcol),
+                "l"(da), "l"(db), "r"(id), "r"(acc)
+                : "memory");
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                   : "memory");
+    }
+    ok = __syncthreads_and(oz_wait(bar_mma, phase));
+    if (!ok) {
+      stuck_bar = bar_mma;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (last_of_fold) {
+#pragma unroll
+      for (int l = 2; l <= OZ_L; ++l) {
+        const int sh = l <= 5 ? 7 * (5 - l) : 7 * (9 - l);
+#pragma unroll
+        for (int c = 0; c < OZ_CPT; c += 16) {
+          uint32_t r[16];
+          const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((l - 2) * OZ_TN + col0 + c);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const long long t = (long long)((unsigned long long)(long long)oz_int(__uint_as_float(r[j])) << sh);
+            if (l <= 5)
+              w1[c + j] += t;
+            else
+              w2[c + j] += t;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // shared buffers and tensor memory are free for the next chunk
+  }
+
+  if (ok) {
+    const int a = a0 + quarter * 32 + lane;
+    if (a < Mv) {
+      const int e = ea[a];
+#pragma unroll
+      for (int j = 0; j < OZ_CPT; ++j) {
+        const int b = b0 + col0 + j;
+        if (b < Nv) {
+          const int f = fb[b];
+          const int x = e + f;  // 2^x as a float64 (x outside the normal range: 0 or inf)
+          const double sc = x < -1022 ? 0.0 : (x > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
+                                                        : __longlong_as_double((long long)(x + 1023) << 52));
+          double v = fma((double)w1[j], 0x1p-35, (double)w2[j] * 0x1p-63) * sc;
+          if (e == OZ_EXP_BAD || f == OZ_EXP_BAD) v = __longlong_as_double(0x7FF8000000000000ll);
+          double* o = Out + a + (int64_t)b * ldo;
+          *o = add ? (*o + v) : v;
+        }
+      }
+    }
+  } else {
+    if (tid == 0) {
+      st->breakdown_where = 200;
+      atomicExch(&st->status, (int)ST_WAIT_TIMEOUT);
+    }
+    // copies or MMAs that timed out may still be in flight: a second bounded wait before
+    // the shared memory and the tensor memory are given up
+    oz_wait(stuck_bar, phase);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+}
+
+// <Out(1:r,1:r), Z> and <Out, Out> over the rp x rp extent; the last CTA sets omega.
+__global__ void __launch_bounds__(NT) oz_omega_kernel(DevState* st, int r, int rp, const double* __restrict__ Out,
+                                                      const double* __restrict__ Z, int64_t lds,
+                                                      double* __restrict__ partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  double ts = 0.0, tt = 0.0;
+  const int64_t E = (int64_t)rp * rp;
+  for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < E; e += (int64_t)gridDim.x * NT) {
+    const int a = (int)(e % rp), b = (int)(e / rp);
+    const double v = Out[a + (int64_t)b * lds];
+    tt += v * v;
+    if (a < r && b < r) ts += v * Z[a + (int64_t)b * lds];
+  }
+  ts = block_sum(ts, sh);
+  tt = block_sum(tt, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = ts;
+    partials[2 * blockIdx.x + 1] = tt;
+  }
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+      s1 += __ldcg(partials + 2 * i);
+      s2 += __ldcg(partials + 2 * i + 1);
+    }
+    if (!isfinite(s1) || !isfinite(s2)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 4;
+    } else if (s2 == 0.0 || s1 == 0.0) {
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 5;
+    } else {
+      st->omega = s1 / s2;
+    }
+  }
+}
+
+int oz_pad(int x, int t) { return (x + t - 1) / t * t; }
+
+}  // namespace
+
+size_t ozaki_scratch_bytes(int rmax) {
+  const int Mp = oz_pad(rmax, OZ_TM), Kp = oz_pad(rmax, OZ_KC * OZ_FOLD);
+  // two digit sets (A and B operand) of Mp x Kp BF16 x 8 planes, exponents, omega partials
+  return (size_t)2 * OZ_P * Mp * Kp * 2 + (size_t)2 * Mp * sizeof(int) + (size_t)4 * Mp * sizeof(unsigned long long) +
+         (size_t)2 * OZ_OMEGA_CTAS * sizeof(double) + 256;
+}
+
+bool ozaki_setup() {
+  return cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM) ==
+         cudaSuccess;
+}
+
+// Out(rp x rp, ld lds) = [H Z, 0] + [Z G^T; 0]: two tensor-core passes, each after splitting its
+// two operands.  scratch: ozaki_scratch_bytes(rp) bytes.  Returns the number of kernels launched.
+int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const double* H, const double* G,
+                           int64_t ldh, const double* Z, double* Out, int64_t lds, bool omega, void* scratch) {
+  const int rp = r + s;
+  const int Mp = oz_pad(rp, OZ_TM);           // A rows (output rows)
+  const int Np = oz_pad(rp, OZ_TN);           // B rows (output columns)
+  const int Kp = oz_pad(r, OZ_KC * OZ_FOLD);  // contraction length
+  const int nkc = Kp / OZ_KC;
+  const int64_t planeA = (int64_t)Mp * Kp, planeB = (int64_t)Np * Kp;
+  __nv_bfloat16* Ad = (__nv_bfloat16*)scratch;
+  __nv_bfloat16* Bd = Ad + (size_t)OZ_P * planeA;
+  int* ea = (int*)(Bd + (size_t)OZ_P * planeB);
+  int* fb = ea + Mp;
+  unsigned long long* mx = (unsigned long long*)(((uintptr_t)(fb + Mp) + 15) & ~(uintptr_t)15);  // 4 x Mp
+  double* partials = (double*)(mx + 4 * (size_t)Mp);
+  const dim3 grid(Mp / OZ_TM, Np / OZ_TN);
+  const dim3 gmA((unsigned)((rp + 31) / 32), (unsigned)((r + 63) / 64));
+  const dim3 gmZ((unsigned)((r + 31) / 32), (unsigned)((r + 63) / 64));
+  const unsigned gsA = (unsigned)(((int64_t)Mp * (Kp / 8) + NT - 1) / NT);
+  const unsigned gsB = (unsigned)(((int64_t)Np * (Kp / 8) + NT - 1) / NT);
+  cudaMemsetAsync(mx, 0, (size_t)4 * Mp * sizeof(unsigned long long), strm);
+  // pass 1: Out = H Z  (A(a, c) = H[a + c ldh], B(b, c) = Z[c + b lds]), all rp x rp outputs
+  oz_max_kernel<<<gmA, NT, 0, strm>>>(st, H, 1, ldh, rp, r, mx);
+  oz_max_kernel<<<gmZ, NT, 0, strm>>>(st, Z, lds, 1, r, r, mx + Mp);
+  oz_split_kernel<<<gsA, NT, 0, strm>>>(st, H, 1, ldh, rp, r, Mp, Kp, OZ_TM, mx, ea, Ad, planeA);
+  oz_split_kernel<<<gsB, NT, 0, strm>>>(st, Z, lds, 1, r, r, Np, Kp, OZ_TN, mx + Mp, fb, Bd, planeB);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 1, s, Out, lds, rp,
+                                                       rp, 0);
+  // pass 2: Out += Z G^T  (A(a, c) = Z[a + c lds], B(b, c) = G[b + c ldh]), rows a < r
+  oz_max_kernel<<<gmZ, NT, 0, strm>>>(st, Z, 1, lds, r, r, mx + 2 * (size_t)Mp);
+  oz_max_kernel<<<gmA, NT, 0, strm>>>(st, G, 1, ldh, rp, r, mx + 3 * (size_t)Mp);
+  oz_split_kernel<<<gsA, NT, 0, strm>>>(st, Z, 1, lds, r, r, Mp, Kp, OZ_TM, mx + 2 * (size_t)Mp, ea, Ad, planeA);
+  oz_split_kernel<<<gsB, NT, 0, strm>>>(st, G, 1, ldh, rp, r, Np, Kp, OZ_TN, mx + 3 * (size_t)Mp, fb, Bd, planeB);
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 2, s, Out, lds, r,
+                                                       rp, 1);
+  int launched = 10;
+  if (omega) {
+    const int64_t E = (int64_t)rp * rp;
+    const unsigned g = (unsigned)std::min<int64_t>((E + NT - 1) / NT, OZ_OMEGA_CTAS);
+    oz_omega_kernel<<<g, NT, 0, strm>>>(st, r, rp, Out, Z, lds, partials);
+    launched += 1;
+  }
+  return launched;
+}
+
+}  // namespace sylv

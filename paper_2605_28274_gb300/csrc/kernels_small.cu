@@ -545,6 +545,8 @@ void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
 int launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
   const int rp = r + c.s;
   const dim3 gg((rp + GBM - 1) / GBM, (rp + GBM - 1) / GBM);
+  if (c.oz_scratch != nullptr && r >= c.oz_min_r)
+    return launch_sylv_gemm_ozaki(strm, c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, omega, c.oz_scratch);
   if (c.df_small) {
     dfp* Hs = (dfp*)c.Hs;
     dfp* Gs = (dfp*)c.Gs;
