@@ -345,7 +345,6 @@ void prof_finish(sylv_handle* h, int iters) {
   do {                                              \
     cudaEvent_t prof_a_ = prof_begin(h);            \
     stmt;                                           \
-    (h)->launches += 1;                             \
     prof_end((h), (cls), (bytes), (flops), prof_a_); \
   } while (0)
 
@@ -444,7 +443,6 @@ void setup_qr(sylv_handle* h, int si) {
   a.Rout = sd.RQR;
   sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
   sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr);
-  h->launches += 5;  // pack, self-Gram, Cholesky, scale+Gram, Cholesky, scale (one counted by PROF)
 }
 
 // One block Lanczos (lanczos=true) or BCGS2 block Arnoldi step on side si:
@@ -591,7 +589,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   }
   h->split_cols = 0;
   prof_reset(h);
-  h->launches = 0;
+  const int64_t launches0 = sylv::launch_counter();
   for (int i = 0; i < nsides(h); ++i) {
     PROF(h, KC_SETUP, 0.0, 0.0, setup_qr<T>(h, i));
   }
@@ -599,7 +597,6 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   const Side& sA = h->side[0];
   const Side& sB = h->side[h->lyap ? 0 : 1];
   sylv::launch_init_small(strm, c, sA.RQR, sB.RQR, tol, method == M_BICG);
-  h->launches += 1;
   CU(cudaGetLastError());
   const int poll = h->opt.poll_every > 0 ? h->opt.poll_every : 8;
   int slot = 0, pending = -1;
@@ -660,14 +657,14 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       basis_step<T>(h, 1, 2 * k, false);
       TRY(small_wait_basis(0));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * (double)r1 * r1 + q2), sylv::sylv_gemm_flops(r1, s),
-           h->launches += sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false) - 1);
+           sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false));
       PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
       PROF(h, KC_SMALL_ELEM, e8 * 3.0 * q2, 2.0 * q2, sylv::launch_bicg_s(strm, c, rp));
       basis_step<T>(h, 0, 2 * k + 1, false);
       basis_step<T>(h, 1, 2 * k + 1, false);
       TRY(small_wait_basis(1));
       PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + t2), sylv::sylv_gemm_flops(rp, s) + 4.0 * t2,
-           h->launches += sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true) - 1);
+           sylv::launch_sylv_gemm(strm, c, rp, c.Sh, c.Th, true));
       PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
            sylv::launch_bicg_update(strm, c, k, rp, rpp));
       PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));
@@ -708,6 +705,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   }
   if (maxit == 0 && ds.status == sylv::ST_RUNNING) rc = SYLV_ENOTCONV;
   h->status = rc;
+  h->launches = sylv::launch_counter() - launches0;
   if (info) {
     std::memset(info, 0, sizeof(*info));
     info->status = rc;
@@ -848,7 +846,6 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
     PROF(h, KC_RESID_SMALL, 0.0, 2.0 * r * r * k, sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2));
     PROF(h, KC_RESID_TSU, (double)rows_out * (r * sizeof(T) + 2.0 * k * 8.0), fl * rows_out,
          sylv::launch_tsu<T>(h->stream, rows_out, Uout, bsout, v.s, v.nb, P2, k, 1.0, first ? 0.0 : 1.0, Yout));
-    h->launches += 2;
     first = false;
   }
   if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
@@ -888,7 +885,6 @@ int sketch_R(sylv_handle* h, const double* Om, double* Y, size_t from_round = 0)
     sylv::launch_neg_sum(h->stream, n * SKK, X16, Xb, X16);                                  // -(A dX Om + dX B Om)
     sylv::launch_axpy(h->stream, n * SKK, 1.0, X16, Y);
   }
-  h->launches += 8;
   return SYLV_OK;
 }
 
@@ -917,7 +913,6 @@ int sketch_Rt(sylv_handle* h, const double* Q, double* Z) {
   sylv::launch_spmm<double>(h->stream, nullptr, m, SKK, Bt.rp, Bt.ci, Bt.vald, Zb, Z, nullptr, nullptr, 0);
   sylv::launch_neg_sum(h->stream, m * SKK, Z, Za, Z);
   sylv::launch_lowrank_axpy(h->stream, m, s, SKK, h->C2rm, G, 1.0, Z);
-  h->launches += 8;
   return SYLV_OK;
 }
 
@@ -947,7 +942,6 @@ void qr8_impl(sylv_handle* h, int64_t n, double* Y, double* Rout) {
   a.Rout = Rout;
   sylv::launch_chol(h->stream, h->st_sk, h->spart, nc, a);
   sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, nullptr);
-  h->launches += 5;
 }
 
 // Enqueues the ||R||_F estimate on h->stream; leaves Q (n x 8, buffer 11) and Z
@@ -976,7 +970,6 @@ int sketch_enqueue(sylv_handle* h) {
     sylv::launch_tsg<double>(h->stream, n, h->C1rm, n * s, s, 1, h->C1rm, s, part2, 0, G1);
     sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, h->C2rm, s, part2, 0, G1 + 64);
     sylv::launch_trace_prod(h->stream, s, G1, G1 + 64, sums + 2);
-    h->launches += 5;
   }
   const double* Om1 = h->Om;
   const double* Om2 = h->Om + m * SKK;
@@ -999,7 +992,6 @@ int sketch_enqueue(sylv_handle* h) {
   sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Y3);
   sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
   sylv::launch_sumsq(h->stream, n * SKK, Y3, part, ticket + 1, sums + 1);
-  h->launches += 6;
   CU(cudaMemcpyAsync(h->sk_host, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaMemcpyAsync(h->sk_host + 4, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   return SYLV_OK;
@@ -1084,6 +1076,7 @@ void prof_add(sylv_handle* dst, const sylv_handle* src) {
 template <typename T>
 int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
   const double t0 = now_s();
+  const int64_t launches0 = sylv::launch_counter();
   free_subs(h);
   h->true_rel = -1.0;
   h->refinements = 0;
@@ -1128,7 +1121,6 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       // a correction only has to reach tol_c; its basis is sized for at most 100 iterations
       const int src = run_inner<T>(sub, method, tol_c, std::min(maxit, 100), &si);
       prof_add(h, sub);
-      h->launches += sub->launches;
       h->total_iters += sub->iters;
       h->total_width += sub->width;
       if (info) info->matvecs += (int64_t)(method == M_CG ? sub->iters : 2 * sub->iters);
@@ -1147,7 +1139,7 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     info->true_rel_res = h->true_rel;
     info->refinements = h->refinements;
     info->solve_ms = (now_s() - t0) * 1e3;
-    info->kernel_launches = h->launches;
+    info->kernel_launches = sylv::launch_counter() - launches0;
   }
   return rc;
 }
@@ -1188,7 +1180,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
   if (!(tol >= 0.0) || maxit < 0) return fail(SYLV_EINVAL, "tol must be >= 0 and maxit >= 0");
   const int count = (int)h->batch.size();
   cudaStream_t strm = h->stream;
-  h->launches = 0;
+  const int64_t launches0 = sylv::launch_counter();
   std::vector<sylv::BatchInst> insts(count);
   int maxs = 1;
   for (int i = 0; i < count; ++i) {
@@ -1201,7 +1193,6 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     setup_qr<double>(x, 0);
     sylv::SmallCtx c = small_ctx(x);
     sylv::launch_init_small(strm, c, x->side[0].RQR, x->side[0].RQR, tol, 0);
-    h->launches += 7;
     sylv::BatchInst& I = insts[i];
     std::memset(&I, 0, sizeof(I));
     I.n = x->side[0].n;
@@ -1264,7 +1255,6 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
         CU(cudaEventSynchronize(e1));
         float ms = 0.f;
         CU(cudaEventElapsedTime(&ms, e0, e1));
-        h->launches += 8;
         if (ms < best) {
           best = ms;
           h->tuned_chunk = ch;
@@ -1289,7 +1279,10 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
   }
   cudaGraph_t g = nullptr;
   CU(cudaStreamBeginCapture(strm, cudaStreamCaptureModeThreadLocal));
+  const int64_t cap0 = sylv::launch_counter();
   sylv::launch_batch_iteration(strm, bc);
+  const int64_t per_iteration = sylv::launch_counter() - cap0;  // captured, not launched
+  sylv::launch_counter() = cap0;
   CU(cudaStreamEndCapture(strm, &g));
   cudaError_t ge = cudaGraphInstantiate(&h->graph, g, 0);
   cudaGraphDestroy(g);
@@ -1300,8 +1293,8 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
   while (k < maxit && !done) {
     const int nrep = std::min(poll, maxit - k);
     for (int r = 0; r < nrep; ++r) CU(cudaGraphLaunch(h->graph, strm));
+    sylv::launch_counter() += per_iteration * nrep;
     k += nrep;
-    h->launches += 15 * nrep;
     CU(cudaMemcpyAsync(&h->h_running[slot], h->d_running, sizeof(int), cudaMemcpyDeviceToHost, strm));
     CU(cudaEventRecord(h->ev[slot], strm));
     if (pending >= 0) {
@@ -1353,7 +1346,6 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     for (size_t i = 0; i < todo.size(); ++i) {
       todo[i]->stream = h->pool[i % h->pool.size()];
       TRY(sketch_enqueue<double>(todo[i]));
-      h->launches += 60;
     }
     int rc_all = SYLV_OK;
     for (sylv_handle* x : todo) {
@@ -1378,7 +1370,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     info->rel_res = worst;
     info->true_rel_res = worst_true;
     info->solve_ms = (now_s() - t0) * 1e3;
-    info->kernel_launches = h->launches;
+    info->kernel_launches = sylv::launch_counter() - launches0;
   }
   return agg;
 }

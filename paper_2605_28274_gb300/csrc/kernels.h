@@ -9,6 +9,15 @@
 
 namespace sylv {
 
+// Kernels enqueued by the calling host thread.  Every launch passes its grid through
+// counted(), so sylv_info.kernel_launches is a count of actual launches.
+int64_t& launch_counter();
+template <typename G>
+inline G counted(G grid) {
+  ++launch_counter();
+  return grid;
+}
+
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -17,6 +17,11 @@
 
 namespace sylv {
 
+int64_t& launch_counter() {
+  static thread_local int64_t c = 0;
+  return c;
+}
+
 namespace {
 
 int num_sms() {
@@ -539,7 +544,7 @@ void launch_spmm(cudaStream_t strm, const DevState* st, int64_t n, int s, const 
   const int grid = (int)((threads + NT - 1) / NT);
   if (grid == 0) return;
 #define CASE(SV) \
-  case SV: spmm_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm); break;
+  case SV: spmm_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
 }
@@ -555,7 +560,7 @@ int launch_gram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T
   const int64_t rpc = (n + grid - 1) / grid;
   T* tpart = reinterpret_cast<T*>(partial);
 #define CASE(SV) \
-  case SV: gram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, tpart); break;
+  case SV: gram_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, rpc, V, bstride, nb, Y, tpart); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
   return grid;
@@ -566,10 +571,10 @@ void launch_reduce_H(cudaStream_t strm, const DevState* st, const double* partia
   const int E = nb * s * s;
   const int grid = (E + RED_E - 1) / RED_E;
   if (float_partials)
-    reduce_H_kernel<float><<<grid, RED_E * RED_G, 0, strm>>>(st, reinterpret_cast<const float*>(partial), ncta, nb, s,
+    reduce_H_kernel<float><<<counted(grid), RED_E * RED_G, 0, strm>>>(st, reinterpret_cast<const float*>(partial), ncta, nb, s,
                                                              H, ldh, row0, col0, Hc, add ? 1 : 0);
   else
-    reduce_H_kernel<double><<<grid, RED_E * RED_G, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc,
+    reduce_H_kernel<double><<<counted(grid), RED_E * RED_G, 0, strm>>>(st, partial, ncta, nb, s, H, ldh, row0, col0, Hc,
                                                               add ? 1 : 0);
 }
 
@@ -580,9 +585,9 @@ int launch_update(cudaStream_t strm, const DevState* st, int64_t n, int s, const
 #define CASE(SV)                                                                                         \
   case SV:                                                                                               \
     if (self_partial)                                                                                    \
-      update_kernel<T, SV, true><<<grid, NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, self_partial);     \
+      update_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, self_partial);     \
     else                                                                                                 \
-      update_kernel<T, SV, false><<<grid, NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, nullptr);         \
+      update_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, n, V, bstride, nb, Hc, Y, nullptr);         \
     break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
@@ -593,7 +598,7 @@ template <typename T>
 int launch_selfgram(cudaStream_t strm, const DevState* st, int64_t n, int s, const T* Y, double* self_partial) {
   const int grid = grid_for(n, NT, 4 * num_sms());
 #define CASE(SV) \
-  case SV: selfgram_kernel<T, SV><<<grid, NT, 0, strm>>>(st, n, Y, self_partial); break;
+  case SV: selfgram_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, Y, self_partial); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
   return grid;
@@ -605,9 +610,9 @@ int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, 
 #define CASE(SV)                                                                               \
   case SV:                                                                                     \
     if (self_partial)                                                                          \
-      scale_kernel<T, SV, true><<<grid, NT, 0, strm>>>(st, n, Y, RinvT, self_partial);         \
+      scale_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, self_partial);         \
     else                                                                                       \
-      scale_kernel<T, SV, false><<<grid, NT, 0, strm>>>(st, n, Y, RinvT, nullptr);             \
+      scale_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, nullptr);             \
     break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
@@ -615,7 +620,7 @@ int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, 
 }
 
 void launch_chol(cudaStream_t strm, DevState* st, const double* self_partial, int ncta, const CholArgs& a) {
-  chol_kernel<<<1, NT, 0, strm>>>(st, self_partial, ncta, a);
+  chol_kernel<<<counted(1), NT, 0, strm>>>(st, self_partial, ncta, a);
 }
 
 template <typename T>
@@ -623,7 +628,7 @@ void launch_pack(cudaStream_t strm, int64_t n, int s, const double* Ccol, T* Vbl
   const int grid = (int)((n * s + NT - 1) / NT);
   if (grid == 0) return;
 #define CASE(SV) \
-  case SV: pack_kernel<T, SV><<<grid, NT, 0, strm>>>(n, Ccol, Vblk); break;
+  case SV: pack_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(n, Ccol, Vblk); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
 }
@@ -632,13 +637,13 @@ template <typename T>
 void launch_unpack(cudaStream_t strm, int64_t n, int s, int nb, const T* Vblk, int64_t bstride, double* Vcol) {
   const int64_t total = n * s * (int64_t)nb;
   if (total == 0) return;
-  unpack_kernel<T><<<(unsigned)((total + NT - 1) / NT), NT, 0, strm>>>(n, s, total, Vblk, bstride, Vcol);
+  unpack_kernel<T><<<counted((unsigned)((total + NT - 1) / NT)), NT, 0, strm>>>(n, s, total, Vblk, bstride, Vcol);
 }
 
 template <typename T>
 void launch_convert(cudaStream_t strm, int64_t count, const double* src, T* dst) {
   if (count == 0) return;
-  convert_kernel<T><<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, src, dst);
+  convert_kernel<T><<<counted((unsigned)((count + NT - 1) / NT)), NT, 0, strm>>>(count, src, dst);
 }
 
 #define SYLV_INST(T)                                                                                              \

@@ -497,28 +497,28 @@ __global__ void k_advance(BatchCtx c) {
 }  // namespace
 
 void launch_batch_spmm_gram(cudaStream_t st, const BatchCtx& c) {
-  k_rows<RP_SPMM><<<c.grid, NT, 0, st>>>(c);
-  k_rows<RP_GRAM><<<c.grid, NT, 0, st>>>(c);
+  k_rows<RP_SPMM><<<counted(c.grid), NT, 0, st>>>(c);
+  k_rows<RP_GRAM><<<counted(c.grid), NT, 0, st>>>(c);
 }
 
 void launch_batch_iteration(cudaStream_t st, const BatchCtx& c) {
   const int gi = (c.count + 63) / 64;
   const int gs = c.sgrid;
-  k_rows<RP_SPMM><<<c.grid, NT, 0, st>>>(c);
-  k_rows<RP_GRAM><<<c.grid, NT, 0, st>>>(c);
-  k_reduce_h<<<c.count, 64, 0, st>>>(c);
-  k_rows<RP_UPDATE><<<c.grid, NT, 0, st>>>(c);
-  k_chol<<<c.count, 64, 0, st>>>(c, 1);
-  k_rows<RP_SCALE_SELF><<<c.grid, NT, 0, st>>>(c);
-  k_chol<<<c.count, 64, 0, st>>>(c, 2);
-  k_rows<RP_SCALE><<<c.grid, NT, 0, st>>>(c);
-  k_lyap_m<<<gs, NT, 0, st>>>(c);
-  k_lyap_q<<<gs, NT, 0, st>>>(c);
-  k_alpha<<<gi, 64, 0, st>>>(c);
-  k_cg_update<<<gs, NT, 0, st>>>(c);
-  k_test<<<gi, 64, 0, st>>>(c);
-  k_cg_p<<<gs, NT, 0, st>>>(c);
-  k_advance<<<1, 32, 0, st>>>(c);
+  k_rows<RP_SPMM><<<counted(c.grid), NT, 0, st>>>(c);
+  k_rows<RP_GRAM><<<counted(c.grid), NT, 0, st>>>(c);
+  k_reduce_h<<<counted(c.count), 64, 0, st>>>(c);
+  k_rows<RP_UPDATE><<<counted(c.grid), NT, 0, st>>>(c);
+  k_chol<<<counted(c.count), 64, 0, st>>>(c, 1);
+  k_rows<RP_SCALE_SELF><<<counted(c.grid), NT, 0, st>>>(c);
+  k_chol<<<counted(c.count), 64, 0, st>>>(c, 2);
+  k_rows<RP_SCALE><<<counted(c.grid), NT, 0, st>>>(c);
+  k_lyap_m<<<counted(gs), NT, 0, st>>>(c);
+  k_lyap_q<<<counted(gs), NT, 0, st>>>(c);
+  k_alpha<<<counted(gi), 64, 0, st>>>(c);
+  k_cg_update<<<counted(gs), NT, 0, st>>>(c);
+  k_test<<<counted(gi), 64, 0, st>>>(c);
+  k_cg_p<<<counted(gs), NT, 0, st>>>(c);
+  k_advance<<<counted(1), 32, 0, st>>>(c);
 }
 
 }  // namespace sylv

@@ -422,24 +422,24 @@ int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const 
   const unsigned gsB = (unsigned)(((int64_t)Np * (Kp / 8) + NT - 1) / NT);
   cudaMemsetAsync(mx, 0, (size_t)4 * Mp * sizeof(unsigned long long), strm);
   // pass 1: Out = H Z  (A(a, c) = H[a + c ldh], B(b, c) = Z[c + b lds]), all rp x rp outputs
-  oz_max_kernel<<<gmA, NT, 0, strm>>>(st, H, 1, ldh, rp, r, mx);
-  oz_max_kernel<<<gmZ, NT, 0, strm>>>(st, Z, lds, 1, r, r, mx + Mp);
-  oz_split_kernel<<<gsA, NT, 0, strm>>>(st, H, 1, ldh, rp, r, Mp, Kp, OZ_TM, mx, ea, Ad, planeA);
-  oz_split_kernel<<<gsB, NT, 0, strm>>>(st, Z, lds, 1, r, r, Np, Kp, OZ_TN, mx + Mp, fb, Bd, planeB);
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 1, s, Out, lds, rp,
+  oz_max_kernel<<<counted(gmA), NT, 0, strm>>>(st, H, 1, ldh, rp, r, mx);
+  oz_max_kernel<<<counted(gmZ), NT, 0, strm>>>(st, Z, lds, 1, r, r, mx + Mp);
+  oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, H, 1, ldh, rp, r, Mp, Kp, OZ_TM, mx, ea, Ad, planeA);
+  oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, Z, lds, 1, r, r, Np, Kp, OZ_TN, mx + Mp, fb, Bd, planeB);
+  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 1, s, Out, lds, rp,
                                                        rp, 0);
   // pass 2: Out += Z G^T  (A(a, c) = Z[a + c lds], B(b, c) = G[b + c ldh]), rows a < r
-  oz_max_kernel<<<gmZ, NT, 0, strm>>>(st, Z, 1, lds, r, r, mx + 2 * (size_t)Mp);
-  oz_max_kernel<<<gmA, NT, 0, strm>>>(st, G, 1, ldh, rp, r, mx + 3 * (size_t)Mp);
-  oz_split_kernel<<<gsA, NT, 0, strm>>>(st, Z, 1, lds, r, r, Mp, Kp, OZ_TM, mx + 2 * (size_t)Mp, ea, Ad, planeA);
-  oz_split_kernel<<<gsB, NT, 0, strm>>>(st, G, 1, ldh, rp, r, Np, Kp, OZ_TN, mx + 3 * (size_t)Mp, fb, Bd, planeB);
-  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 2, s, Out, lds, r,
+  oz_max_kernel<<<counted(gmZ), NT, 0, strm>>>(st, Z, 1, lds, r, r, mx + 2 * (size_t)Mp);
+  oz_max_kernel<<<counted(gmA), NT, 0, strm>>>(st, G, 1, ldh, rp, r, mx + 3 * (size_t)Mp);
+  oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, Z, 1, lds, r, r, Mp, Kp, OZ_TM, mx + 2 * (size_t)Mp, ea, Ad, planeA);
+  oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, G, 1, ldh, rp, r, Np, Kp, OZ_TN, mx + 3 * (size_t)Mp, fb, Bd, planeB);
+  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 2, s, Out, lds, r,
                                                        rp, 1);
   int launched = 10;
   if (omega) {
     const int64_t E = (int64_t)rp * rp;
     const unsigned g = (unsigned)std::min<int64_t>((E + NT - 1) / NT, OZ_OMEGA_CTAS);
-    oz_omega_kernel<<<g, NT, 0, strm>>>(st, r, rp, Out, Z, lds, partials);
+    oz_omega_kernel<<<counted(g), NT, 0, strm>>>(st, r, rp, Out, Z, lds, partials);
     launched += 1;
   }
   return launched;

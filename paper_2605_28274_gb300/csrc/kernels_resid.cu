@@ -312,9 +312,9 @@ void launch_tsg(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int 
   const int64_t rpc = (n + rc - 1) / rc;
   rc = (int)((n + rpc - 1) / rpc);
   const dim3 g((unsigned)rc, (unsigned)cchunks);
-  tsg_kernel<TU><<<g, NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, cw, partial);
+  tsg_kernel<TU><<<counted(g), NT, 0, strm>>>(n, rpc, U, bstride, su, ncol, Y, k, cw, partial);
   const int64_t E = (int64_t)ncol * k;
-  tsg_reduce_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(partial, rc, E, P);
+  tsg_reduce_kernel<<<counted((unsigned)((E + NT - 1) / NT)), NT, 0, strm>>>(partial, rc, E, P);
 }
 
 template <typename TU>
@@ -322,48 +322,48 @@ void launch_tsu(cudaStream_t strm, int64_t n, const TU* U, int64_t bstride, int 
                 double alpha, double beta, double* Z) {
   const int ncol = nb * su;  // ncol = 0: Z = beta Z
   if (n == 0) return;
-  tsu_kernel<TU><<<(unsigned)((n + NT - 1) / NT), NT, 0, strm>>>(n, U, bstride, su, ncol, M, k, alpha, beta, Z);
+  tsu_kernel<TU><<<counted((unsigned)((n + NT - 1) / NT)), NT, 0, strm>>>(n, U, bstride, su, ncol, M, k, alpha, beta, Z);
 }
 
 void launch_small_apply(cudaStream_t strm, int r, int k, const double* Xh, int64_t lds, bool trans, const double* in,
                         double* out) {
   if (r == 0 || k == 0) return;
-  small_apply_kernel<<<(unsigned)((r + 15) / 16), NT, 0, strm>>>(r, k, Xh, lds, trans ? 1 : 0, in, out);
+  small_apply_kernel<<<counted((unsigned)((r + 15) / 16)), NT, 0, strm>>>(r, k, Xh, lds, trans ? 1 : 0, in, out);
 }
 
 void launch_lowrank_axpy(cudaStream_t strm, int64_t n, int s, int k, const double* C, const double* G, double alpha,
                          double* Y) {
-  lowrank_axpy_kernel<<<(unsigned)((n * k + NT - 1) / NT), NT, 0, strm>>>(n, s, k, C, G, alpha, Y);
+  lowrank_axpy_kernel<<<counted((unsigned)((n * k + NT - 1) / NT)), NT, 0, strm>>>(n, s, k, C, G, alpha, Y);
 }
 
 void launch_interleave(cudaStream_t strm, int64_t rows, const double* a, const double* b, double* out) {
   if (rows == 0) return;
-  interleave_kernel<<<(unsigned)((rows * 16 + NT - 1) / NT), NT, 0, strm>>>(rows, a, b, out);
+  interleave_kernel<<<counted((unsigned)((rows * 16 + NT - 1) / NT)), NT, 0, strm>>>(rows, a, b, out);
 }
 
 void launch_deinterleave(cudaStream_t strm, int64_t rows, const double* in, double* a, double* b) {
   if (rows == 0) return;
-  deinterleave_kernel<<<(unsigned)((rows * 16 + NT - 1) / NT), NT, 0, strm>>>(rows, in, a, b);
+  deinterleave_kernel<<<counted((unsigned)((rows * 16 + NT - 1) / NT)), NT, 0, strm>>>(rows, in, a, b);
 }
 
 void launch_axpy(cudaStream_t strm, int64_t count, double a, const double* x, double* y) {
   if (count == 0) return;
-  axpy_kernel<<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, a, x, y);
+  axpy_kernel<<<counted((unsigned)((count + NT - 1) / NT)), NT, 0, strm>>>(count, a, x, y);
 }
 
 void launch_neg_sum(cudaStream_t strm, int64_t count, const double* X1, const double* X2, double* out) {
   if (count == 0) return;
-  neg_sum_kernel<<<(unsigned)((count + NT - 1) / NT), NT, 0, strm>>>(count, X1, X2, out);
+  neg_sum_kernel<<<counted((unsigned)((count + NT - 1) / NT)), NT, 0, strm>>>(count, X1, X2, out);
 }
 
 void launch_sumsq(cudaStream_t strm, int64_t count, const double* x, double* partials, unsigned int* ticket,
                   double* out) {
   const int grid = (int)std::min<int64_t>(256, std::max<int64_t>(1, (count + NT - 1) / NT));
-  sumsq_kernel<<<grid, NT, 0, strm>>>(count, x, partials, ticket, out);
+  sumsq_kernel<<<counted(grid), NT, 0, strm>>>(count, x, partials, ticket, out);
 }
 
 void launch_trace_prod(cudaStream_t strm, int s, const double* G1, const double* G2, double* out) {
-  trace_prod_kernel<<<1, 32, 0, strm>>>(s, G1, G2, out);
+  trace_prod_kernel<<<counted(1), 32, 0, strm>>>(s, G1, G2, out);
 }
 
 template void launch_tsg<float>(cudaStream_t, int64_t, const float*, int64_t, int, int, const double*, int, double*,

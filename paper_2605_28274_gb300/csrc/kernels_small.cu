@@ -522,24 +522,24 @@ dim3 elem_grid(int rows, int cols) { return dim3((unsigned)((rows + NT - 1) / NT
 
 void launch_init_small(cudaStream_t strm, const SmallCtx& c, const double* RL, const double* RR, double tol,
                        int bicg) {
-  init_small_kernel<<<1, 32, 0, strm>>>(c.st, c.hist, c.s, c.lds, c.Rh, c.Ph, c.Rt, RL, RR, tol, bicg);
+  init_small_kernel<<<counted(1), 32, 0, strm>>>(c.st, c.hist, c.s, c.lds, c.Rh, c.Ph, c.Rt, RL, RR, tol, bicg);
 }
 
 void launch_cg_q(cudaStream_t strm, const SmallCtx& c, int mode, int r) {
   const int rp = r + c.s;
   double* out = mode == 1 ? c.Th : c.Qh;  // Lyapunov: the T^ buffer holds M = [H P^, 0]
-  cg_q_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, mode, r, c.s, c.H, c.G, c.ldh, c.Ph, c.Th, out, c.lds,
+  cg_q_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, mode, r, c.s, c.H, c.G, c.ldh, c.Ph, c.Th, out, c.lds,
                                                   c.partials);
 }
 
 void launch_cg_update(cudaStream_t strm, const SmallCtx& c, int k, int r) {
   const int rp = r + c.s;
-  cg_update_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, c.hist, k, r, c.s, c.Xh, c.Rh, c.Ph, c.Qh, c.lds,
+  cg_update_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, c.hist, k, r, c.s, c.Xh, c.Rh, c.Ph, c.Qh, c.lds,
                                                        c.partials);
 }
 
 void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
-  cg_p_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, rp, c.Ph, c.Rh, c.lds);
+  cg_p_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, rp, c.Ph, c.Rh, c.lds);
 }
 
 int launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* Z, double* Out, bool omega) {
@@ -556,26 +556,26 @@ int launch_sylv_gemm(cudaStream_t strm, const SmallCtx& c, int r, const double* 
     if (*c.split_cols < r) {
       const int c0 = *c.split_cols;
       const int64_t E = (int64_t)rp * (r - c0);
-      split_cols_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(c.st, rp, c0, r, c.H, c.ldh, Hs);
+      split_cols_kernel<<<counted((unsigned)((E + NT - 1) / NT)), NT, 0, strm>>>(c.st, rp, c0, r, c.H, c.ldh, Hs);
       launched += 1;
       if (c.G != c.H) {
-        split_cols_kernel<<<(unsigned)((E + NT - 1) / NT), NT, 0, strm>>>(c.st, rp, c0, r, c.G, c.ldh, Gs);
+        split_cols_kernel<<<counted((unsigned)((E + NT - 1) / NT)), NT, 0, strm>>>(c.st, rp, c0, r, c.G, c.ldh, Gs);
         launched += 1;
       }
       *c.split_cols = r;
     }
     const int64_t EZ = (int64_t)r * r;
-    split_cols_kernel<<<(unsigned)((EZ + NT - 1) / NT), NT, 0, strm>>>(c.st, r, 0, r, Z, c.lds, Zs);
+    split_cols_kernel<<<counted((unsigned)((EZ + NT - 1) / NT)), NT, 0, strm>>>(c.st, r, 0, r, Z, c.lds, Zs);
     if (omega)
-      sylv_gemm_df_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, c.partials);
+      sylv_gemm_df_kernel<true><<<counted(gg), NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, c.partials);
     else
-      sylv_gemm_df_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, nullptr);
+      sylv_gemm_df_kernel<false><<<counted(gg), NT, 0, strm>>>(c.st, r, c.s, Hs, Gs, c.ldh, Zs, Z, Out, c.lds, nullptr);
     return launched;
   }
   if (omega)
-    sylv_gemm_kernel<true><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
+    sylv_gemm_kernel<true><<<counted(gg), NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, c.partials);
   else
-    sylv_gemm_kernel<false><<<gg, NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
+    sylv_gemm_kernel<false><<<counted(gg), NT, 0, strm>>>(c.st, r, c.s, c.H, c.G, c.ldh, Z, Out, c.lds, nullptr);
   return 1;
 }
 
@@ -591,20 +591,20 @@ double sylv_gemm_flops(int r, int s) {
 }
 
 void launch_bicg_alpha(cudaStream_t strm, const SmallCtx& c) {
-  bicg_alpha_kernel<<<1, 32, 0, strm>>>(c.st, c.s, c.Rt, c.Qh, c.lds);
+  bicg_alpha_kernel<<<counted(1), 32, 0, strm>>>(c.st, c.s, c.Rt, c.Qh, c.lds);
 }
 
 void launch_bicg_s(cudaStream_t strm, const SmallCtx& c, int rp) {
-  bicg_s_kernel<<<elem_grid(rp, rp), NT, 0, strm>>>(c.st, rp, c.Sh, c.Rh, c.Qh, c.lds);
+  bicg_s_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, rp, c.Sh, c.Rh, c.Qh, c.lds);
 }
 
 void launch_bicg_update(cudaStream_t strm, const SmallCtx& c, int k, int rp, int rpp) {
-  bicg_update_kernel<<<elem_grid(rpp, rpp), NT, 0, strm>>>(c.st, c.hist, k, rp, rpp, c.s, c.Xh, c.Rh, c.Ph, c.Sh,
+  bicg_update_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, c.hist, k, rp, rpp, c.s, c.Xh, c.Rh, c.Ph, c.Sh,
                                                            c.Th, c.Rt, c.lds, c.partials);
 }
 
 void launch_bicg_p(cudaStream_t strm, const SmallCtx& c, int rpp) {
-  bicg_p_kernel<<<elem_grid(rpp, rpp), NT, 0, strm>>>(c.st, rpp, c.Ph, c.Rh, c.Qh, c.lds);
+  bicg_p_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, rpp, c.Ph, c.Rh, c.Qh, c.lds);
 }
 
 }  // namespace sylv
