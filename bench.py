@@ -353,6 +353,12 @@ def max_over_ranks(x: float, dist=None) -> float:
     return float(t.item())
 
 
+# (kernel class, precision) -> (DRAM read + write MB, algorithmic MB, summary) of one ncu capture
+NCU_DRAM_PER_ALGORITHMIC = {
+    ("gram", "fp64"): (318.5, 318.8, "profiles/gram_update_fp64_convdiff64x48_s4.md"),
+}
+
+
 def nvtx_push(name):
     try:
         import torch
@@ -434,7 +440,12 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "kernel": dname, "peak_src": f"{pk['src']} HBM copy"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per algorithmic byte from one ncu capture of the same kernel on a smaller case,
+    # scaled to the average launch of this run by its algorithmic bytes (the kernel reads each
+    # basis element once, so traffic grows in proportion)
+    ratio = NCU_DRAM_PER_ALGORITHMIC.get((dname, args.precision))
+    roof["traffic"] = ratio[0] / ratio[1] * d["bytes"] / max(1, d["launches"]) if ratio else None
+    roof["traffic_src"] = ratio[2] if ratio else None
     roof["launches"] = d["launches"]
     roof["avg_launch_us"] = d["ms"] * 1e3 / max(1, d["launches"])
     hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
