@@ -303,3 +303,74 @@ def factorized_bicgstab(A, B, C1: np.ndarray, C2: np.ndarray, tol: float, maxit:
         rho = rho_new
         Ph = Rh + beta * (pad(Ph, 2 * s) - omega * pad(Qh, s))
     return result(maxit, "maxit")
+
+
+def factorized_cgs(A, B, C1: np.ndarray, C2: np.ndarray, tol: float, maxit: int, delta: float = 1e-12,
+                   keep_iterates: bool = False) -> FactorizedResult:
+    """Factorized CGS: ``matrix_oriented.cgs`` with every iterate kept as V X^ W^T on block
+    Arnoldi bases, built the way Sec. 4.2 builds Algorithm 4.2 from Algorithm 2.2 (Sec. 4
+    states the approach carries over to CGS; the paper prints no listing for it).
+
+    With the iterates R_k, U_k, P_k on the first 2k+1 blocks, each iteration takes two
+    Arnoldi steps per side: L(P_k) needs V_{2k+2} (eq. 3.7), Q_k and U_k + Q_k live there,
+    and L(U_k + Q_k) needs V_{2k+3}.  Additions are additions of the zero-padded small
+    matrices (eq. 3.5); R~_0 = R_0 lives in the first block, so <R~_0, M> is the inner
+    product with the leading s x s block of M^ (eq. 3.6).  Returns V_{2k+2}, X^_{k+1},
+    W_{2k+2} (width (2k+2)s), the shapes of Algorithm 4.2.
+    """
+    s = C1.shape[1]
+    bA = BlockKrylovBasis(A, C1, "arnoldi", delta)
+    bB = BlockKrylovBasis(B.T, C2, "arnoldi", delta)
+    Rh = bA.R0 @ bB.R0.T
+    Rt = Rh.copy()  # shadow residual R~_0 (s x s)
+    Uh = Rh.copy()
+    Ph = Rh.copy()
+    rho = inner(Rt, Rh)
+    Xh = np.zeros((0, 0))
+    r0 = np.sqrt(inner(Rh, Rh))
+    hist = [1.0]
+    xs = [Xh.copy()] if keep_iterates else None
+
+    def result(k, status):
+        w = Xh.shape[0] // s
+        return FactorizedResult(bA.V(w), Xh, bB.V(w), k, status, hist, xs, bA, bB)
+
+    for k in range(maxit):
+        # Arnoldi step 2k+1 on both sides -> V_{2k+2}: L(P_k)
+        try:
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        Vh = small_sylvester(bA.Hk(2 * k + 2, 2 * k + 1), Ph, bB.Hk(2 * k + 2, 2 * k + 1))
+        d = inner(Rt, Vh[:s, :s])
+        if not np.isfinite(d) or d == 0.0:
+            return result(k, "breakdown")
+        alpha = rho / d
+        Qh = pad(Uh, s) - alpha * Vh
+        Wh = pad(Uh, s) + Qh
+        Xh = pad(Xh, 2 * s) + alpha * Wh
+        # Arnoldi step 2k+2 -> V_{2k+3}: L(U_k + Q_k)
+        try:
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        Th = small_sylvester(bA.Hk(2 * k + 3, 2 * k + 2), Wh, bB.Hk(2 * k + 3, 2 * k + 2))
+        Rh = pad(Rh, 2 * s) - alpha * Th
+        rn = np.sqrt(inner(Rh, Rh))
+        hist.append(rn / r0)
+        if xs is not None:
+            xs.append(Xh.copy())
+        if not np.isfinite(rn):
+            return result(k + 1, "breakdown")
+        if rn <= r0 * tol:
+            return result(k + 1, "converged")
+        rho_new = inner(Rt, Rh[:s, :s])
+        if rho_new == 0.0:
+            return result(k + 1, "breakdown")
+        beta = rho_new / rho
+        rho = rho_new
+        Uh = Rh + beta * pad(Qh, s)
+        Ph = Uh + beta * (pad(Qh, s) + beta * pad(Ph, 2 * s))
+    return result(maxit, "maxit")

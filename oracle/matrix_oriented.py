@@ -1,4 +1,5 @@
-"""Matrix-oriented CG and BiCGSTAB on full n x m iterates (Algorithms 2.1, 2.2).
+"""Matrix-oriented CG, BiCGSTAB and CGS on full n x m iterates (Algorithms 2.1, 2.2; CGS as
+Sec. 4 names it, Sonneveld 1989).
 
 Test infrastructure only (see ``oracle/__init__``).  These are the plain
 definitions that the factorized methods are mathematically equivalent to
@@ -93,4 +94,45 @@ def bicgstab(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = 
         beta = alpha / omega * rho_new / rho
         rho = rho_new
         P = R + beta * (P - omega * Q)
+    return FullResult(X, maxit, "maxit", hist, its)
+
+
+def cgs(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False) -> FullResult:
+    """Conjugate Gradient Squared (Sonneveld 1989) on the Kronecker system (eq. 1.2), written
+    with the matrix operations of Sec. 2, X_0 = 0, shadow residual R~_0 = R_0.  Sec. 4 names
+    CGS among the methods the factorized approach applies to; the paper gives no algorithm
+    listing for it, so this is the textbook recurrence with its vectors read as n x m matrices:
+
+        alpha = rho_k / <R~_0, L(P_k)>,  Q_k = U_k - alpha L(P_k),
+        X_{k+1} = X_k + alpha (U_k + Q_k),  R_{k+1} = R_k - alpha L(U_k + Q_k),
+        beta = rho_{k+1} / rho_k,  U_{k+1} = R_{k+1} + beta Q_k,
+        P_{k+1} = U_{k+1} + beta (Q_k + beta P_k),    L(Y) = A Y + Y B.
+    """
+    X = np.zeros_like(C)
+    R = C - sylvester_op(A, B, X)
+    Rt = R.copy()
+    U = R.copy()
+    P = R.copy()
+    rho = inner(Rt, R)
+    r0 = np.linalg.norm(R)
+    hist = [1.0]
+    its = [X.copy()] if keep_iterates else None
+    for k in range(maxit):
+        V = sylvester_op(A, B, P)
+        alpha = rho / inner(Rt, V)
+        Q = U - alpha * V
+        W = U + Q
+        X = X + alpha * W
+        R = R - alpha * sylvester_op(A, B, W)
+        rn = np.linalg.norm(R)
+        hist.append(rn / r0)
+        if its is not None:
+            its.append(X.copy())
+        if rn <= r0 * tol:
+            return FullResult(X, k + 1, "converged", hist, its)
+        rho_new = inner(Rt, R)
+        beta = rho_new / rho
+        rho = rho_new
+        U = R + beta * Q
+        P = U + beta * (Q + beta * P)
     return FullResult(X, maxit, "maxit", hist, its)

@@ -339,3 +339,99 @@ def test_planted_mistakes_fail_the_pins():
     for bad in (transposed_operand, wrong_sign, dropped_term, wrong_pad):
         Q = bad(H, Z, G)
         assert rel(bA.V(k + 1) @ Q @ bB.V(k + 1).T, lhs) > 1e-3, bad.__name__
+
+
+# ------------------------------------------- CGS (Sec. 4 names it; Sonneveld 1989)
+def kron_operator(A, B):
+    """F = I (x) A + B^T (x) I, so that F vec(X) = vec(A X + X B) (eq. 1.2, column-major vec)."""
+    import scipy.sparse as sp
+
+    n, m = A.shape[0], B.shape[0]
+    return (sp.kron(sp.eye(m), A) + sp.kron(B.T, sp.eye(n))).tocsr()
+
+
+def test_matrix_oriented_cgs_matches_scipy_cgs_on_kronecker_system():
+    import scipy.sparse.linalg as spla
+
+    A = wl.convdiff_3d(5, 1).to_scipy()
+    B = wl.convdiff_3d(4, 2).to_scipy()
+    C1, C2 = wl.rhs(125, 64, 2, 0)
+    C = C1 @ C2.T
+    rm = mo.cgs(A, B, C, 0.0, 10, keep_iterates=True)
+    xs = []
+    spla.cgs(kron_operator(A, B), C.flatten(order="F"), rtol=0.0, atol=0.0, maxiter=10,
+             callback=lambda x: xs.append(x.copy()))
+    assert len(xs) == 10
+    for k in range(1, 11):
+        assert rel(rm.iterates[k].flatten(order="F"), xs[k - 1]) < 1e-12, k
+
+
+def test_matrix_oriented_cgs_converges_to_exact():
+    A = wl.convdiff_3d(5, 1).to_scipy()
+    B = wl.convdiff_3d(4, 2).to_scipy()
+    C1, C2 = wl.rhs(125, 64, 2, 0)
+    r = mo.cgs(A, B, C1 @ C2.T, 1e-12, 200)
+    assert r.status == "converged"
+    X = exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)
+    assert rel(r.X, X) < 1e-9
+
+
+def test_factorized_cgs_equals_matrix_oriented_iterates():
+    A = wl.convdiff_3d(5, 1).to_scipy()
+    B = wl.convdiff_3d(4, 2).to_scipy()
+    C1, C2 = wl.rhs(125, 64, 2, 0)
+    rf = fz.factorized_cgs(A, B, C1, C2, 1e-10, 200, keep_iterates=True)
+    rm = mo.cgs(A, B, C1 @ C2.T, 1e-10, 200, keep_iterates=True)
+    assert rf.status == rm.status == "converged"
+    assert abs(rf.iters - rm.iters) <= max(2, rm.iters // 10)
+    for k in range(1, min(12, rf.iters) + 1):
+        assert rf.Xhats[k].shape[0] == (2 * k) * 2
+        assert rel(rf.X_at(k, 2 * k), rm.iterates[k]) < 1e-10, k
+        assert rank_at_most(rm.iterates[k], 2 * k * 2)
+    np.testing.assert_allclose(rf.history[:12], rm.history[:12], rtol=1e-8)
+    X = exact.kron_solve(A.toarray(), B.toarray(), C1 @ C2.T)
+    assert rel(rf.X(), X) < 1e-8
+
+
+def test_factorized_cgs_diagonal_case_closed_form():
+    rng = np.random.default_rng(9)
+    a = rng.uniform(1.0, 3.0, 40)
+    b = rng.uniform(1.0, 3.0, 30)
+    A = wl.diagonal(a).to_scipy()
+    B = wl.diagonal(b).to_scipy()
+    C1, C2 = wl.rhs(40, 30, 2, 3)
+    r = fz.factorized_cgs(A, B, C1, C2, 1e-11, 60)
+    assert r.status == "converged"
+    assert rel(r.X(), exact.diagonal_exact(a, b, C1 @ C2.T)) < 1e-9
+
+
+def test_planted_cgs_mistake_fails_the_scipy_pin():
+    """A CGS recurrence with beta instead of beta^2 in the P update drifts away from the
+    library's CGS iterates: the scipy pin would catch that mistake in the oracle."""
+    import scipy.sparse.linalg as spla
+
+    A = wl.convdiff_3d(5, 1).to_scipy()
+    B = wl.convdiff_3d(4, 2).to_scipy()
+    C1, C2 = wl.rhs(125, 64, 2, 0)
+    C = C1 @ C2.T
+    X = np.zeros_like(C)
+    R = C.copy()
+    Rt, U, P = R.copy(), R.copy(), R.copy()
+    rho = mo.inner(Rt, R)
+    its = []
+    for _ in range(6):
+        V = mo.sylvester_op(A, B, P)
+        alpha = rho / mo.inner(Rt, V)
+        Q = U - alpha * V
+        X = X + alpha * (U + Q)
+        R = R - alpha * mo.sylvester_op(A, B, U + Q)
+        its.append(X.copy())
+        rho_new = mo.inner(Rt, R)
+        beta = rho_new / rho
+        rho = rho_new
+        U = R + beta * Q
+        P = U + beta * (Q + P)  # planted: beta instead of beta^2 on P_k
+    xs = []
+    spla.cgs(kron_operator(A, B), C.flatten(order="F"), rtol=0.0, atol=0.0, maxiter=6,
+             callback=lambda x: xs.append(x.copy()))
+    assert max(rel(its[k].flatten(order="F"), xs[k]) for k in range(6)) > 1e-3
