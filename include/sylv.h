@@ -167,6 +167,19 @@ int sylv_cg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 
 /*
+ * Factorized CGS (conjugate gradient squared, Sonneveld 1989), which Sec. 4 names
+ * among the methods the factorized approach carries over to; the paper prints no
+ * listing, so the recurrence is CGS on the Kronecker system (eq. 1.2) written with
+ * the matrix operations of Sec. 2 and factorized as Algorithm 4.2 is: the same block
+ * Arnoldi bases (two steps per iteration), additions of padded small matrices
+ * (eq. 3.5), inner products with R~_0 = R_0 on the leading s x s block (eq. 3.6),
+ * and two applications of the small operator of eq. 3.7 per iteration.  General A,
+ * B; returns V_{2k+2}, X^_{k+1}, W_{2k+2} as sylv_bicgstab.  Batched handles:
+ * SYLV_EINVAL.  Otherwise as sylv_cg.
+ */
+int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
+
+/*
  * Copies the factors of the last solve: V (n x r), X^ (r x r), W (m x r),
  * column-major, float64.  Any of V, Xhat, W may be NULL to skip it; *r
  * receives r (the call with all three NULL only queries r).  In the Lyapunov

@@ -68,7 +68,7 @@ struct Side {
   void* RinvT = nullptr;
 };
 
-enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2 };
+enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3 };  // CGS: Arnoldi bases like BiCGSTAB
 
 // Kernel classes timed by the optional profiler.
 enum KClass {
@@ -116,6 +116,7 @@ struct sylv_handle {
   int maxb = 0, cap_method = M_NONE;
   int64_t lds = 0;
   double *Xh = nullptr, *Rh = nullptr, *Ph = nullptr, *Qh = nullptr, *Sh = nullptr, *Th = nullptr, *Rt = nullptr;
+  double* Uh = nullptr;  // CGS only
   DevState* st = nullptr;
   DevState* st_host = nullptr;  // pinned, 2 slots
   double* hist = nullptr;
@@ -203,6 +204,7 @@ void free_solve(sylv_handle* h) {
     sd.H = nullptr;
   }
   h->Hs = h->Gs = h->Zs = nullptr;
+  h->Uh = nullptr;
   h->oz_scratch = nullptr;
 }
 
@@ -353,8 +355,10 @@ void prof_finish(sylv_handle* h, int iters) {
 constexpr int kOzakiMinR = 448;  // measured crossover with the CUDA-core float64 kernel
 
 int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
-  const bool want_oz = method == M_BICG && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
-  if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE && (!want_oz || h->oz_scratch))
+  const bool want_oz =
+      (method == M_BICG || method == M_CGS) && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
+  if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE && (!want_oz || h->oz_scratch) &&
+      (method != M_CGS || h->Uh))
     return SYLV_OK;
   free_solve(h);
   const int64_t s = h->s;
@@ -373,6 +377,7 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   TRY(alloc_solve(h, &h->Qh, l2));
   TRY(alloc_solve(h, &h->Sh, l2));
   TRY(alloc_solve(h, &h->Th, l2));
+  if (method == M_CGS) TRY(alloc_solve(h, &h->Uh, l2));
   TRY(alloc_solve(h, &h->Rt, 64));
   TRY(alloc_solve(h, &h->hist, (size_t)hist_need));
   // Gram partials: at most 2*SMs CTAs x (maxb * s * s)
@@ -524,6 +529,7 @@ sylv::SmallCtx small_ctx(sylv_handle* h) {
   c.Qh = h->Qh;
   c.Sh = h->Sh;
   c.Th = h->Th;
+  c.Uh = h->Uh;
   c.Rt = h->Rt;
   c.H = h->side[0].H;
   c.G = h->lyap ? h->side[0].H : h->side[1].H;
@@ -581,7 +587,8 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   cudaStream_t strm = h->stream;
   CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), strm));
   const size_t l2 = (size_t)(h->lds * h->lds) * sizeof(double);
-  for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th}) CU(cudaMemsetAsync(p, 0, l2, strm));
+  for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th, h->Uh})
+    if (p) CU(cudaMemsetAsync(p, 0, l2, strm));
   for (int i = 0; i < nsides(h); ++i) CU(cudaMemsetAsync(h->side[i].H, 0, l2, strm));
   if (h->mixed) {  // split copies of H, G follow H's zero fill
     CU(cudaMemsetAsync(h->Hs, 0, l2, strm));
@@ -596,7 +603,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   sylv::SmallCtx c = small_ctx(h);
   const Side& sA = h->side[0];
   const Side& sB = h->side[h->lyap ? 0 : 1];
-  sylv::launch_init_small(strm, c, sA.RQR, sB.RQR, tol, method == M_BICG);
+  sylv::launch_init_small(strm, c, sA.RQR, sB.RQR, tol, method == M_CGS);
   CU(cudaGetLastError());
   const int poll = h->opt.poll_every > 0 ? h->opt.poll_every : 8;
   int slot = 0, pending = -1;
@@ -650,7 +657,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       }
       PROF(h, KC_SMALL_ELEM, e8 * 6.0 * r2, 4.0 * r2, sylv::launch_cg_update(strm, c, k, r));
       PROF(h, KC_SMALL_ELEM, e8 * 3.0 * r2, 2.0 * r2, sylv::launch_cg_p(strm, c, rp));
-    } else {
+    } else if (method == M_BICG) {
       const int r1 = (2 * k + 1) * s, rp = r1 + s, rpp = rp + s;
       const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
       basis_step<T>(h, 0, 2 * k, false);
@@ -668,6 +675,23 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
            sylv::launch_bicg_update(strm, c, k, rp, rpp));
       PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));
+    } else {  // M_CGS: the same bases and operator, the CGS recurrences on the small side
+      const int r1 = (2 * k + 1) * s, rp = r1 + s, rpp = rp + s;
+      const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
+      basis_step<T>(h, 0, 2 * k, false);
+      basis_step<T>(h, 1, 2 * k, false);
+      TRY(small_wait_basis(0));
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * (double)r1 * r1 + q2), sylv::sylv_gemm_flops(r1, s),
+           sylv::launch_sylv_gemm(strm, c, r1, c.Ph, c.Qh, false));  // V^ = L(P^)
+      PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
+      PROF(h, KC_SMALL_ELEM, e8 * 6.0 * q2, 4.0 * q2, sylv::launch_cgs_q(strm, c, rp));
+      basis_step<T>(h, 0, 2 * k + 1, false);
+      basis_step<T>(h, 1, 2 * k + 1, false);
+      TRY(small_wait_basis(1));
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + t2), sylv::sylv_gemm_flops(rp, s),
+           sylv::launch_sylv_gemm(strm, c, rp, c.Th, c.Sh, false));  // T^ = L(W^)
+      PROF(h, KC_SMALL_ELEM, e8 * 3.0 * t2, 4.0 * t2, sylv::launch_cgs_update(strm, c, k, rpp));
+      PROF(h, KC_SMALL_ELEM, e8 * 5.0 * t2, 5.0 * t2, sylv::launch_cgs_p(strm, c, rpp));
     }
     CU(cudaEventRecord(h->ev_small[k % 8], strm));
     if ((k + 1) % poll == 0 && k + 1 < maxit) {
@@ -1491,6 +1515,11 @@ int sylv_cg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
 int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
   g_err.clear();
   return solve(h, M_BICG, tol, maxit, info);
+}
+
+int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
+  g_err.clear();
+  return solve(h, M_CGS, tol, maxit, info);
 }
 
 int sylv_create_batch(int32_t count, const sylv_csr* A, const sylv_csr* B, const double* const* C1,

@@ -96,6 +96,7 @@ struct SmallCtx {
   int s;
   int64_t lds;
   double *Xh, *Rh, *Ph, *Qh, *Sh, *Th, *Rt;  // Rt: shadow residual R~_0 (s x s, ld s)
+  double* Uh;                                // CGS only: U^
   const double* H;  // A-side block Hessenberg (ld ldh)
   const double* G;  // B^T-side (== H in the Lyapunov case)
   int64_t ldh;
@@ -113,7 +114,7 @@ struct SmallCtx {
 };
 
 // R^_0 = R_L R_R^T, P^_0 = R^_0, R~_0 = R^_0, rho_0, ||R^_0||, history[0] = 1.
-void launch_init_small(cudaStream_t, const SmallCtx&, const double* RL, const double* RR, double tol, int bicg);
+void launch_init_small(cudaStream_t, const SmallCtx&, const double* RL, const double* RR, double tol, bool cgs);
 
 // Algorithm 4.1 pieces.  cg_q: mode 0 Q^ = [H P^, 0] + [P^ G^T; 0]; mode 1 M = [H P^, 0]
 // (Lyapunov, into the T^ buffer); mode 2 Q^ = M + M^T.  Modes 0/2 also set alpha.
@@ -134,6 +135,13 @@ int launch_sylv_gemm_ozaki(cudaStream_t, DevState* st, int r, int s, const doubl
                            const double* Z, double* Out, int64_t lds, bool omega, void* scratch);
 double sylv_gemm_flops(int r, int s);
 void launch_bicg_alpha(cudaStream_t, const SmallCtx&);
+// Factorized CGS (Sec. 4 names it; same bases and operator as Algorithm 4.2): with V^ = L(P^)
+// in Qh and alpha from launch_bicg_alpha, cgs_q forms Q^ (in Qh), W^ = U^ + Q^ (in Th) and
+// X^ += alpha W^ (extent rp); with T^ = L(W^) in Sh, cgs_update forms R^ -= alpha T^, the
+// test and beta (extent rpp); cgs_p forms U^ and P^.
+void launch_cgs_q(cudaStream_t, const SmallCtx&, int rp);
+void launch_cgs_update(cudaStream_t, const SmallCtx&, int k, int rpp);
+void launch_cgs_p(cudaStream_t, const SmallCtx&, int rpp);
 void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);
 void launch_bicg_update(cudaStream_t, const SmallCtx&, int k, int rp, int rpp);
 void launch_bicg_p(cudaStream_t, const SmallCtx&, int rpp);

@@ -19,8 +19,8 @@ namespace {
 
 // ---------------------------------------------------------------- init
 __global__ void init_small_kernel(DevState* st, double* hist, int s, int64_t lds, double* Rh, double* Ph,
-                                  double* Rt, const double* __restrict__ RL, const double* __restrict__ RR,
-                                  double tol, int bicg) {
+                                  double* Rt, double* Uh, const double* __restrict__ RL,
+                                  const double* __restrict__ RR, double tol) {
   // one CTA, thread 0 (s <= 8)
   if (threadIdx.x != 0) return;
   hist[0] = 1.0;
@@ -33,6 +33,7 @@ __global__ void init_small_kernel(DevState* st, double* hist, int s, int64_t lds
       Rh[u + t * lds] = acc;
       Ph[u + t * lds] = acc;
       Rt[u + t * s] = acc;
+      if (Uh) Uh[u + t * lds] = acc;  // CGS: U^_0 = R^_0
       nrm2 += acc * acc;
     }
   st->r0 = sqrt(nrm2);
@@ -45,7 +46,6 @@ __global__ void init_small_kernel(DevState* st, double* hist, int s, int64_t lds
   if (!isfinite(nrm2)) st->status = ST_NONFINITE;
   else if (nrm2 == 0.0) st->status = ST_CONVERGED;  // C1 C2^T = 0: X = 0
   else st->status = ST_RUNNING;
-  (void)bicg;
 }
 
 // ---------------------------------------------------------------- CG: Q^ for block tridiagonal H, G
@@ -516,13 +516,117 @@ __global__ void __launch_bounds__(NT) bicg_p_kernel(const DevState* st, int rpp,
   P[i] = R[i] + st->beta * (P[i] - st->omega * Q[i]);
 }
 
+// ---------------------------------------------------------------- factorized CGS
+// The CGS recurrence on padded small matrices (eq. 3.5), inner products with R~_0 on the
+// leading s x s block (eq. 3.6); alpha = rho / <R~_0, V^(1:s,1:s)> comes from
+// bicg_alpha_kernel with V^ = L(P^) in the Q^ buffer.
+//
+// Q^ = pad(U^) - alpha V^ (in place, V -> Q), W^ = pad(U^) + Q^, X^ <- pad(X^) + alpha W^,
+// over extent rp = (2k+2)s.
+__global__ void __launch_bounds__(NT) cgs_q_kernel(const DevState* st, int rp, double* __restrict__ X,
+                                                   const double* __restrict__ U, double* __restrict__ VQ,
+                                                   double* __restrict__ W, int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= rp) return;
+  const int64_t i = a + (int64_t)b * lds;
+  const double alpha = st->alpha;
+  const double u = U[i];
+  const double q = u - alpha * VQ[i];
+  const double w = u + q;
+  VQ[i] = q;
+  W[i] = w;
+  X[i] = X[i] + alpha * w;
+}
+
+// R^ <- pad(R^) - alpha T^ over extent rpp = (2k+3)s (T^ = L(W^)); then the test,
+// rho_{k+1} = <R~_0, R^(1:s,1:s)> and beta = rho_{k+1} / rho_k (last CTA).
+__global__ void __launch_bounds__(NT) cgs_update_kernel(DevState* st, double* hist, int k, int rpp, int s,
+                                                        double* __restrict__ R, const double* __restrict__ T,
+                                                        const double* __restrict__ Rt, int64_t lds,
+                                                        double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  const double alpha = st->alpha;
+  double rr = 0.0;
+  if (a < rpp) {
+    const int64_t i = a + (int64_t)b * lds;
+    const double v = R[i] - alpha * T[i];
+    R[i] = v;
+    rr = v * v;
+  }
+  rr = block_sum(rr, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = rr;
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    const double rn = sqrt(tot);
+    hist[k + 1] = rn / st->r0;
+    st->rnorm = rn;
+    st->iters = k + 1;
+    if (!isfinite(rn)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 8;
+    } else if (rn <= st->r0 * st->tol) {
+      st->status = ST_CONVERGED;
+    } else {
+      double rho_new = 0.0;
+      for (int t = 0; t < s; ++t)
+        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+      if (rho_new == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 9;
+      } else {
+        st->beta = rho_new / st->rho;
+        st->rho = rho_new;
+      }
+    }
+  }
+}
+
+// U^ <- R^ + beta pad(Q^);  P^ <- U^ + beta (pad(Q^) + beta pad(P^))  over extent rpp.
+__global__ void __launch_bounds__(NT) cgs_p_kernel(const DevState* st, int rpp, double* __restrict__ U,
+                                                   double* __restrict__ P, const double* __restrict__ R,
+                                                   const double* __restrict__ Q, int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= rpp) return;
+  const int64_t i = a + (int64_t)b * lds;
+  const double beta = st->beta;
+  const double q = Q[i];
+  const double u = R[i] + beta * q;
+  U[i] = u;
+  P[i] = u + beta * (q + beta * P[i]);
+}
+
 dim3 elem_grid(int rows, int cols) { return dim3((unsigned)((rows + NT - 1) / NT), (unsigned)cols); }
 
 }  // namespace
 
 void launch_init_small(cudaStream_t strm, const SmallCtx& c, const double* RL, const double* RR, double tol,
-                       int bicg) {
-  init_small_kernel<<<counted(1), 32, 0, strm>>>(c.st, c.hist, c.s, c.lds, c.Rh, c.Ph, c.Rt, RL, RR, tol, bicg);
+                       bool cgs) {
+  init_small_kernel<<<counted(1), 32, 0, strm>>>(c.st, c.hist, c.s, c.lds, c.Rh, c.Ph, c.Rt, cgs ? c.Uh : nullptr,
+                                                 RL, RR, tol);
+}
+
+void launch_cgs_q(cudaStream_t strm, const SmallCtx& c, int rp) {
+  cgs_q_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, rp, c.Xh, c.Uh, c.Qh, c.Th, c.lds);
+}
+
+void launch_cgs_update(cudaStream_t strm, const SmallCtx& c, int k, int rpp) {
+  cgs_update_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, c.hist, k, rpp, c.s, c.Rh, c.Sh, c.Rt,
+                                                                   c.lds, c.partials);
+}
+
+void launch_cgs_p(cudaStream_t strm, const SmallCtx& c, int rpp) {
+  cgs_p_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, rpp, c.Uh, c.Ph, c.Rh, c.Qh, c.lds);
 }
 
 void launch_cg_q(cudaStream_t strm, const SmallCtx& c, int mode, int r) {
