@@ -374,3 +374,75 @@ def factorized_cgs(A, B, C1: np.ndarray, C2: np.ndarray, tol: float, maxit: int,
         Uh = Rh + beta * pad(Qh, s)
         Ph = Uh + beta * (pad(Qh, s) + beta * pad(Ph, 2 * s))
     return result(maxit, "maxit")
+
+
+def factorized_cr(A, B, C1: np.ndarray, C2: Optional[np.ndarray], tol: float, maxit: int,
+                  lyapunov: bool = False, delta: float = 1e-12, keep_iterates: bool = False) -> FactorizedResult:
+    """Factorized CR: ``matrix_oriented.cr`` with every iterate kept as V X^ W^T on block
+    Lanczos bases (A, B symmetric), built the way Sec. 4.1 builds Algorithm 4.1 from
+    Algorithm 2.1 (Sec. 4 states the approach carries over to CR; the paper prints no listing).
+
+    R_k lives on the first k+1 blocks and L(R_k), L(P_k) on k+2 (eq. 3.7), so each iteration
+    takes one Lanczos step per side, after the convergence test, for L(R_{k+1}); one more
+    step before the loop gives L(R_0).  Inner products of padded small matrices (eq. 3.6);
+    with ``lyapunov`` one basis and the operator of Sec. 4.3.  Returns V_{k+1}, X^_{k+1},
+    W_{k+1} (width (k+1)s), the shapes of Algorithm 4.1.
+    """
+    s = C1.shape[1]
+    bA = BlockKrylovBasis(A, C1, "lanczos", delta)
+    bB = bA if lyapunov else BlockKrylovBasis(B.T, C2, "lanczos", delta)
+    Rh = bA.R0 @ bB.R0.T
+    if lyapunov:
+        Rh = 0.5 * (Rh + Rh.T)
+    Xh = np.zeros((0, 0))
+    r0 = np.sqrt(inner(Rh, Rh))
+    hist = [1.0]
+    xs = [Xh.copy()] if keep_iterates else None
+
+    def result(k, status):
+        w = Xh.shape[0] // s
+        return FactorizedResult(bA.V(w), Xh, bB.V(w), k, status, hist, xs, bA, None if lyapunov else bB)
+
+    def op(j, Z):  # L(V_j Z W_j^T) on blocks 1..j+1 (eq. 3.7)
+        H = bA.Hk(j + 1, j)
+        return small_lyapunov(H, Z) if lyapunov else small_sylvester(H, Z, bB.Hk(j + 1, j))
+
+    def step():
+        bA.step()
+        if not lyapunov:
+            bB.step()
+
+    try:
+        step()  # V_2: L(R_0)
+    except Breakdown:
+        return result(0, "breakdown")
+    LRh = op(1, Rh)
+    rho = inner(Rh, LRh[:s, :s])
+    Ph, LPh = Rh.copy(), LRh.copy()
+    for k in range(maxit):
+        lp = inner(LPh, LPh)
+        if not np.isfinite(rho) or rho == 0.0 or not np.isfinite(lp) or lp == 0.0:
+            return result(k, "breakdown")
+        alpha = rho / lp
+        Xh = pad(Xh, s) + alpha * Ph
+        Rh = pad(Rh, s) - alpha * LPh
+        rn = np.sqrt(inner(Rh, Rh))
+        hist.append(rn / r0)
+        if xs is not None:
+            xs.append(Xh.copy())
+        if not np.isfinite(rn):
+            return result(k + 1, "breakdown")
+        if rn <= r0 * tol:
+            return result(k + 1, "converged")
+        try:
+            step()  # V_{k+3}: L(R_{k+1})
+        except Breakdown:
+            return result(k + 1, "breakdown")
+        LRh = op(k + 2, Rh)
+        r = (k + 2) * s
+        rho_new = inner(Rh, LRh[:r, :r])
+        beta = rho_new / rho
+        rho = rho_new
+        Ph = Rh + beta * pad(Ph, s)
+        LPh = LRh + beta * pad(LPh, s)
+    return result(maxit, "maxit")

@@ -1,5 +1,5 @@
-"""Matrix-oriented CG, BiCGSTAB and CGS on full n x m iterates (Algorithms 2.1, 2.2; CGS as
-Sec. 4 names it, Sonneveld 1989).
+"""Matrix-oriented CG, BiCGSTAB, CGS and CR on full n x m iterates (Algorithms 2.1, 2.2; CGS
+and CR as Sec. 4 names them: Sonneveld 1989, Stiefel 1955).
 
 Test infrastructure only (see ``oracle/__init__``).  These are the plain
 definitions that the factorized methods are mathematically equivalent to
@@ -135,4 +135,41 @@ def cgs(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False
         rho = rho_new
         U = R + beta * Q
         P = U + beta * (Q + beta * P)
+    return FullResult(X, maxit, "maxit", hist, its)
+
+
+def cr(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False) -> FullResult:
+    """Conjugate Residual (Stiefel 1955) on the Kronecker system (eq. 1.2) with A, B symmetric,
+    so that L(Y) = A Y + Y B is self-adjoint for <., .> (Sec. 2); X_0 = 0.  Sec. 4 names CR
+    among the methods the factorized approach applies to; the paper gives no listing, so this
+    is the textbook recurrence with its vectors read as n x m matrices:
+
+        alpha = <R_k, L(R_k)> / <L(P_k), L(P_k)>,  X_{k+1} = X_k + alpha P_k,
+        R_{k+1} = R_k - alpha L(P_k),  beta = <R_{k+1}, L(R_{k+1})> / <R_k, L(R_k)>,
+        P_{k+1} = R_{k+1} + beta P_k,  L(P_{k+1}) = L(R_{k+1}) + beta L(P_k).
+    """
+    X = np.zeros_like(C)
+    R = C - sylvester_op(A, B, X)
+    LR = sylvester_op(A, B, R)
+    P, LP = R.copy(), LR.copy()
+    rho = inner(R, LR)
+    r0 = np.linalg.norm(R)
+    hist = [1.0]
+    its = [X.copy()] if keep_iterates else None
+    for k in range(maxit):
+        alpha = rho / inner(LP, LP)
+        X = X + alpha * P
+        R = R - alpha * LP
+        rn = np.linalg.norm(R)
+        hist.append(rn / r0)
+        if its is not None:
+            its.append(X.copy())
+        if rn <= r0 * tol:
+            return FullResult(X, k + 1, "converged", hist, its)
+        LR = sylvester_op(A, B, R)
+        rho_new = inner(R, LR)
+        beta = rho_new / rho
+        rho = rho_new
+        P = R + beta * P
+        LP = LR + beta * LP
     return FullResult(X, maxit, "maxit", hist, its)

@@ -435,3 +435,93 @@ def test_planted_cgs_mistake_fails_the_scipy_pin():
     spla.cgs(kron_operator(A, B), C.flatten(order="F"), rtol=0.0, atol=0.0, maxiter=6,
              callback=lambda x: xs.append(x.copy()))
     assert max(rel(its[k].flatten(order="F"), xs[k]) for k in range(6)) > 1e-3
+
+
+# ---------------------------------------------- CR (Sec. 4 names it; Stiefel 1955)
+def spd_pair():
+    return wl.laplacian_2d(9).to_scipy(), wl.laplacian_2d(7).to_scipy()
+
+
+def test_matrix_oriented_cr_matches_scipy_minres_on_kronecker_system():
+    """For a self-adjoint operator CR and MINRES both minimise ||R|| over the same Krylov
+    space, so their iterates coincide; scipy's MINRES is the independent reference."""
+    import scipy.sparse.linalg as spla
+
+    A, B = spd_pair()
+    C1, C2 = wl.rhs(81, 49, 2, 0)
+    C = C1 @ C2.T
+    rm = mo.cr(A, B, C, 0.0, 12, keep_iterates=True)
+    xs = []
+    spla.minres(kron_operator(A, B), C.flatten(order="F"), rtol=1e-300, maxiter=12,
+                callback=lambda x: xs.append(x.copy()))
+    assert len(xs) == 12
+    for k in range(1, 13):
+        assert rel(rm.iterates[k].flatten(order="F"), xs[k - 1]) < 1e-12, k
+
+
+def test_factorized_cr_equals_matrix_oriented_iterates():
+    A, B = spd_pair()
+    C1, C2 = wl.rhs(81, 49, 2, 0)
+    rf = fz.factorized_cr(A, B, C1, C2, 1e-10, 200, keep_iterates=True)
+    rm = mo.cr(A, B, C1 @ C2.T, 1e-10, 200, keep_iterates=True)
+    assert rf.status == rm.status == "converged"
+    assert abs(rf.iters - rm.iters) <= 2
+    for k in range(1, min(15, rf.iters) + 1):
+        assert rf.Xhats[k].shape[0] == k * 2
+        assert rel(rf.X_at(k, k), rm.iterates[k]) < 1e-10, k
+        assert rank_at_most(rm.iterates[k], k * 2)
+    np.testing.assert_allclose(rf.history[:15], rm.history[:15], rtol=1e-8)
+    X = exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)
+    assert rel(rf.X(), X) < 1e-8
+
+
+def test_factorized_cr_lyapunov_symmetric_and_exact():
+    A = wl.laplacian_2d(9, 0.5).to_scipy()
+    C1, _ = wl.rhs(81, None, 3, 2)
+    r = fz.factorized_cr(A, None, C1, None, 1e-11, 200, lyapunov=True)
+    assert r.status == "converged"
+    assert np.abs(r.Xhat - r.Xhat.T).max() == 0.0
+    X = exact.bartels_stewart(A.toarray(), A.toarray(), C1 @ C1.T)
+    assert rel(r.X(), X) < 1e-8
+    r2 = fz.factorized_cr(A, A, C1, C1, 1e-11, 200)
+    assert rel(r.X(), r2.X()) < 1e-9
+
+
+def test_factorized_cr_diagonal_case_closed_form():
+    rng = np.random.default_rng(10)
+    a, b = rng.uniform(1.0, 3.0, 40), rng.uniform(1.0, 3.0, 30)
+    A, B = wl.diagonal(a).to_scipy(), wl.diagonal(b).to_scipy()
+    C1, C2 = wl.rhs(40, 30, 2, 3)
+    r = fz.factorized_cr(A, B, C1, C2, 1e-11, 60)
+    assert r.status == "converged"
+    assert rel(r.X(), exact.diagonal_exact(a, b, C1 @ C2.T)) < 1e-9
+
+
+def test_planted_cr_mistake_fails_the_minres_pin():
+    """CR that forgets the beta L(P_k) term of the L(P) recurrence leaves MINRES's iterates."""
+    import scipy.sparse.linalg as spla
+
+    A, B = spd_pair()
+    C1, C2 = wl.rhs(81, 49, 2, 0)
+    C = C1 @ C2.T
+    X = np.zeros_like(C)
+    R = C.copy()
+    LR = mo.sylvester_op(A, B, R)
+    P, LP = R.copy(), LR.copy()
+    rho = mo.inner(R, LR)
+    its = []
+    for _ in range(6):
+        alpha = rho / mo.inner(LP, LP)
+        X = X + alpha * P
+        R = R - alpha * LP
+        its.append(X.copy())
+        LR = mo.sylvester_op(A, B, R)
+        rho_new = mo.inner(R, LR)
+        beta = rho_new / rho
+        rho = rho_new
+        P = R + beta * P
+        LP = LR  # planted: dropped beta L(P_k)
+    xs = []
+    spla.minres(kron_operator(A, B), C.flatten(order="F"), rtol=1e-300, maxiter=6,
+                callback=lambda x: xs.append(x.copy()))
+    assert max(rel(its[k].flatten(order="F"), xs[k]) for k in range(6)) > 1e-3
