@@ -180,6 +180,18 @@ int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 
 /*
+ * Factorized CR (conjugate residual, Stiefel 1955), the other method Sec. 4 names for
+ * symmetric problems; no listing in the paper, so the recurrence is CR on the Kronecker
+ * system (eq. 1.2) in the matrix operations of Sec. 2, factorized as Algorithm 4.1 is:
+ * block Lanczos bases (A, B symmetric; not checked), one step per iteration plus one
+ * before the first, the small operator of eq. 3.7 applied to R^ (one per iteration),
+ * L(P) by its recurrence.  Lyapunov handles use the one-basis form of Sec. 4.3.
+ * Returns V_{k+1}, X^_{k+1}, W_{k+1} as sylv_cg; matvecs = iters + 1.  Batched handles:
+ * SYLV_EINVAL.  Otherwise as sylv_cg.
+ */
+int sylv_cr(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
+
+/*
  * Copies the factors of the last solve: V (n x r), X^ (r x r), W (m x r),
  * column-major, float64.  Any of V, Xhat, W may be NULL to skip it; *r
  * receives r (the call with all three NULL only queries r).  In the Lyapunov

@@ -68,7 +68,8 @@ struct Side {
   void* RinvT = nullptr;
 };
 
-enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3 };  // CGS: Arnoldi bases like BiCGSTAB
+enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3, M_CR = 4 };  // CGS: Arnoldi bases, CR: Lanczos
+inline bool lanczos_method(int m) { return m == M_CG || m == M_CR; }
 
 // Kernel classes timed by the optional profiler.
 enum KClass {
@@ -581,7 +582,8 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   const double t0 = now_s();
   const double deadline = t0 + (h->opt.timeout_s > 0 ? h->opt.timeout_s : 3600.0);
   if (!(tol >= 0.0) || maxit < 0) return fail(SYLV_EINVAL, "tol must be >= 0 and maxit >= 0");
-  const int maxb = std::max(2, method == M_CG ? maxit + 1 : 2 * maxit + 1);
+  // CG: V_{k+2} in iteration k; CR: one step ahead (L(R_{k+1}) needs V_{k+3}); Arnoldi: two per iteration
+  const int maxb = std::max(2, method == M_CG ? maxit + 1 : method == M_CR ? maxit + 2 : 2 * maxit + 1);
   TRY(ensure_capacity(h, method, maxb, maxit + 1));
   const int s = (int)h->s;
   cudaStream_t strm = h->stream;
@@ -639,10 +641,38 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     }
     return SYLV_OK;
   };
+  if (method == M_CR) {  // L(R_0) needs V_2: one Lanczos step, the operator on R^_0, P^_0 = R^_0, alpha
+    basis_step<T>(h, 0, 0, true);
+    if (!h->lyap) basis_step<T>(h, 1, 0, true);
+    TRY(small_wait_basis(0));
+    const double r2 = 4.0 * s * s;
+    if (h->lyap) {
+      PROF(h, KC_SMALL_OP, e8 * 2.0 * r2, r2, sylv::launch_cr_op(strm, c, 1, s, true));
+      PROF(h, KC_SMALL_OP, e8 * 3.0 * r2, r2, sylv::launch_cr_op(strm, c, 2, s, true));
+    } else {
+      PROF(h, KC_SMALL_OP, e8 * 2.0 * r2, 2.0 * r2, sylv::launch_cr_op(strm, c, 0, s, true));
+    }
+    PROF(h, KC_SMALL_ELEM, e8 * 5.0 * r2, 5.0 * r2, sylv::launch_cr_p(strm, c, 2 * s));
+  }
   for (int k = 0; k < maxit && !stopped; ++k) {
     h->prof.cur_k = k;
     TRY(basis_wait_small(k));
-    if (method == M_CG) {
+    if (method == M_CR) {  // the update and test first; then L(R_{k+1}) on V_{k+3}
+      const int r = (k + 1) * s, rp = r + s, rpp = rp + s;
+      const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
+      PROF(h, KC_SMALL_ELEM, e8 * 6.0 * q2, 4.0 * q2, sylv::launch_cg_update(strm, c, k, r, true));
+      basis_step<T>(h, 0, k + 1, true);
+      if (!h->lyap) basis_step<T>(h, 1, k + 1, true);
+      TRY(small_wait_basis(0));
+      const double opflops = 2.0 * 2.0 * t2 * 3.0 * s;
+      if (h->lyap) {
+        PROF(h, KC_SMALL_OP, e8 * (2.0 * t2), opflops / 2, sylv::launch_cr_op(strm, c, 1, rp, false));
+        PROF(h, KC_SMALL_OP, e8 * (3.0 * t2), t2, sylv::launch_cr_op(strm, c, 2, rp, false));
+      } else {
+        PROF(h, KC_SMALL_OP, e8 * (2.0 * t2), opflops, sylv::launch_cr_op(strm, c, 0, rp, false));
+      }
+      PROF(h, KC_SMALL_ELEM, e8 * 5.0 * t2, 5.0 * t2, sylv::launch_cr_p(strm, c, rpp));
+    } else if (method == M_CG) {
       basis_step<T>(h, 0, k, true);
       if (!h->lyap) basis_step<T>(h, 1, k, true);
       TRY(small_wait_basis(0));
@@ -717,8 +747,8 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   prof_finish(h, ds.iters);
   h->method = method;
   h->iters = ds.iters;
-  h->width = (int64_t)(method == M_CG ? ds.iters : 2 * ds.iters) * s;
-  h->nblocks = method == M_CG ? ds.iters + 1 : 2 * ds.iters + 1;
+  h->width = (int64_t)(lanczos_method(method) ? ds.iters : 2 * ds.iters) * s;
+  h->nblocks = lanczos_method(method) ? ds.iters + 1 : 2 * ds.iters + 1;
   int rc;
   switch (ds.status) {
     case sylv::ST_CONVERGED: rc = SYLV_OK; break;
@@ -734,7 +764,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     std::memset(info, 0, sizeof(*info));
     info->status = rc;
     info->iters = ds.iters;
-    info->matvecs = (int64_t)(method == M_CG ? ds.iters : 2 * ds.iters);
+    info->matvecs = (int64_t)(method == M_CG ? ds.iters : method == M_CR ? ds.iters + 1 : 2 * ds.iters);
     info->width = h->width;
     info->rel_res = ds.r0 > 0 ? ds.rnorm / ds.r0 : 0.0;
     info->true_rel_res = -1.0;
@@ -1147,7 +1177,8 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       prof_add(h, sub);
       h->total_iters += sub->iters;
       h->total_width += sub->width;
-      if (info) info->matvecs += (int64_t)(method == M_CG ? sub->iters : 2 * sub->iters);
+      if (info)
+        info->matvecs += (int64_t)(method == M_CG ? sub->iters : method == M_CR ? sub->iters + 1 : 2 * sub->iters);
       h->refinements += 1;
       if (src != SYLV_OK && src != SYLV_ENOTCONV) {
         rc = src;
@@ -1520,6 +1551,11 @@ int sylv_bicgstab(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
 int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
   g_err.clear();
   return solve(h, M_CGS, tol, maxit, info);
+}
+
+int sylv_cr(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
+  g_err.clear();
+  return solve(h, M_CR, tol, maxit, info);
 }
 
 int sylv_create_batch(int32_t count, const sylv_csr* A, const sylv_csr* B, const double* const* C1,

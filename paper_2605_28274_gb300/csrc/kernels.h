@@ -120,7 +120,7 @@ void launch_init_small(cudaStream_t, const SmallCtx&, const double* RL, const do
 // (Lyapunov, into the T^ buffer); mode 2 Q^ = M + M^T.  Modes 0/2 also set alpha.
 void launch_cg_q(cudaStream_t, const SmallCtx&, int mode, int r);
 // X^ += alpha P^, R^ -= alpha Q^, residual test, rho, beta (extent r -> r+s).
-void launch_cg_update(cudaStream_t, const SmallCtx&, int k, int r);
+void launch_cg_update(cudaStream_t, const SmallCtx&, int k, int r, bool cr = false);
 // P^ = R^ + beta P^ over extent rp.
 void launch_cg_p(cudaStream_t, const SmallCtx&, int rp);
 
@@ -140,6 +140,12 @@ void launch_bicg_alpha(cudaStream_t, const SmallCtx&);
 // X^ += alpha W^ (extent rp); with T^ = L(W^) in Sh, cgs_update forms R^ -= alpha T^, the
 // test and beta (extent rpp); cgs_p forms U^ and P^.
 void launch_cgs_q(cudaStream_t, const SmallCtx&, int rp);
+// Factorized CR (Sec. 4 names it; block Lanczos bases as Algorithm 4.1): cr_op applies the
+// operator to R^ (extent r -> r+s) into the S^ buffer and sets rho = <R^, L(R)^> (first) or
+// beta and rho; cr_p forms P^ and L(P)^ (in the Q^ buffer, extent rpp) and alpha.  The update
+// of X^, R^ and the test is launch_cg_update(.., cr = true) with L(P)^ in place of Q^.
+void launch_cr_op(cudaStream_t, const SmallCtx&, int mode, int r, bool first);
+void launch_cr_p(cudaStream_t, const SmallCtx&, int rpp);
 void launch_cgs_update(cudaStream_t, const SmallCtx&, int k, int rpp);
 void launch_cgs_p(cudaStream_t, const SmallCtx&, int rpp);
 void launch_bicg_s(cudaStream_t, const SmallCtx&, int rp);

@@ -53,10 +53,14 @@ __global__ void init_small_kernel(DevState* st, double* hist, int s, int64_t lds
 // mode 1: M  = [H P^, 0]                 (Lyapunov, first half)
 // mode 2: Q^ = M + M^T                   (Lyapunov, second half; Out is Q^, In is M)
 // Modes 0 and 2 also reduce <P^, Q^(1:r,1:r)> and set alpha = rho / that (last CTA).
+// cr = 0 (CG): the reduction <P^, Q^> sets alpha = rho / <P^, Q^>.  cr = 1 (CR: P is R^, Out
+// is L(R)^): the reduction is rho_new = <R^, L(R)^>; with first it sets rho, otherwise
+// beta = rho_new / rho and rho = rho_new.
 __global__ void __launch_bounds__(NT) cg_q_kernel(DevState* st, int mode, int r, int s, const double* __restrict__ H,
                                                   const double* __restrict__ G, int64_t ldh,
                                                   const double* __restrict__ P, const double* __restrict__ In,
-                                                  double* __restrict__ Out, int64_t lds, double* partials) {
+                                                  double* __restrict__ Out, int64_t lds, double* partials, int cr,
+                                                  int first) {
   if (stopped(st)) return;
   __shared__ double sh[32];
   __shared__ int last_sh;
@@ -96,6 +100,14 @@ __global__ void __launch_bounds__(NT) cg_q_kernel(DevState* st, int mode, int r,
     if (!isfinite(tot)) {
       st->status = ST_NONFINITE;
       st->breakdown_where = 1;
+    } else if (cr) {
+      if (tot == 0.0) {  // <R, L(R)> = 0: the CR recurrence breaks down
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 20;
+      } else {
+        if (!first) st->beta = tot / st->rho;
+        st->rho = tot;
+      }
     } else if (!(tot > 0.0)) {  // <P, Q> <= 0: F not positive definite on this direction
       st->status = ST_BREAKDOWN;
       st->breakdown_where = 2;
@@ -107,10 +119,11 @@ __global__ void __launch_bounds__(NT) cg_q_kernel(DevState* st, int mode, int r,
 
 // X^ <- pad(X^) + alpha P^ (extent r), R^ <- pad(R^) - alpha Q^ (extent r+s); then the
 // test, rho_{k+1} = <R^,R^>, beta = rho_{k+1}/rho_k (last CTA).
+// cr = 1: Q is L(P)^ and beta, rho come from the next operator application (cg_q_kernel, cr).
 __global__ void __launch_bounds__(NT) cg_update_kernel(DevState* st, double* hist, int k, int r, int s,
                                                        double* __restrict__ X, double* __restrict__ R,
                                                        const double* __restrict__ P, const double* __restrict__ Q,
-                                                       int64_t lds, double* partials) {
+                                                       int64_t lds, double* partials, int cr) {
   if (stopped(st)) return;
   __shared__ double sh[32];
   __shared__ int last_sh;
@@ -142,9 +155,47 @@ __global__ void __launch_bounds__(NT) cg_update_kernel(DevState* st, double* his
       st->breakdown_where = 3;
     } else if (rn <= st->r0 * st->tol) {
       st->status = ST_CONVERGED;
-    } else {
+    } else if (!cr) {
       st->beta = tot / st->rho;
       st->rho = tot;
+    }
+  }
+}
+
+// CR: P^ <- R^ + beta pad(P^), L(P)^ <- L(R)^ + beta pad(L(P)^) over extent rpp, then
+// alpha = rho / <L(P)^, L(P)^> (last CTA).
+__global__ void __launch_bounds__(NT) cr_p_kernel(DevState* st, int rpp, double* __restrict__ P,
+                                                  double* __restrict__ LP, const double* __restrict__ R,
+                                                  const double* __restrict__ LR, int64_t lds, double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  const double beta = st->beta;
+  double qq = 0.0;
+  if (a < rpp) {
+    const int64_t i = a + (int64_t)b * lds;
+    P[i] = R[i] + beta * P[i];
+    const double v = LR[i] + beta * LP[i];
+    LP[i] = v;
+    qq = v * v;
+  }
+  qq = block_sum(qq, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = qq;
+  if (last_cta(&st->tickets[TK_CG_Q], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    if (!isfinite(tot)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 21;
+    } else if (tot == 0.0) {
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 22;
+    } else {
+      st->alpha = st->rho / tot;
     }
   }
 }
@@ -633,13 +684,24 @@ void launch_cg_q(cudaStream_t strm, const SmallCtx& c, int mode, int r) {
   const int rp = r + c.s;
   double* out = mode == 1 ? c.Th : c.Qh;  // Lyapunov: the T^ buffer holds M = [H P^, 0]
   cg_q_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, mode, r, c.s, c.H, c.G, c.ldh, c.Ph, c.Th, out, c.lds,
-                                                  c.partials);
+                                                  c.partials, 0, 0);
 }
 
-void launch_cg_update(cudaStream_t strm, const SmallCtx& c, int k, int r) {
+void launch_cr_op(cudaStream_t strm, const SmallCtx& c, int mode, int r, bool first) {
+  const int rp = r + c.s;
+  double* out = mode == 1 ? c.Th : c.Sh;  // L(R)^ in the S^ buffer (Lyapunov: M in T^ first)
+  cg_q_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, mode, r, c.s, c.H, c.G, c.ldh, c.Rh, c.Th, out, c.lds,
+                                                  c.partials, 1, first ? 1 : 0);
+}
+
+void launch_cr_p(cudaStream_t strm, const SmallCtx& c, int rpp) {
+  cr_p_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, rpp, c.Ph, c.Qh, c.Rh, c.Sh, c.lds, c.partials);
+}
+
+void launch_cg_update(cudaStream_t strm, const SmallCtx& c, int k, int r, bool cr) {
   const int rp = r + c.s;
   cg_update_kernel<<<counted(elem_grid(rp, rp)), NT, 0, strm>>>(c.st, c.hist, k, r, c.s, c.Xh, c.Rh, c.Ph, c.Qh, c.lds,
-                                                       c.partials);
+                                                       c.partials, cr ? 1 : 0);
 }
 
 void launch_cg_p(cudaStream_t strm, const SmallCtx& c, int rp) {
