@@ -250,19 +250,19 @@ def profiled_breakdown(p, stream, precision, maxit):
     return gbs, (gbs / pk["hbm_gbs"] if gbs else None), per
 
 
-def timed_solves(p, stream, precision, steps, warmup):
+def timed_solves(p, stream, precision, steps, warmup, method="bicgstab"):
     import torch
 
     import paper_2605_28274_gb300 as ps
 
     with ps.Solver(p.A, p.B, p.C1, p.C2, precision=precision, cuda_stream=stream.cuda_stream) as sv:
         for _ in range(warmup):
-            sv.bicgstab(p.tol, p.maxit)
+            getattr(sv, method)(p.tol, p.maxit)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            info = sv.bicgstab(p.tol, p.maxit)
+            info = getattr(sv, method)(p.tol, p.maxit)
         e1.record(stream)
         torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps / 1e3, info
@@ -278,6 +278,29 @@ def measure_mixed(p, stream, steps, warmup):
             "true_rel_res": info["true_rel_res"], "width": info["width"],
             "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
             "kernel_profile_one_stream": per}
+
+
+def measure_methods(p, stream, steps, warmup):
+    """The other factorized methods (Sec. 4 names CGS and CR) at full size: CGS on the benchmarked
+    convection-diffusion operators, CG and CR on a symmetric workload of the same size class
+    (A = L_512 + I/2, B = L_384 + I/2: 2D 5-point Laplacians, n = 262,144, m = 147,456, s = 4).
+    Time to a relative residual of 1e-8 (mixed: true residual), FP64 and mixed."""
+    out = {}
+    for prec in ("fp64", "mixed"):
+        t, info = timed_solves(p, stream, prec, steps, warmup, "cgs")
+        out[f"cgs_{prec}_convdiff3d_64^3_x_48^3_s4"] = {"value": t, "unit": "s", "status": info["status_name"],
+                                                        "iters_total": info["iters"], "width": info["width"],
+                                                        "true_rel_res": info["true_rel_res"]}
+    A, B = wl.laplacian_2d(512, 0.5), wl.laplacian_2d(384, 0.5)
+    C1, C2 = wl.rhs(A.nrows, B.nrows, 4, 0)
+    q = wl.Problem(name="laplace2d_512x384_s4", A=A, B=B, C1=C1, C2=C2, s=4, method="cg", tol=1e-8, maxit=300)
+    for meth in ("cg", "cr"):
+        for prec in ("fp64", "mixed"):
+            t, info = timed_solves(q, stream, prec, steps, warmup, meth)
+            out[f"{meth}_{prec}_laplace2d_512^2_x_384^2_shift0.5_s4"] = {
+                "value": t, "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
+                "width": info["width"], "true_rel_res": info["true_rel_res"]}
+    return out
 
 
 def measure_batched(stream, steps, warmup):
@@ -501,6 +524,7 @@ def run_ours(args):
         variants["mixed"] = measure_mixed(p, stream, args.steps, 2)
         variants["mixed"]["speedup_vs_fp64"] = (ms_step / 1e3) / variants["mixed"]["value"]
         variants["batched"] = measure_batched(stream, args.steps, 2)
+        variants["methods"] = measure_methods(p, stream, max(1, min(args.steps, 2)), 1)
     if args.large:
         variants["large_mixed"] = measure_large(stream, 1, 1)
 
