@@ -214,10 +214,11 @@ __global__ void __launch_bounds__(NT) gram_kernel(const DevState* st, int64_t n,
   }
 }
 
-// Fixed-order sum of the per-CTA partials.  A CTA covers 32 outputs; its 8 warps
-// split each output's partials (warp g takes CTAs g, g+8, ...), so every thread has
-// only ncta/8 loads in its chain, and the 8 group sums are added in a fixed order.
-constexpr int RED_E = 32, RED_G = 8;
+// Fixed-order sum of the per-CTA partials.  A CTA covers 8 outputs; 32 groups of threads
+// split each output's partials (group g takes CTAs g, g+32, ...), so every thread has only
+// ncta/32 loads in its chain (the sum is latency-bound, not bandwidth-bound), and the 32
+// group sums are added in a fixed order.
+constexpr int RED_E = 8, RED_G = 32;
 
 template <typename P>
 __global__ void __launch_bounds__(RED_E * RED_G) reduce_H_kernel(const DevState* st, const P* __restrict__ partial,
@@ -408,94 +409,123 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
   double hsq = 0.0;
   if (a.pass == 1 && a.Hcol != nullptr) {  // ||H_{1:j,j}||^2, four independent chains per thread
     double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
-    const int64_t tot = a.hrows * s;
-    int64_t i = threadIdx.x;
-    for (; i + 3 * NT < tot; i += 4 * NT) {
-      const double x0 = a.Hcol[(i % a.hrows) + (i / a.hrows) * a.ldh];
-      const double x1 = a.Hcol[((i + NT) % a.hrows) + ((i + NT) / a.hrows) * a.ldh];
-      const double x2 = a.Hcol[((i + 2 * NT) % a.hrows) + ((i + 2 * NT) / a.hrows) * a.ldh];
-      const double x3 = a.Hcol[((i + 3 * NT) % a.hrows) + ((i + 3 * NT) / a.hrows) * a.ldh];
-      h0 += x0 * x0;
-      h1 += x1 * x1;
-      h2 += x2 * x2;
-      h3 += x3 * x3;
-    }
-    for (; i < tot; i += NT) {
-      const double x = a.Hcol[(i % a.hrows) + (i / a.hrows) * a.ldh];
-      h0 += x * x;
+    for (int t = 0; t < s; ++t) {
+      const double* col = a.Hcol + (int64_t)t * a.ldh;
+      int64_t i = threadIdx.x;
+      for (; i + 3 * NT < a.hrows; i += 4 * NT) {
+        const double x0 = col[i], x1 = col[i + NT], x2 = col[i + 2 * NT], x3 = col[i + 3 * NT];
+        h0 += x0 * x0;
+        h1 += x1 * x1;
+        h2 += x2 * x2;
+        h3 += x3 * x3;
+      }
+      for (; i < a.hrows; i += NT) h0 += col[i] * col[i];
     }
     hsq = (h0 + h1) + (h2 + h3);
   }
   hsq = block_sum(hsq, sh);
-  if (threadIdx.x == 0) {
-    // G[u*s+t] = sum_rows y_u y_t (symmetric)
-    double tr = 0.0;
+  // The s x s factorisation runs on one warp with the lanes in parallel: on this GPU every
+  // float64 instruction of a single thread holds the FP64 pipe of its quarter-SM for tens of
+  // cycles, so a one-thread Cholesky + inverse + product took ~20 us.  Shared memory holds
+  // the Schur complement S, R, R^-1, 1/R_jj, R1 (pass 2) and the product R2 R1.
+  __shared__ double R1s[64], Pm[64], S[64], dinv[8];
+  __shared__ int out_sh;  // 0: write nothing, 1: write the factors (zero ones if exhausted)
+  if (threadIdx.x < 64) {
+    R[threadIdx.x] = 0.0;
+    Ri[threadIdx.x] = 0.0;
+    Pm[threadIdx.x] = 0.0;
+    S[threadIdx.x] = threadIdx.x < E ? G[threadIdx.x] : 0.0;
+    R1s[threadIdx.x] = (a.pass == 2 && threadIdx.x < E) ? a.R1[threadIdx.x] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     bool finite = true;
-    for (int e = 0; e < E; ++e) finite = finite && isfinite(G[e]);
+    for (int e = lane; e < E; e += 32) finite = finite && isfinite(G[e]);
+    finite = __all_sync(0xffffffffu, finite);
+    double tr = 0.0;  // G[u*s+t] = sum_rows y_u y_t (symmetric)
     for (int u = 0; u < s; ++u) tr += G[u * s + u];
     const double nu2 = hsq + tr;
     int exh = (a.pass == 2) ? st->exhausted[a.side] : 0;
     int bad = 0;
     if (!finite || !isfinite(hsq)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 100 + a.side;
       bad = 1;
+      if (lane == 0) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 100 + a.side;
+      }
     } else if (a.pass == 1 && !a.setup && tr <= a.delta * a.delta * nu2) {
       exh = 1;
-      st->exhausted[a.side] = 1;
+      if (lane == 0) st->exhausted[a.side] = 1;
     }
-    for (int e = 0; e < 64; ++e) { R[e] = 0.0; Ri[e] = 0.0; }
     if (!bad && !exh) {
+      // right-looking Cholesky G = R^T R (upper R, positive diagonal); the updates of each
+      // entry subtract the same terms in the same order as the left-looking form
       const double thr = (a.pass == 1) ? a.delta * a.delta * nu2 : 0.0;
-      for (int j = 0; j < s && !bad; ++j) {
-        double d = G[j * s + j];
-        for (int k = 0; k < j; ++k) d -= R[k + j * s] * R[k + j * s];
-        if (!(d > thr)) {
+      for (int j = 0; j < s; ++j) {
+        const double d = S[j * s + j];
+        if (!(d > thr)) {  // the same value in every lane: a uniform branch
           bad = 1;
-          st->status = ST_BREAKDOWN;
-          st->breakdown_where = 10 + a.side;
+          if (lane == 0) {
+            st->status = ST_BREAKDOWN;
+            st->breakdown_where = 10 + a.side;
+          }
           break;
         }
-        const double rjj = sqrt(d);
-        R[j + j * s] = rjj;
-        for (int i = j + 1; i < s; ++i) {
-          double g = G[j * s + i];
-          for (int k = 0; k < j; ++k) g -= R[k + j * s] * R[k + i * s];
-          R[j + i * s] = g / rjj;
+        const double rjj = sqrt(d), rinv = 1.0 / rjj;
+        if (lane == j) {
+          R[j + j * s] = rjj;
+          dinv[j] = rinv;
+        } else if (lane > j && lane < s) {
+          R[j + lane * s] = S[j * s + lane] * rinv;
         }
+        __syncwarp();
+        const int m = s - j - 1;
+        for (int p = lane; p < m * m; p += 32) {
+          const int i = j + 1 + p / m, l = j + 1 + p % m;
+          S[i * s + l] -= R[j + i * s] * R[j + l * s];
+        }
+        __syncwarp();
       }
       if (!bad) {
+        // R^-1 column by column; the rows of a column in parallel
         for (int j = 0; j < s; ++j) {
-          Ri[j + j * s] = 1.0 / R[j + j * s];
-          for (int i = j - 1; i >= 0; --i) {
+          if (lane == j) {
+            Ri[j + j * s] = dinv[j];
+          } else if (lane < j) {
             double acc = 0.0;
-            for (int k = i; k < j; ++k) acc += Ri[i + k * s] * R[k + j * s];
-            Ri[i + j * s] = -acc / R[j + j * s];
+            for (int k = lane; k < j; ++k) acc += Ri[lane + k * s] * R[k + j * s];
+            Ri[lane + j * s] = -acc * dinv[j];
           }
+          __syncwarp();
         }
       }
     }
-    if (!bad) {
-      for (int e = 0; e < E; ++e) {
-        a.Rinv[e] = Ri[e];
-        if (a.factor_is_float) ((float*)a.RinvT)[e] = (float)Ri[e];
-        else ((double*)a.RinvT)[e] = Ri[e];
-      }
-      if (a.pass == 1) {
-        for (int e = 0; e < E; ++e) a.R1[e] = R[e];
-      } else {
-        // R2 R1 (both upper triangular)
-        for (int j = 0; j < s; ++j)
-          for (int i = 0; i < s; ++i) {
-            double acc = 0.0;
-            for (int k = 0; k < s; ++k) acc += R[i + k * s] * a.R1[k + j * s];
-            if (exh) acc = 0.0;
-            if (a.Hsub) a.Hsub[i + j * a.ldh] = acc;
-            if (a.Hsup) a.Hsup[j + i * a.ldh] = acc;
-            if (a.Rout) a.Rout[i + j * s] = acc;
-          }
+    if (!bad && a.pass == 2) {  // R2 R1 (both upper triangular)
+      for (int e = lane; e < E; e += 32) {
+        const int i = e % s, j = e / s;
+        double acc = 0.0;
+        for (int k = 0; k < s; ++k) acc += R[i + k * s] * R1s[k + j * s];
+        Pm[e] = exh ? 0.0 : acc;
       }
     }
+    if (lane == 0) out_sh = bad ? 0 : 1;
+  }
+  __syncthreads();
+  const int e = threadIdx.x;
+  if (out_sh == 0 || e >= E) return;
+  a.Rinv[e] = Ri[e];
+  if (a.factor_is_float)
+    ((float*)a.RinvT)[e] = (float)Ri[e];
+  else
+    ((double*)a.RinvT)[e] = Ri[e];
+  if (a.pass == 1) {
+    a.R1[e] = R[e];
+  } else {
+    const int i = e % s, j = e / s;
+    if (a.Hsub) a.Hsub[i + j * a.ldh] = Pm[e];
+    if (a.Hsup) a.Hsup[j + i * a.ldh] = Pm[e];
+    if (a.Rout) a.Rout[e] = Pm[e];
   }
 }
 
