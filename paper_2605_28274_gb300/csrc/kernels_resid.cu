@@ -34,14 +34,22 @@ __device__ __forceinline__ dfl split(double x) {
 }
 __device__ __forceinline__ dfl split(float x) { return {x, 0.0f}; }
 
-// acc += u * y for double-float u, y (the lo * lo term, ~2^-48 relative, is dropped)
+// acc += u * y for double-float u, y (the lo * lo term, ~2^-48 relative, is dropped), in the
+// accumulation of Ogita, Rump, Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26, 2005): the high word takes the rounded sum, the low word collects the exact two-sum
+// error and the product's error; df_renorm folds the low word back every few terms, which
+// keeps it a small correction (11 FP32 instructions per term instead of 14).
 __device__ __forceinline__ void df_acc(dfl& acc, float ph, float pl) {
   const float s = __fadd_rn(acc.hi, ph);  // two-sum of acc.hi + ph
   const float bb = __fsub_rn(s, acc.hi);
   const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
-  const float t = __fadd_rn(__fadd_rn(e, acc.lo), pl);
-  acc.hi = __fadd_rn(s, t);  // renormalise
-  acc.lo = __fsub_rn(t, __fsub_rn(acc.hi, s));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pl));
+}
+__device__ __forceinline__ void df_renorm(dfl& acc) {
+  const float s = __fadd_rn(acc.hi, acc.lo);
+  acc.lo = __fsub_rn(acc.lo, __fsub_rn(s, acc.hi));
+  acc.hi = s;
 }
 __device__ __forceinline__ void df_fma(dfl& acc, dfl u, dfl y) {
   const float ph = __fmul_rn(u.hi, y.hi);
@@ -57,6 +65,7 @@ __device__ __forceinline__ void df_fma(dfl& acc, float u, dfl y) {
   pl = __fmaf_rn(u, y.lo, pl);
   df_acc(acc, ph, pl);
 }
+constexpr int DF_RENORM_EVERY = 8;  // terms between renormalisations of an accumulator
 
 __device__ __forceinline__ dfl load_df(const double* p) { return split(*p); }
 __device__ __forceinline__ float load_df(const float* p) { return *p; }
@@ -82,17 +91,45 @@ __global__ void __launch_bounds__(NT) tsg_kernel(int64_t n, int64_t rpc, const T
   const bool active = col < ncol;
   const int b = active ? col / su : 0, u = active ? col - b * su : 0;
   const TU* Ub = U + (int64_t)b * bstride + u;
+  int terms = 0;
   for (int64_t base = r0; base < r1; base += TS_ROWS) {
     const int rows = (int)((r1 - base) < TS_ROWS ? (r1 - base) : TS_ROWS);
     __syncthreads();
     for (int e = threadIdx.x; e < rows * k; e += NT) ys[e] = split(Y[base * k + e]);
     __syncthreads();
     if (active) {
-      for (int i = slot; i < rows; i += nslot) {
+      int i = slot;
+      // four rows' loads in flight before their products
+      for (; i + 3 * nslot < rows; i += 4 * nslot) {
+        const auto u0 = load_df(Ub + (base + i) * su);
+        const auto u1 = load_df(Ub + (base + i + nslot) * su);
+        const auto u2 = load_df(Ub + (base + i + 2 * nslot) * su);
+        const auto u3 = load_df(Ub + (base + i + 3 * nslot) * su);
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (t < k) {
+            df_fma(acc[t], u0, ys[i * k + t]);
+            df_fma(acc[t], u1, ys[(i + nslot) * k + t]);
+            df_fma(acc[t], u2, ys[(i + 2 * nslot) * k + t]);
+            df_fma(acc[t], u3, ys[(i + 3 * nslot) * k + t]);
+          }
+        terms += 4;
+        if (terms >= DF_RENORM_EVERY) {
+          terms = 0;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) df_renorm(acc[t]);
+        }
+      }
+      for (; i < rows; i += nslot) {
         const auto uv = load_df(Ub + (base + i) * su);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
           if (t < k) df_fma(acc[t], uv, ys[i * k + t]);
+        if (++terms >= DF_RENORM_EVERY) {
+          terms = 0;
+#pragma unroll
+          for (int t = 0; t < 16; ++t) df_renorm(acc[t]);
+        }
       }
     }
   }
@@ -149,12 +186,40 @@ __global__ void __launch_bounds__(NT) tsu_kernel(int64_t n, const TU* __restrict
     for (int e = threadIdx.x; e < cc * k; e += NT) ms[e] = split(M[(int64_t)c0 * k + e]);
     __syncthreads();
     if (row < n) {
-      for (int c = 0; c < cc; ++c) {
-        const int col = c0 + c, b = col / su, u = col - b * su;
-        const auto uv = load_df(U + (int64_t)b * bstride + row * su + u);
+      int b = c0 / su, u = c0 - b * su;  // (block, column) of column c0 + c, advanced incrementally
+      const TU* Ur = U + row * su;
+      int c = 0;
+      for (; c + 3 < cc; c += 4) {  // four columns' loads in flight before their products
+        TU x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q] = Ur[(int64_t)b * bstride + u];
+          if (++u == su) {
+            u = 0;
+            ++b;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const auto uv = load_df(&x[q]);
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (t < k) df_fma(acc[t], uv, ms[(c + q) * k + t]);
+        }
+        if ((c & (DF_RENORM_EVERY - 1)) == DF_RENORM_EVERY - 4) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) df_renorm(acc[t]);
+        }
+      }
+      for (; c < cc; ++c) {
+        const auto uv = load_df(Ur + (int64_t)b * bstride + u);
 #pragma unroll
         for (int t = 0; t < 16; ++t)
           if (t < k) df_fma(acc[t], uv, ms[c * k + t]);
+        if (++u == su) {
+          u = 0;
+          ++b;
+        }
       }
     }
   }
