@@ -446,3 +446,95 @@ def factorized_cr(A, B, C1: np.ndarray, C2: Optional[np.ndarray], tol: float, ma
         Ph = Rh + beta * pad(Ph, s)
         LPh = LRh + beta * pad(LPh, s)
     return result(maxit, "maxit")
+
+
+def pad_to(M: np.ndarray, e: int) -> np.ndarray:
+    """M in the top-left corner of an e x e zero matrix (M is at most e x e)."""
+    return pad(M, e - M.shape[0]) if M.shape[0] <= e else M
+
+
+def factorized_gpbicg(A, B, C1: np.ndarray, C2: np.ndarray, tol: float, maxit: int, delta: float = 1e-12,
+                      keep_iterates: bool = False) -> FactorizedResult:
+    """Factorized GPBiCG: ``matrix_oriented.gpbicg`` with every iterate kept as V M^ W^T on
+    block Arnoldi bases, built the way Sec. 4.2 builds Algorithm 4.2 (Sec. 4 states the
+    approach carries over to GPBiCG; the paper prints no listing).
+
+    With R_n on the first 2n+1 blocks, L(P_n) (eq. 3.7) needs V_{2n+2} and L(T_n) needs
+    V_{2n+3}: two Arnoldi steps per iteration, as BiCGSTAB.  Extents: P, R on (2n+1)s; L(P),
+    T, Y, U, Z and X on (2n+2)s; L(T), W and the new R on (2n+3)s.  Additions of zero-padded
+    small matrices (eq. 3.5), inner products of small matrices (eq. 3.6; <R~_0, M> on the
+    leading s x s block).  Returns V_{2k+2}, X^_{k+1}, W_{2k+2} like Algorithm 4.2.
+    """
+    s = C1.shape[1]
+    bA = BlockKrylovBasis(A, C1, "arnoldi", delta)
+    bB = BlockKrylovBasis(B.T, C2, "arnoldi", delta)
+    Rh = bA.R0 @ bB.R0.T
+    Rt = Rh.copy()
+    z = np.zeros((0, 0))
+    Ph, Uh, Wh, Zh, Tph, Xh = z, z, z, z, z, z
+    beta = 0.0
+    rho = inner(Rt, Rh)
+    r0 = np.sqrt(inner(Rh, Rh))
+    hist = [1.0]
+    xs = [Xh.copy()] if keep_iterates else None
+
+    def result(k, status):
+        w = Xh.shape[0] // s
+        return FactorizedResult(bA.V(w), Xh, bB.V(w), k, status, hist, xs, bA, bB)
+
+    for k in range(maxit):
+        e1, e2, e3 = (2 * k + 1) * s, (2 * k + 2) * s, (2 * k + 3) * s
+        Ph = pad_to(Rh, e1) + beta * (pad_to(Ph, e1) - pad_to(Uh, e1))
+        try:  # Arnoldi step 2k+1 -> V_{2k+2}: L(P)
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        LPh = small_sylvester(bA.Hk(2 * k + 2, 2 * k + 1), Ph, bB.Hk(2 * k + 2, 2 * k + 1))
+        d = inner(Rt, LPh[:s, :s])
+        if not np.isfinite(d) or d == 0.0:
+            return result(k, "breakdown")
+        alpha = rho / d
+        Yh = pad_to(Tph, e2) - pad_to(Rh, e2) - alpha * pad_to(Wh, e2) + alpha * LPh
+        Th = pad_to(Rh, e2) - alpha * LPh
+        try:  # Arnoldi step 2k+2 -> V_{2k+3}: L(T)
+            bA.step()
+            bB.step()
+        except Breakdown:
+            return result(k, "breakdown")
+        LTh = small_sylvester(bA.Hk(2 * k + 3, 2 * k + 2), Th, bB.Hk(2 * k + 3, 2 * k + 2))
+        if k == 0:
+            aa = inner(LTh, LTh)
+            if not np.isfinite(aa) or aa == 0.0:
+                return result(k, "breakdown")
+            zeta, eta = inner(LTh[:e2, :e2], Th) / aa, 0.0
+        else:
+            yy, tt_, yt = inner(Yh, Yh), inner(LTh[:e2, :e2], Th), inner(Yh, Th)
+            ty, aa = inner(LTh[:e2, :e2], Yh), inner(LTh, LTh)
+            den = aa * yy - ty * ty
+            if not np.isfinite(den) or den == 0.0:
+                return result(k, "breakdown")
+            zeta = (yy * tt_ - yt * ty) / den
+            eta = (aa * yt - ty * tt_) / den
+        if zeta == 0.0:
+            return result(k, "breakdown")
+        Uh = zeta * LPh + eta * (pad_to(Tph, e2) - pad_to(Rh, e2) + beta * pad_to(Uh, e2))
+        Zh = zeta * pad_to(Rh, e2) + eta * pad_to(Zh, e2) - alpha * Uh
+        Xh = pad_to(Xh, e2) + alpha * pad_to(Ph, e2) + Zh
+        Rh = pad_to(Th, e3) - eta * pad_to(Yh, e3) - zeta * LTh
+        rn = np.sqrt(inner(Rh, Rh))
+        hist.append(rn / r0)
+        if xs is not None:
+            xs.append(Xh.copy())
+        if not np.isfinite(rn):
+            return result(k + 1, "breakdown")
+        if rn <= r0 * tol:
+            return result(k + 1, "converged")
+        rho_new = inner(Rt, Rh[:s, :s])
+        if rho_new == 0.0:
+            return result(k + 1, "breakdown")
+        beta = (alpha / zeta) * (rho_new / rho)
+        rho = rho_new
+        Wh = LTh + beta * pad_to(LPh, e3)
+        Tph = Th
+    return result(maxit, "maxit")

@@ -1,5 +1,5 @@
-"""Matrix-oriented CG, BiCGSTAB, CGS and CR on full n x m iterates (Algorithms 2.1, 2.2; CGS
-and CR as Sec. 4 names them: Sonneveld 1989, Stiefel 1955).
+"""Matrix-oriented CG, BiCGSTAB, CGS, CR and GPBiCG on full n x m iterates (Algorithms 2.1,
+2.2; CGS, CR and GPBiCG as Sec. 4 names them: Sonneveld 1989, Stiefel 1955, Zhang 1997).
 
 Test infrastructure only (see ``oracle/__init__``).  These are the plain
 definitions that the factorized methods are mathematically equivalent to
@@ -172,4 +172,71 @@ def cr(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False)
         rho = rho_new
         P = R + beta * P
         LP = LR + beta * LP
+    return FullResult(X, maxit, "maxit", hist, its)
+
+
+def gpbicg(A, B, C: np.ndarray, tol: float, maxit: int, keep_iterates: bool = False,
+           eta_zero: bool = False, record: Optional[list] = None) -> FullResult:
+    """GPBiCG (Zhang 1997, generalized product-type BiCG) on the Kronecker system (eq. 1.2) in
+    the matrix operations of Sec. 2, X_0 = 0, R~_0 = R_0.  Sec. 4 names GPBiCG among the
+    methods the factorized approach applies to; the paper gives no listing, so this is the
+    published recurrence with its vectors read as n x m matrices.  Per iteration, with
+    L(Y) = A Y + Y B:
+
+        P = R + beta (P - U),  alpha = <R~_0, R> / <R~_0, L(P)>,
+        Y = T_prev - R - alpha W + alpha L(P),  T = R - alpha L(P),
+        (zeta, eta) minimise ||T - zeta L(T) - eta Y||  (eta = 0 in the first iteration),
+        U = zeta L(P) + eta (T_prev - R + beta U),  Z = zeta R + eta Z - alpha U,
+        X = X + alpha P + Z,  R = T - eta Y - zeta L(T),
+        beta = (alpha / zeta) <R~_0, R_new> / <R~_0, R_old>,  W = L(T) + beta L(P),  T_prev = T.
+
+    With ``eta_zero`` every eta is 0 and the recurrence is BiCGSTAB's (omega = zeta): a pin.
+    ``record`` (a list) receives (R_new, L(T), Y) of every iteration.
+    """
+    X = np.zeros_like(C)
+    R = C - sylvester_op(A, B, X)
+    Rt = R.copy()
+    P = np.zeros_like(C)
+    U = np.zeros_like(C)
+    W = np.zeros_like(C)
+    Z = np.zeros_like(C)
+    Tp = np.zeros_like(C)
+    beta = 0.0
+    rho = inner(Rt, R)
+    r0 = np.linalg.norm(R)
+    hist = [1.0]
+    its = [X.copy()] if keep_iterates else None
+    for k in range(maxit):
+        P = R + beta * (P - U)
+        LP = sylvester_op(A, B, P)
+        alpha = rho / inner(Rt, LP)
+        Y = Tp - R - alpha * W + alpha * LP
+        T = R - alpha * LP
+        LT = sylvester_op(A, B, T)
+        if k == 0 or eta_zero:
+            zeta = inner(LT, T) / inner(LT, LT)
+            eta = 0.0
+        else:
+            yy, tt_, yt = inner(Y, Y), inner(LT, T), inner(Y, T)
+            ty, aa = inner(LT, Y), inner(LT, LT)
+            den = aa * yy - ty * ty
+            zeta = (yy * tt_ - yt * ty) / den
+            eta = (aa * yt - ty * tt_) / den
+        U = zeta * LP + eta * (Tp - R + beta * U)
+        Z = zeta * R + eta * Z - alpha * U
+        X = X + alpha * P + Z
+        R = T - eta * Y - zeta * LT
+        if record is not None:
+            record.append((R.copy(), LT, Y))
+        rn = np.linalg.norm(R)
+        hist.append(rn / r0)
+        if its is not None:
+            its.append(X.copy())
+        if rn <= r0 * tol:
+            return FullResult(X, k + 1, "converged", hist, its)
+        rho_new = inner(Rt, R)
+        beta = (alpha / zeta) * (rho_new / rho)
+        rho = rho_new
+        W = LT + beta * LP
+        Tp = T
     return FullResult(X, maxit, "maxit", hist, its)

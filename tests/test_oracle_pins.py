@@ -525,3 +525,100 @@ def test_planted_cr_mistake_fails_the_minres_pin():
     spla.minres(kron_operator(A, B), C.flatten(order="F"), rtol=1e-300, maxiter=6,
                 callback=lambda x: xs.append(x.copy()))
     assert max(rel(its[k].flatten(order="F"), xs[k]) for k in range(6)) > 1e-3
+
+
+# -------------------------------------------- GPBiCG (Sec. 4 names it; Zhang 1997)
+def cd_pair():
+    A = wl.convdiff_3d(5, 1).to_scipy()
+    B = wl.convdiff_3d(4, 2).to_scipy()
+    C1, C2 = wl.rhs(125, 64, 2, 0)
+    return A, B, C1, C2
+
+
+def test_gpbicg_with_eta_zero_is_bicgstab():
+    """With eta = 0 in every step the GPBiCG recurrence is BiCGSTAB's (omega = zeta), itself
+    pinned above: this ties every term except the eta terms."""
+    A, B, C1, C2 = cd_pair()
+    g = mo.gpbicg(A, B, C1 @ C2.T, 1e-10, 200, keep_iterates=True, eta_zero=True)
+    b = mo.bicgstab(A, B, C1 @ C2.T, 1e-10, 200, keep_iterates=True)
+    assert g.iters == b.iters
+    for k in range(1, g.iters + 1):
+        assert rel(g.iterates[k], b.iterates[k]) < 1e-12, k
+
+
+def test_gpbicg_residual_is_orthogonal_to_LT_and_Y():
+    """zeta, eta minimise ||T - zeta L(T) - eta Y||: the new residual is orthogonal to both."""
+    A, B, C1, C2 = cd_pair()
+    rec = []
+    r = mo.gpbicg(A, B, C1 @ C2.T, 1e-10, 200, record=rec)
+    assert r.status == "converged" and len(rec) >= 5
+    for R, LT, Y in rec[1:]:
+        assert abs(mo.inner(R, LT)) <= 1e-12 * np.linalg.norm(R) * np.linalg.norm(LT)
+        assert abs(mo.inner(R, Y)) <= 1e-12 * np.linalg.norm(R) * np.linalg.norm(Y)
+
+
+def test_matrix_oriented_gpbicg_converges_to_exact():
+    A, B, C1, C2 = cd_pair()
+    r = mo.gpbicg(A, B, C1 @ C2.T, 1e-12, 200)
+    assert r.status == "converged"
+    assert rel(r.X, exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)) < 1e-9
+
+
+def test_factorized_gpbicg_equals_matrix_oriented_iterates():
+    A, B, C1, C2 = cd_pair()
+    rf = fz.factorized_gpbicg(A, B, C1, C2, 1e-10, 200, keep_iterates=True)
+    rm = mo.gpbicg(A, B, C1 @ C2.T, 1e-10, 200, keep_iterates=True)
+    assert rf.status == rm.status == "converged"
+    assert abs(rf.iters - rm.iters) <= 1
+    for k in range(1, min(12, rf.iters) + 1):
+        assert rf.Xhats[k].shape[0] == (2 * k) * 2
+        assert rel(rf.X_at(k, 2 * k), rm.iterates[k]) < 1e-10, k
+        assert rank_at_most(rm.iterates[k], 2 * k * 2)
+    np.testing.assert_allclose(rf.history[:12], rm.history[:12], rtol=1e-8)
+    assert rel(rf.X(), exact.kron_solve(A.toarray(), B.toarray(), C1 @ C2.T)) < 1e-8
+
+
+def test_factorized_gpbicg_diagonal_case_closed_form():
+    rng = np.random.default_rng(11)
+    a, b = rng.uniform(1.0, 3.0, 40), rng.uniform(1.0, 3.0, 30)
+    A, B = wl.diagonal(a).to_scipy(), wl.diagonal(b).to_scipy()
+    C1, C2 = wl.rhs(40, 30, 2, 3)
+    r = fz.factorized_gpbicg(A, B, C1, C2, 1e-11, 60)
+    assert r.status == "converged"
+    assert rel(r.X(), exact.diagonal_exact(a, b, C1 @ C2.T)) < 1e-9
+
+
+def test_planted_gpbicg_mistake_fails_the_orthogonality_pin():
+    """A zeta with two inner products swapped no longer solves the 2 x 2 least-squares
+    problem: the residual loses its orthogonality to L(T)."""
+    A, B, C1, C2 = cd_pair()
+    C = C1 @ C2.T
+    R = C.copy()
+    Rt, P, U, W, Z, Tp = R.copy(), 0 * R, 0 * R, 0 * R, 0 * R, 0 * R
+    beta, rho = 0.0, mo.inner(R, R)
+    worst = 0.0
+    for k in range(6):
+        P = R + beta * (P - U)
+        LP = mo.sylvester_op(A, B, P)
+        alpha = rho / mo.inner(Rt, LP)
+        Y = Tp - R - alpha * W + alpha * LP
+        T = R - alpha * LP
+        LT = mo.sylvester_op(A, B, T)
+        if k == 0:
+            zeta, eta = mo.inner(LT, T) / mo.inner(LT, LT), 0.0
+        else:
+            yy, tt_, yt, ty, aa = mo.inner(Y, Y), mo.inner(LT, T), mo.inner(Y, T), mo.inner(LT, Y), mo.inner(LT, LT)
+            den = aa * yy - ty * ty
+            zeta = (yy * tt_ - ty * yt * 0.5) / den  # planted: a wrong term in zeta
+            eta = (aa * yt - ty * tt_) / den
+        U = zeta * LP + eta * (Tp - R + beta * U)
+        Z = zeta * R + eta * Z - alpha * U
+        R = T - eta * Y - zeta * LT
+        if k > 0:
+            worst = max(worst, abs(mo.inner(R, LT)) / (np.linalg.norm(R) * np.linalg.norm(LT)))
+        rho_new = mo.inner(Rt, R)
+        beta = (alpha / zeta) * (rho_new / rho)
+        rho = rho_new
+        W = LT + beta * LP
+        Tp = T
+    assert worst > 1e-6
