@@ -281,16 +281,17 @@ def measure_mixed(p, stream, steps, warmup):
 
 
 def measure_methods(p, stream, steps, warmup):
-    """The other factorized methods (Sec. 4 names CGS and CR) at full size: CGS on the benchmarked
-    convection-diffusion operators, CG and CR on a symmetric workload of the same size class
+    """The other factorized methods (Sec. 4 names CR, CGS and GPBiCG) at full size: CGS and GPBiCG on
+    the benchmarked convection-diffusion operators, CG and CR on a symmetric workload of the same size class
     (A = L_512 + I/2, B = L_384 + I/2: 2D 5-point Laplacians, n = 262,144, m = 147,456, s = 4).
     Time to a relative residual of 1e-8 (mixed: true residual), FP64 and mixed."""
     out = {}
-    for prec in ("fp64", "mixed"):
-        t, info = timed_solves(p, stream, prec, steps, warmup, "cgs")
-        out[f"cgs_{prec}_convdiff3d_64^3_x_48^3_s4"] = {"value": t, "unit": "s", "status": info["status_name"],
-                                                        "iters_total": info["iters"], "width": info["width"],
-                                                        "true_rel_res": info["true_rel_res"]}
+    for meth in ("cgs", "gpbicg"):
+        for prec in ("fp64", "mixed"):
+            t, info = timed_solves(p, stream, prec, steps, warmup, meth)
+            out[f"{meth}_{prec}_convdiff3d_64^3_x_48^3_s4"] = {
+                "value": t, "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
+                "width": info["width"], "true_rel_res": info["true_rel_res"]}
     A, B = wl.laplacian_2d(512, 0.5), wl.laplacian_2d(384, 0.5)
     C1, C2 = wl.rhs(A.nrows, B.nrows, 4, 0)
     q = wl.Problem(name="laplace2d_512x384_s4", A=A, B=B, C1=C1, C2=C2, s=4, method="cg", tol=1e-8, maxit=300)

@@ -192,6 +192,18 @@ int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 int sylv_cr(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 
 /*
+ * Factorized GPBiCG (generalized product-type BiCG, Zhang 1997), the third method Sec. 4
+ * names; no listing in the paper, so the recurrence is GPBiCG on the Kronecker system
+ * (eq. 1.2) in the matrix operations of Sec. 2 (R~_0 = R_0; zeta, eta minimising
+ * ||T - zeta L(T) - eta Y|| with eta = 0 in the first step), factorized as Algorithm 4.2
+ * is: the same block Arnoldi bases (two steps per iteration), additions of padded small
+ * matrices (eq. 3.5), inner products of small matrices (eq. 3.6), two applications of the
+ * small operator of eq. 3.7 per iteration.  General A, B; returns V_{2k+2}, X^_{k+1},
+ * W_{2k+2} as sylv_bicgstab.  Batched handles: SYLV_EINVAL.  Otherwise as sylv_cg.
+ */
+int sylv_gpbicg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
+
+/*
  * Copies the factors of the last solve: V (n x r), X^ (r x r), W (m x r),
  * column-major, float64.  Any of V, Xhat, W may be NULL to skip it; *r
  * receives r (the call with all three NULL only queries r).  In the Lyapunov

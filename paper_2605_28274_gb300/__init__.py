@@ -2,7 +2,7 @@
 
 Argument marshalling only: every step of the solve runs in the CUDA kernels of
 ``lib/libsylv.so`` behind the C ABI declared in ``include/sylv.h``.  The
-functions keep the C names (``sylv_create``, ``sylv_cg``, ``sylv_bicgstab``, ``sylv_cgs``, ``sylv_cr``,
+functions keep the C names (``sylv_create``, ``sylv_cg``, ``sylv_bicgstab``, ``sylv_cgs``, ``sylv_cr``, ``sylv_gpbicg``,
 ``sylv_get_factors``, ``sylv_get_history``, ``sylv_get_hessenberg``,
 ``sylv_apply``, ``sylv_destroy``); ``Solver`` wraps a handle.
 
@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr",
-           "sylv_get_factors",
+           "sylv_gpbicg", "sylv_get_factors",
            "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
            "sylv_create_batch", "sylv_batch_instance", "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
@@ -88,7 +88,7 @@ def load(path: Optional[str] = None):
     lib.sylv_create.argtypes = [P(sylv_csr), P(sylv_csr), dp, dp, ctypes.c_int64, P(sylv_options),
                                 P(ctypes.c_void_p)]
     lib.sylv_create.restype = ctypes.c_int
-    for f in ("sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr"):
+    for f in ("sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr", "sylv_gpbicg"):
         getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, P(sylv_info)]
         getattr(lib, f).restype = ctypes.c_int
     lib.sylv_get_factors.argtypes = [ctypes.c_void_p, dp, dp, dp, P(ctypes.c_int64)]
@@ -192,6 +192,12 @@ def sylv_cgs(h, tol: float, maxit: int) -> sylv_info:
 def sylv_cr(h, tol: float, maxit: int) -> sylv_info:
     info = sylv_info()
     load().sylv_cr(h, tol, maxit, ctypes.byref(info))
+    return info
+
+
+def sylv_gpbicg(h, tol: float, maxit: int) -> sylv_info:
+    info = sylv_info()
+    load().sylv_gpbicg(h, tol, maxit, ctypes.byref(info))
     return info
 
 
@@ -399,6 +405,9 @@ class Solver:
 
     def cr(self, tol: float, maxit: int) -> dict:
         return sylv_cr(self.h, tol, maxit).as_dict()
+
+    def gpbicg(self, tol: float, maxit: int) -> dict:
+        return sylv_gpbicg(self.h, tol, maxit).as_dict()
 
     def factors(self, out=None):
         return sylv_get_factors(self.h, self.n, self.m, out=out)

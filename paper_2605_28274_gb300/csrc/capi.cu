@@ -68,7 +68,8 @@ struct Side {
   void* RinvT = nullptr;
 };
 
-enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3, M_CR = 4 };  // CGS: Arnoldi bases, CR: Lanczos
+enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3, M_CR = 4, M_GPBICG = 5 };  // CR: Lanczos, others Arnoldi
+inline bool arnoldi_method(int m) { return m == M_BICG || m == M_CGS || m == M_GPBICG; }
 inline bool lanczos_method(int m) { return m == M_CG || m == M_CR; }
 
 // Kernel classes timed by the optional profiler.
@@ -117,7 +118,8 @@ struct sylv_handle {
   int maxb = 0, cap_method = M_NONE;
   int64_t lds = 0;
   double *Xh = nullptr, *Rh = nullptr, *Ph = nullptr, *Qh = nullptr, *Sh = nullptr, *Th = nullptr, *Rt = nullptr;
-  double* Uh = nullptr;  // CGS only
+  double* Uh = nullptr;  // CGS, GPBiCG
+  double *gW = nullptr, *gZ = nullptr, *gTp = nullptr, *gY = nullptr, *gPart = nullptr;  // GPBiCG only
   DevState* st = nullptr;
   DevState* st_host = nullptr;  // pinned, 2 slots
   double* hist = nullptr;
@@ -206,6 +208,7 @@ void free_solve(sylv_handle* h) {
   }
   h->Hs = h->Gs = h->Zs = nullptr;
   h->Uh = nullptr;
+  h->gW = h->gZ = h->gTp = h->gY = h->gPart = nullptr;
   h->oz_scratch = nullptr;
 }
 
@@ -356,10 +359,9 @@ void prof_finish(sylv_handle* h, int iters) {
 constexpr int kOzakiMinR = 448;  // measured crossover with the CUDA-core float64 kernel
 
 int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
-  const bool want_oz =
-      (method == M_BICG || method == M_CGS) && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
+  const bool want_oz = arnoldi_method(method) && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
   if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE && (!want_oz || h->oz_scratch) &&
-      (method != M_CGS || h->Uh))
+      ((method != M_CGS && method != M_GPBICG) || h->Uh) && (method != M_GPBICG || h->gW))
     return SYLV_OK;
   free_solve(h);
   const int64_t s = h->s;
@@ -378,7 +380,14 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   TRY(alloc_solve(h, &h->Qh, l2));
   TRY(alloc_solve(h, &h->Sh, l2));
   TRY(alloc_solve(h, &h->Th, l2));
-  if (method == M_CGS) TRY(alloc_solve(h, &h->Uh, l2));
+  if (method == M_CGS || method == M_GPBICG) TRY(alloc_solve(h, &h->Uh, l2));
+  if (method == M_GPBICG) {
+    TRY(alloc_solve(h, &h->gW, l2));
+    TRY(alloc_solve(h, &h->gZ, l2));
+    TRY(alloc_solve(h, &h->gTp, l2));
+    TRY(alloc_solve(h, &h->gY, l2));
+    TRY(alloc_solve(h, &h->gPart, (size_t)5 * sylv::GP_ZETA_CTAS));
+  }
   TRY(alloc_solve(h, &h->Rt, 64));
   TRY(alloc_solve(h, &h->hist, (size_t)hist_need));
   // Gram partials: at most 2*SMs CTAs x (maxb * s * s)
@@ -531,6 +540,11 @@ sylv::SmallCtx small_ctx(sylv_handle* h) {
   c.Sh = h->Sh;
   c.Th = h->Th;
   c.Uh = h->Uh;
+  c.gW = h->gW;
+  c.gZ = h->gZ;
+  c.gTp = h->gTp;
+  c.gY = h->gY;
+  c.gPart = h->gPart;
   c.Rt = h->Rt;
   c.H = h->side[0].H;
   c.G = h->lyap ? h->side[0].H : h->side[1].H;
@@ -589,7 +603,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   cudaStream_t strm = h->stream;
   CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), strm));
   const size_t l2 = (size_t)(h->lds * h->lds) * sizeof(double);
-  for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th, h->Uh})
+  for (double* p : {h->Xh, h->Rh, h->Ph, h->Qh, h->Sh, h->Th, h->Uh, h->gW, h->gZ, h->gTp, h->gY})
     if (p) CU(cudaMemsetAsync(p, 0, l2, strm));
   for (int i = 0; i < nsides(h); ++i) CU(cudaMemsetAsync(h->side[i].H, 0, l2, strm));
   if (h->mixed) {  // split copies of H, G follow H's zero fill
@@ -705,6 +719,25 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       PROF(h, KC_SMALL_ELEM, e8 * (4.0 * q2 + 3.0 * t2), 4.0 * q2 + 4.0 * t2,
            sylv::launch_bicg_update(strm, c, k, rp, rpp));
       PROF(h, KC_SMALL_ELEM, e8 * 4.0 * t2, 4.0 * t2, sylv::launch_bicg_p(strm, c, rpp));
+    } else if (method == M_GPBICG) {  // the same bases and operator, the GPBiCG recurrences
+      const int e1 = (2 * k + 1) * s, e2 = e1 + s, e3 = e2 + s;
+      const double q1 = (double)e1 * e1, q2 = (double)e2 * e2, q3 = (double)e3 * e3;
+      PROF(h, KC_SMALL_ELEM, e8 * 4.0 * q1, 3.0 * q1, sylv::launch_gp_p(strm, c, e1));
+      basis_step<T>(h, 0, 2 * k, false);
+      basis_step<T>(h, 1, 2 * k, false);
+      TRY(small_wait_basis(0));
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q1 + q2), sylv::sylv_gemm_flops(e1, s),
+           sylv::launch_sylv_gemm(strm, c, e1, c.Ph, c.Qh, false));  // L(P)^
+      PROF(h, KC_SMALL_ELEM, 0.0, 0.0, sylv::launch_bicg_alpha(strm, c));
+      PROF(h, KC_SMALL_ELEM, e8 * 6.0 * q2, 6.0 * q2, sylv::launch_gp_ty(strm, c, e2));
+      basis_step<T>(h, 0, 2 * k + 1, false);
+      basis_step<T>(h, 1, 2 * k + 1, false);
+      TRY(small_wait_basis(1));
+      PROF(h, KC_SMALL_GEMM, e8 * (3.0 * q2 + q3), sylv::sylv_gemm_flops(e2, s),
+           sylv::launch_sylv_gemm(strm, c, e2, c.Th, c.Sh, false));  // L(T)^
+      PROF(h, KC_SMALL_ELEM, e8 * (3.0 * q2 + q3), 8.0 * q2 + 2.0 * q3, sylv::launch_gp_zeta(strm, c, k, e2));
+      PROF(h, KC_SMALL_ELEM, e8 * (10.0 * q2 + 4.0 * q3), 12.0 * q2 + 6.0 * q3, sylv::launch_gp_update(strm, c, k, e2));
+      PROF(h, KC_SMALL_ELEM, e8 * 5.0 * q3, 2.0 * q3, sylv::launch_gp_w(strm, c, e3));
     } else {  // M_CGS: the same bases and operator, the CGS recurrences on the small side
       const int r1 = (2 * k + 1) * s, rp = r1 + s, rpp = rp + s;
       const double q2 = (double)rp * rp, t2 = (double)rpp * rpp;
@@ -1556,6 +1589,11 @@ int sylv_cgs(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
 int sylv_cr(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
   g_err.clear();
   return solve(h, M_CR, tol, maxit, info);
+}
+
+int sylv_gpbicg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info) {
+  g_err.clear();
+  return solve(h, M_GPBICG, tol, maxit, info);
 }
 
 int sylv_create_batch(int32_t count, const sylv_csr* A, const sylv_csr* B, const double* const* C1,

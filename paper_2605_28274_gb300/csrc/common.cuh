@@ -22,11 +22,13 @@ enum Ticket : int {
   TK_CG_UPD = 1,
   TK_BI_T = 2,
   TK_BI_UPD = 3,
+  TK_GP_ZETA = 4,
   TK_NUM = 8
 };
 
 struct DevState {
-  double rho, alpha, beta, omega;
+  double rho, alpha, beta, omega;  // GPBiCG: omega holds zeta
+  double eta;    // GPBiCG only
   double r0;     // ||R^_0||_F
   double rnorm;  // ||R^_k||_F of the latest iterate
   double tol;

@@ -96,7 +96,9 @@ struct SmallCtx {
   int s;
   int64_t lds;
   double *Xh, *Rh, *Ph, *Qh, *Sh, *Th, *Rt;  // Rt: shadow residual R~_0 (s x s, ld s)
-  double* Uh;                                // CGS only: U^
+  double* Uh;                                // CGS, GPBiCG: U^
+  double *gW, *gZ, *gTp, *gY;                // GPBiCG only: W^, Z^, T_prev^, Y^
+  double* gPart;                             // GPBiCG: 5 x GP_ZETA_CTAS partials of the zeta/eta step
   const double* H;  // A-side block Hessenberg (ld ldh)
   const double* G;  // B^T-side (== H in the Lyapunov case)
   int64_t ldh;
@@ -145,6 +147,17 @@ void launch_cgs_q(cudaStream_t, const SmallCtx&, int rp);
 // beta and rho; cr_p forms P^ and L(P)^ (in the Q^ buffer, extent rpp) and alpha.  The update
 // of X^, R^ and the test is launch_cg_update(.., cr = true) with L(P)^ in place of Q^.
 void launch_cr_op(cudaStream_t, const SmallCtx&, int mode, int r, bool first);
+// Factorized GPBiCG (Sec. 4 names it; same bases and operator as Algorithm 4.2).  With
+// e1 = (2k+1)s, e2 = e1 + s: gp_p forms P^ (e1); the operator gives L(P)^ in Qh and
+// launch_bicg_alpha alpha; gp_ty forms Y^ (gY) and T^ (Th) (e2); the operator gives L(T)^ in
+// Sh; gp_zeta the five inner products, zeta and eta; gp_update U^, Z^, X^, R^, the test and
+// beta; gp_w W^ and T_prev^ (e3).
+constexpr int GP_ZETA_CTAS = 1024;
+void launch_gp_p(cudaStream_t, const SmallCtx&, int e1);
+void launch_gp_ty(cudaStream_t, const SmallCtx&, int e2);
+void launch_gp_zeta(cudaStream_t, const SmallCtx&, int k, int e2);
+void launch_gp_update(cudaStream_t, const SmallCtx&, int k, int e2);
+void launch_gp_w(cudaStream_t, const SmallCtx&, int e3);
 void launch_cr_p(cudaStream_t, const SmallCtx&, int rpp);
 void launch_cgs_update(cudaStream_t, const SmallCtx&, int k, int rpp);
 void launch_cgs_p(cudaStream_t, const SmallCtx&, int rpp);

@@ -657,6 +657,179 @@ __global__ void __launch_bounds__(NT) cgs_p_kernel(const DevState* st, int rpp, 
   P[i] = u + beta * (q + beta * P[i]);
 }
 
+// ---------------------------------------------------------------- factorized GPBiCG
+// The GPBiCG recurrence on padded small matrices (eq. 3.5; <R~_0, .> on the leading s x s
+// block, eq. 3.6), with extents e1 = (2k+1)s (P^, R^), e2 = e1 + s (L(P)^, T^, Y^, U^, Z^, X^)
+// and e3 = e2 + s (L(T)^, W^, new R^).  zeta lives in DevState::omega, eta in DevState::eta.
+
+// P^ <- R^ + beta (P^ - U^) over extent e1.
+__global__ void __launch_bounds__(NT) gp_p_kernel(const DevState* st, int e1, double* __restrict__ P,
+                                                  const double* __restrict__ R, const double* __restrict__ U,
+                                                  int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= e1) return;
+  const int64_t i = a + (int64_t)b * lds;
+  P[i] = R[i] + st->beta * (P[i] - U[i]);
+}
+
+// Y^ <- T_prev^ - R^ - alpha W^ + alpha L(P)^,  T^ <- R^ - alpha L(P)^  over extent e2.
+__global__ void __launch_bounds__(NT) gp_ty_kernel(const DevState* st, int e2, double* __restrict__ Y,
+                                                   double* __restrict__ T, const double* __restrict__ Tp,
+                                                   const double* __restrict__ R, const double* __restrict__ W,
+                                                   const double* __restrict__ LP, int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= e2) return;
+  const int64_t i = a + (int64_t)b * lds;
+  const double alpha = st->alpha, lp = LP[i], r = R[i];
+  Y[i] = Tp[i] - r - alpha * W[i] + alpha * lp;
+  T[i] = r - alpha * lp;
+}
+
+// zeta, eta minimise ||T - zeta L(T) - eta Y||: the five inner products <Y,Y>, <L(T),T>,
+// <Y,T>, <L(T),Y> (extent e2) and <L(T),L(T)> (extent e3), per-CTA partials summed in CTA
+// order by the last CTA.  The first iteration has eta = 0 (zeta = <L(T),T> / <L(T),L(T)>).
+__global__ void __launch_bounds__(NT) gp_zeta_kernel(DevState* st, int k, int e2, int e3,
+                                                     const double* __restrict__ Y, const double* __restrict__ T,
+                                                     const double* __restrict__ LT, int64_t lds,
+                                                     double* __restrict__ part) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  double yy = 0.0, tt = 0.0, yt = 0.0, ty = 0.0, aa = 0.0;
+  const int64_t E = (int64_t)e3 * e3;
+  for (int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x; q < E; q += (int64_t)gridDim.x * NT) {
+    const int a = (int)(q % e3), b = (int)(q / e3);
+    const int64_t i = a + (int64_t)b * lds;
+    const double lt = LT[i];
+    aa += lt * lt;
+    if (a < e2 && b < e2) {
+      const double y = Y[i], t = T[i];
+      yy += y * y;
+      tt += lt * t;
+      yt += y * t;
+      ty += lt * y;
+    }
+  }
+  yy = block_sum(yy, sh);
+  tt = block_sum(tt, sh);
+  yt = block_sum(yt, sh);
+  ty = block_sum(ty, sh);
+  aa = block_sum(aa, sh);
+  if (threadIdx.x == 0) {
+    double* o = part + 5 * (int64_t)blockIdx.x;
+    o[0] = yy;
+    o[1] = tt;
+    o[2] = yt;
+    o[3] = ty;
+    o[4] = aa;
+  }
+  if (last_cta(&st->tickets[TK_GP_ZETA], &last_sh) && threadIdx.x == 0) {
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c < (int)gridDim.x; ++c)
+      for (int j = 0; j < 5; ++j) v[j] += __ldcg(part + 5 * (int64_t)c + j);
+    double zeta, eta;
+    if (k == 0) {
+      zeta = v[1] / v[4];
+      eta = 0.0;
+    } else {
+      const double den = v[4] * v[0] - v[3] * v[3];
+      zeta = (v[0] * v[1] - v[2] * v[3]) / den;
+      eta = (v[4] * v[2] - v[3] * v[1]) / den;
+    }
+    if (!isfinite(zeta) || !isfinite(eta)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 30;
+    } else if (zeta == 0.0) {
+      st->status = ST_BREAKDOWN;
+      st->breakdown_where = 31;
+    } else {
+      st->omega = zeta;
+      st->eta = eta;
+    }
+  }
+}
+
+// With the old beta, U^, Z^, R^: U^ <- zeta L(P)^ + eta (T_prev^ - R^ + beta U^), Z^ <- zeta R^ +
+// eta Z^ - alpha U^, X^ <- X^ + alpha P^ + Z^ (extent e2); R^ <- T^ - eta Y^ - zeta L(T)^ (e3);
+// then the test, rho_{k+1} = <R~_0, R^(1:s,1:s)> and beta = (alpha / zeta) rho_{k+1} / rho_k.
+__global__ void __launch_bounds__(NT) gp_update_kernel(DevState* st, double* hist, int k, int e2, int e3, int s,
+                                                       double* __restrict__ X, double* __restrict__ R,
+                                                       double* __restrict__ U, double* __restrict__ Z,
+                                                       const double* __restrict__ P, const double* __restrict__ LP,
+                                                       const double* __restrict__ Tp, const double* __restrict__ T,
+                                                       const double* __restrict__ Y, const double* __restrict__ LT,
+                                                       const double* __restrict__ Rt, int64_t lds,
+                                                       double* partials) {
+  if (stopped(st)) return;
+  __shared__ double sh[32];
+  __shared__ int last_sh;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  const double alpha = st->alpha, beta = st->beta, zeta = st->omega, eta = st->eta;
+  double rr = 0.0;
+  if (a < e3) {
+    const int64_t i = a + (int64_t)b * lds;
+    const double r_old = R[i];
+    if (a < e2 && b < e2) {
+      const double u = zeta * LP[i] + eta * (Tp[i] - r_old + beta * U[i]);
+      const double z = zeta * r_old + eta * Z[i] - alpha * u;
+      U[i] = u;
+      Z[i] = z;
+      X[i] = X[i] + alpha * P[i] + z;
+    }
+    const double v = T[i] - eta * Y[i] - zeta * LT[i];
+    R[i] = v;
+    rr = v * v;
+  }
+  rr = block_sum(rr, sh);
+  const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+  if (threadIdx.x == 0) partials[bid] = rr;
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+    const int nb = gridDim.x * gridDim.y;
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
+    const double rn = sqrt(tot);
+    hist[k + 1] = rn / st->r0;
+    st->rnorm = rn;
+    st->iters = k + 1;
+    if (!isfinite(rn)) {
+      st->status = ST_NONFINITE;
+      st->breakdown_where = 32;
+    } else if (rn <= st->r0 * st->tol) {
+      st->status = ST_CONVERGED;
+    } else {
+      double rho_new = 0.0;
+      for (int t = 0; t < s; ++t)
+        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+      if (rho_new == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 33;
+      } else {
+        st->beta = (alpha / zeta) * (rho_new / st->rho);
+        st->rho = rho_new;
+      }
+    }
+  }
+}
+
+// W^ <- L(T)^ + beta L(P)^, T_prev^ <- T^  over extent e3 (the new beta).
+__global__ void __launch_bounds__(NT) gp_w_kernel(const DevState* st, int e3, double* __restrict__ W,
+                                                  double* __restrict__ Tp, const double* __restrict__ LT,
+                                                  const double* __restrict__ LP, const double* __restrict__ T,
+                                                  int64_t lds) {
+  if (stopped(st)) return;
+  const int a = blockIdx.x * NT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (a >= e3) return;
+  const int64_t i = a + (int64_t)b * lds;
+  W[i] = LT[i] + st->beta * LP[i];
+  Tp[i] = T[i];
+}
+
 dim3 elem_grid(int rows, int cols) { return dim3((unsigned)((rows + NT - 1) / NT), (unsigned)cols); }
 
 }  // namespace
@@ -674,6 +847,32 @@ void launch_cgs_q(cudaStream_t strm, const SmallCtx& c, int rp) {
 void launch_cgs_update(cudaStream_t strm, const SmallCtx& c, int k, int rpp) {
   cgs_update_kernel<<<counted(elem_grid(rpp, rpp)), NT, 0, strm>>>(c.st, c.hist, k, rpp, c.s, c.Rh, c.Sh, c.Rt,
                                                                    c.lds, c.partials);
+}
+
+void launch_gp_p(cudaStream_t strm, const SmallCtx& c, int e1) {
+  gp_p_kernel<<<counted(elem_grid(e1, e1)), NT, 0, strm>>>(c.st, e1, c.Ph, c.Rh, c.Uh, c.lds);
+}
+
+void launch_gp_ty(cudaStream_t strm, const SmallCtx& c, int e2) {
+  gp_ty_kernel<<<counted(elem_grid(e2, e2)), NT, 0, strm>>>(c.st, e2, c.gY, c.Th, c.gTp, c.Rh, c.gW, c.Qh, c.lds);
+}
+
+void launch_gp_zeta(cudaStream_t strm, const SmallCtx& c, int k, int e2) {
+  const int e3 = e2 + c.s;
+  const int64_t E = (int64_t)e3 * e3;
+  const unsigned g = (unsigned)std::min<int64_t>((E + NT - 1) / NT, GP_ZETA_CTAS);
+  gp_zeta_kernel<<<counted(g), NT, 0, strm>>>(c.st, k, e2, e3, c.gY, c.Th, c.Sh, c.lds, c.gPart);
+}
+
+void launch_gp_update(cudaStream_t strm, const SmallCtx& c, int k, int e2) {
+  const int e3 = e2 + c.s;
+  gp_update_kernel<<<counted(elem_grid(e3, e3)), NT, 0, strm>>>(c.st, c.hist, k, e2, e3, c.s, c.Xh, c.Rh, c.Uh,
+                                                                c.gZ, c.Ph, c.Qh, c.gTp, c.Th, c.gY, c.Sh, c.Rt,
+                                                                c.lds, c.partials);
+}
+
+void launch_gp_w(cudaStream_t strm, const SmallCtx& c, int e3) {
+  gp_w_kernel<<<counted(elem_grid(e3, e3)), NT, 0, strm>>>(c.st, e3, c.gW, c.gTp, c.Sh, c.Qh, c.Th, c.lds);
 }
 
 void launch_cgs_p(cudaStream_t strm, const SmallCtx& c, int rpp) {
