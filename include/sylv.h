@@ -36,7 +36,9 @@ typedef enum {
   SYLV_ENOMEM = 2,     /* device allocation failed */
   SYLV_ENOTCONV = 3,   /* maxit reached; the factors hold the last iterate */
   SYLV_EBREAKDOWN = 4, /* zero denominator (CG: <P^,Q^> <= 0; BiCGSTAB: <R~0,Q^(1:s,1:s)> = 0,
-                          omega = 0, rho = 0) or a block that lost part of its rank */
+                          omega = 0, rho = 0) or a rank-deficient C1 or C2; a later basis block
+                          that loses part of its rank is deflated (its dependent columns become
+                          zero basis columns), not a breakdown */
   SYLV_ENONFINITE = 5, /* NaN/Inf in the iteration (e.g. from non-finite inputs) */
   SYLV_ETIMEOUT = 6,   /* the host gave up waiting for the device (sylv_options.timeout_s) */
   SYLV_ECUDA = 7,      /* a CUDA runtime call failed */

@@ -43,6 +43,32 @@ def thin_qr(Y: np.ndarray):
     return Q * d[None, :], R * d[:, None]
 
 
+def deflating_qr(Y: np.ndarray, thr: float):
+    """QR of a block whose columns may be (numerically) dependent: column by column, each
+    column is orthogonalised twice against the columns kept so far; if what remains has norm
+    <= thr the column is dropped (its Q column and its R row are zero, its R column keeps the
+    coefficients on the kept columns, so Y = Q R still holds), otherwise it is normalised
+    (diag(R) > 0).  The dropped columns stay zero in every later basis block (their images
+    are zero), which keeps all shapes of Algorithms 4.1/4.2 and V X^ W^T unchanged."""
+    n, s = Y.shape
+    Q = np.zeros((n, s))
+    R = np.zeros((s, s))
+    kept = []
+    for j in range(s):
+        r = Y[:, j].copy()
+        for _ in range(2):
+            if kept:
+                c = Q[:, kept].T @ r
+                r -= Q[:, kept] @ c
+                R[kept, j] += c
+        nr = np.linalg.norm(r)
+        if nr > thr:
+            Q[:, j] = r / nr
+            R[j, j] = nr
+            kept.append(j)
+    return Q, R
+
+
 def pad(M: np.ndarray, t: int) -> np.ndarray:
     """[[M, O], [O, O]]: M in the top-left corner of a matrix t rows/cols larger."""
     out = np.zeros((M.shape[0] + t, M.shape[1] + t))
@@ -72,6 +98,7 @@ class BlockKrylovBasis:
         self.blocks: List[np.ndarray] = [V1]
         self.H = np.zeros((self.s, 0))  # H_{j+1, j} grows to (j+1)s x js
         self.exhausted = False
+        self.deflated = 0  # basis columns dropped by partial losses of rank
 
     @property
     def nblocks(self) -> int:
@@ -122,7 +149,9 @@ class BlockKrylovBasis:
             return
         Q, R = thin_qr(Y)
         if np.min(np.abs(np.diag(R))) <= self.delta * nu:
-            raise Breakdown(f"partial rank loss in block {j + 1}")
+            # partial loss of rank: the dependent columns are deflated to zero columns
+            Q, R = deflating_qr(Y, self.delta * nu)
+            self.deflated += int(np.sum(np.diag(R) == 0.0))
         Hn[j * s:(j + 1) * s, (j - 1) * s:j * s] = R
         self.blocks.append(Q)
         self.H = Hn

@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
     R[threadIdx.x] = 0.0;
     Ri[threadIdx.x] = 0.0;
     Pm[threadIdx.x] = 0.0;
+    if (threadIdx.x < 8) dinv[threadIdx.x] = 0.0;
     S[threadIdx.x] = threadIdx.x < E ? G[threadIdx.x] : 0.0;
     R1s[threadIdx.x] = (a.pass == 2 && threadIdx.x < E) ? a.R1[threadIdx.x] : 0.0;
   }
@@ -460,17 +461,23 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
     }
     if (!bad && !exh) {
       // right-looking Cholesky G = R^T R (upper R, positive diagonal); the updates of each
-      // entry subtract the same terms in the same order as the left-looking form
+      // entry subtract the same terms in the same order as the left-looking form.  A pivot
+      // <= thr is a column (numerically) dependent on the earlier ones: it is deflated -- its
+      // R row, R^-1 row and column stay zero, so its basis column becomes zero and stays zero
+      // in every later block -- except in the QR of C1, C2, where it is a breakdown.
       const double thr = (a.pass == 1) ? a.delta * a.delta * nu2 : 0.0;
       for (int j = 0; j < s; ++j) {
         const double d = S[j * s + j];
         if (!(d > thr)) {  // the same value in every lane: a uniform branch
-          bad = 1;
-          if (lane == 0) {
-            st->status = ST_BREAKDOWN;
-            st->breakdown_where = 10 + a.side;
+          if (a.setup) {
+            bad = 1;
+            if (lane == 0) {
+              st->status = ST_BREAKDOWN;
+              st->breakdown_where = 10 + a.side;
+            }
+            break;
           }
-          break;
+          continue;
         }
         const double rjj = sqrt(d), rinv = 1.0 / rjj;
         if (lane == j) {

@@ -622,3 +622,51 @@ def test_planted_gpbicg_mistake_fails_the_orthogonality_pin():
         W = LT + beta * LP
         Tp = T
     assert worst > 1e-6
+
+
+# ------------------------------------------------- partial loss of rank (deflation)
+def rank_losing_problem():
+    """C1 = [c, A c, x]: the second basis block contains A c, already in the first block's span,
+    so one column of every later block is (exactly, up to rounding) dependent."""
+    A = wl.convdiff_3d(6, 1).to_scipy()
+    B = wl.convdiff_3d(5, 2).to_scipy()
+    rng = np.random.default_rng(3)
+    c = rng.standard_normal(A.shape[0])
+    C1 = np.column_stack([c, A @ c, rng.standard_normal(A.shape[0])])
+    C2 = rng.standard_normal((B.shape[0], 3))
+    return A, B, C1, C2
+
+
+def test_partial_rank_loss_deflates_to_zero_columns():
+    A, B, C1, C2 = rank_losing_problem()
+    r = fz.factorized_bicgstab(A, B, C1, C2, 1e-10, 300)
+    assert r.status == "converged" and r.basisA.deflated > 0
+    V = r.basisA.V()
+    norms = np.linalg.norm(V, axis=0)
+    zero = norms == 0.0
+    assert zero.sum() == r.basisA.deflated and not zero[:3].any()
+    Vk = V[:, ~zero]
+    assert np.abs(Vk.T @ Vk - np.eye(Vk.shape[1])).max() < 1e-12  # the kept columns stay orthonormal
+    k = V.shape[1] - 3
+    assert np.abs(A @ V[:, :k] - V @ r.basisA.H[: V.shape[1], :k]).max() < 1e-12  # eq. 3.4 still holds
+    assert rel(r.X(), exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)) < 1e-8
+
+
+@pytest.mark.parametrize("method", ["cgs", "gpbicg"])
+def test_partial_rank_loss_other_arnoldi_methods(method):
+    A, B, C1, C2 = rank_losing_problem()
+    r = getattr(fz, "factorized_" + method)(A, B, C1, C2, 1e-10, 300)
+    assert r.status == "converged" and r.basisA.deflated > 0
+    assert rel(r.X(), exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)) < 1e-8
+
+
+def test_partial_rank_loss_lanczos_methods():
+    A, B = wl.laplacian_2d(8).to_scipy(), wl.laplacian_2d(7).to_scipy()
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal(64)
+    C1, C2 = np.column_stack([c, A @ c]), rng.standard_normal((49, 2))
+    X = exact.bartels_stewart(A.toarray(), B.toarray(), C1 @ C2.T)
+    for f in (fz.factorized_cg, fz.factorized_cr):
+        r = f(A, B, C1, C2, 1e-10, 300)
+        assert r.status == "converged" and r.basisA.deflated > 0
+        assert rel(r.X(), X) < 1e-8
