@@ -670,3 +670,37 @@ def test_partial_rank_loss_lanczos_methods():
         r = f(A, B, C1, C2, 1e-10, 300)
         assert r.status == "converged" and r.basisA.deflated > 0
         assert rel(r.X(), X) < 1e-8
+
+
+# ------------------------------------------------ final low-rank compression of X
+def test_compression_is_the_best_low_rank_approximation():
+    """Eckart-Young on a formed X: the compressed factors reproduce numpy's truncated SVD of X,
+    and ||X - X_q||_F equals the discarded singular values' norm, within tol * ||X||_F."""
+    from oracle import compress
+
+    A = wl.convdiff_3d(6, 1).to_scipy()
+    B = wl.convdiff_3d(5, 2).to_scipy()
+    C1, C2 = wl.rhs(216, 125, 2, 0)
+    r = fz.factorized_bicgstab(A, B, C1, C2, 1e-10, 300)
+    X = r.X()
+    for tol in (1e-2, 1e-5, 1e-9):
+        Vq, sq, Wq = compress.compress(r.V, r.Xhat, r.W, tol)
+        Xq = (Vq * sq) @ Wq.T
+        sx = np.linalg.svd(X, compute_uv=False)
+        q = compress.truncation_rank(sx, tol)
+        assert len(sq) == q
+        np.testing.assert_allclose(sq, sx[:q], rtol=1e-9, atol=1e-12 * sx[0])
+        err = np.linalg.norm(X - Xq)
+        assert abs(err - np.sqrt(np.sum(sx[q:] ** 2))) <= 1e-9 * np.linalg.norm(X)
+        assert err <= tol * np.linalg.norm(X) * (1 + 1e-9)
+        assert np.abs(Vq.T @ Vq - np.eye(q)).max() < 1e-12  # orthonormal compressed factors
+
+
+def test_truncation_rank_rule():
+    from oracle import compress
+
+    sv = np.array([4.0, 3.0, 0.0])
+    assert compress.truncation_rank(sv, 0.0) == 2
+    assert compress.truncation_rank(sv, 0.6) == 1  # ||(3, 0)|| = 3 <= 0.6 * 5
+    assert compress.truncation_rank(sv, 0.59) == 2
+    assert compress.truncation_rank(sv, 1.0) == 0
