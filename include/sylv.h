@@ -214,6 +214,20 @@ int sylv_gpbicg(sylv_handle* h, double tol, int32_t maxit, sylv_info* info);
 int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t* r);
 
 /*
+ * Final low-rank compression of the last solve's X = V X^ W^T (float64 BiCGSTAB, CGS or
+ * GPBiCG, whose block Arnoldi bases are orthonormal; deflated zero columns allowed).  The
+ * paper has no counterpart (its methods return the factors as built).  Computes the
+ * SVD X^ = U S Z^T on the device (one-sided Jacobi) and keeps the smallest rank q whose
+ * discarded singular values have norm <= tol * ||X||_F -- the best rank-q approximation,
+ * ||X - X_q||_F = that norm.  Afterwards sylv_get_factors returns V U_q (n x q), diag(s_q)
+ * and W Z_q (m x q) until the next solve; *q receives q.
+ * Errors: SYLV_EINVAL (mixed or Lanczos solves, refinement rounds, batched handles, tol < 0),
+ * SYLV_ESTATE (no solve yet, or already compressed), SYLV_ENOMEM, SYLV_ENOTCONV (the Jacobi
+ * iteration did not converge in 100 sweeps), SYLV_ECUDA.
+ */
+int sylv_compress(sylv_handle* h, double tol, int64_t* q);
+
+/*
  * Residual history of the last solve: hist[0] = 1, hist[k] = ||R^_k||/||R^_0||.
  * Writes min(cap, len) values; *len receives the full length (hist may be NULL).
  */

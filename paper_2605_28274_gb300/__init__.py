@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr",
-           "sylv_gpbicg", "sylv_get_factors",
+           "sylv_gpbicg", "sylv_compress", "sylv_get_factors",
            "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
            "sylv_create_batch", "sylv_batch_instance", "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
@@ -91,6 +91,8 @@ def load(path: Optional[str] = None):
     for f in ("sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr", "sylv_gpbicg"):
         getattr(lib, f).argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, P(sylv_info)]
         getattr(lib, f).restype = ctypes.c_int
+    lib.sylv_compress.argtypes = [ctypes.c_void_p, ctypes.c_double, P(ctypes.c_int64)]
+    lib.sylv_compress.restype = ctypes.c_int
     lib.sylv_get_factors.argtypes = [ctypes.c_void_p, dp, dp, dp, P(ctypes.c_int64)]
     lib.sylv_get_factors.restype = ctypes.c_int
     lib.sylv_get_history.argtypes = [ctypes.c_void_p, dp, ctypes.c_int64, P(ctypes.c_int64)]
@@ -199,6 +201,14 @@ def sylv_gpbicg(h, tol: float, maxit: int) -> sylv_info:
     info = sylv_info()
     load().sylv_gpbicg(h, tol, maxit, ctypes.byref(info))
     return info
+
+
+def sylv_compress(h, tol: float) -> int:
+    q = ctypes.c_int64(0)
+    rc = load().sylv_compress(h, tol, ctypes.byref(q))
+    if rc != SYLV_OK:
+        raise SylvError(rc, "sylv_compress")
+    return int(q.value)
 
 
 def sylv_get_factors(h, n: int, m: int, want=("V", "X", "W"), out=None):
@@ -408,6 +418,10 @@ class Solver:
 
     def gpbicg(self, tol: float, maxit: int) -> dict:
         return sylv_gpbicg(self.h, tol, maxit).as_dict()
+
+    def compress(self, tol: float) -> int:
+        """Replaces the factors of the last solve by rank-q ones (see sylv_compress); returns q."""
+        return sylv_compress(self.h, tol)
 
     def factors(self, out=None):
         return sylv_get_factors(self.h, self.n, self.m, out=out)

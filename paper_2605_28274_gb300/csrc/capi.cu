@@ -130,6 +130,11 @@ struct sylv_handle {
   double *Hs = nullptr, *Gs = nullptr, *Zs = nullptr;
   int split_cols = 0;  // columns of H, G split so far in this solve
   void* oz_scratch = nullptr;  // digit planes of the tensor-core small products
+  // sylv_compress: rank-q factors (column-major, device) that sylv_get_factors returns until the
+  // next solve; comp_q < 0: not compressed
+  double *comp_V = nullptr, *comp_W = nullptr;
+  std::vector<double> comp_s;
+  int64_t comp_q = -1;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   Prof prof;
   cudaStream_t prof_stream = nullptr;  // stream the profiler records on (null: h->stream)
@@ -195,6 +200,14 @@ int alloc_fixed(sylv_handle* h, P** p, size_t count) {
 template <typename P>
 int alloc_solve(sylv_handle* h, P** p, size_t count) {
   return dev_alloc(h, h->solve_allocs, (void**)p, count * sizeof(P));
+}
+
+void free_compressed(sylv_handle* h) {
+  if (h->comp_V) cudaFree(h->comp_V);
+  if (h->comp_W) cudaFree(h->comp_W);
+  h->comp_V = h->comp_W = nullptr;
+  h->comp_s.clear();
+  h->comp_q = -1;
 }
 
 void free_solve(sylv_handle* h) {
@@ -1466,6 +1479,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
 int solve(sylv_handle* h, int method, double tol, int32_t maxit, sylv_info* info) {
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
   if (info) std::memset(info, 0, sizeof(*info));
+  free_compressed(h);
   if (!h->batch.empty()) {
     if (method != M_CG) return fail(SYLV_EINVAL, "batched handles run factorized CG (Lyapunov) only");
     return batch_cg(h, tol, maxit, info);
@@ -1666,6 +1680,19 @@ int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t
   if (!h) return fail(SYLV_EINVAL, "NULL handle");
   if (!h->batch.empty()) return fail(SYLV_EINVAL, "batched handle: use sylv_batch_instance");
   if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
+  if (h->comp_q >= 0) {  // compressed: V_q, diag(s_q), W_q
+    const int64_t q = h->comp_q;
+    if (r) *r = q;
+    if (q == 0) return SYLV_OK;
+    const int64_t n = h->side[0].n, m = h->side[h->lyap ? 0 : 1].n;
+    if (Xhat) {
+      std::memset(Xhat, 0, (size_t)q * q * sizeof(double));
+      for (int64_t i = 0; i < q; ++i) Xhat[i + i * q] = h->comp_s[i];
+    }
+    if (V) CU(cudaMemcpy(V, h->comp_V, (size_t)n * q * sizeof(double), cudaMemcpyDeviceToHost));
+    if (W) CU(cudaMemcpy(W, h->comp_W, (size_t)m * q * sizeof(double), cudaMemcpyDeviceToHost));
+    return SYLV_OK;
+  }
   const int64_t R = h->total_width;
   if (r) *r = R;
   if (R == 0) return SYLV_OK;
@@ -1692,6 +1719,126 @@ int sylv_get_factors(sylv_handle* h, double* V, double* Xhat, double* W, int64_t
     off += w;
   }
   return SYLV_OK;
+}
+
+constexpr int kJacobiSweeps = 100;  // sweep limit of the compression's Jacobi SVD
+
+int sylv_compress(sylv_handle* h, double tol, int64_t* q_out) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (!h->batch.empty()) return fail(SYLV_EINVAL, "batched handle: compression needs a single solve");
+  if (h->method == M_NONE) return fail(SYLV_ESTATE, "no solve yet");
+  if (!(tol >= 0.0)) return fail(SYLV_EINVAL, "tol must be >= 0");
+  if (h->mixed || !arnoldi_method(h->method) || !h->subs.empty())
+    return fail(SYLV_EINVAL, "compression needs the orthonormal float64 bases of BiCGSTAB, CGS or GPBiCG");
+  if (h->comp_q >= 0) return fail(SYLV_ESTATE, "already compressed");
+  const int r = (int)h->width;
+  cudaStream_t strm = h->stream;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() {
+    for (void* p : tmp) cudaFree(p);
+  };
+  auto dalloc = [&](void** p, size_t bytes) -> int {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SYLV_ENOMEM, "compression buffers");
+    }
+    tmp.push_back(*p);
+    return SYLV_OK;
+  };
+  int rc = SYLV_OK;
+  double *G = nullptr, *Z = nullptr, *sig = nullptr, *scale = nullptr;
+  int *pairs = nullptr, *rotated = nullptr, *cols = nullptr;
+  const size_t rr = (size_t)std::max(r, 1) * std::max(r, 1);
+  std::vector<int> sched;
+  sylv::jacobi_schedule(r, sched);
+  if ((rc = dalloc((void**)&G, rr * 8)) || (rc = dalloc((void**)&Z, rr * 8)) || (rc = dalloc((void**)&sig, r * 8 + 8)) ||
+      (rc = dalloc((void**)&scale, r * 8 + 8)) || (rc = dalloc((void**)&cols, r * 4 + 4)) ||
+      (rc = dalloc((void**)&rotated, 4)) || (rc = dalloc((void**)&pairs, sched.size() * 4 + 4))) {
+    cleanup();
+    return rc;
+  }
+  auto run = [&]() -> int {
+    if (r > 0) {
+      CU(cudaMemcpy2DAsync(G, (size_t)r * 8, h->Xh, (size_t)h->lds * 8, (size_t)r * 8, r, cudaMemcpyDeviceToDevice,
+                           strm));
+      std::vector<double> eye((size_t)r * r, 0.0);
+      for (int i = 0; i < r; ++i) eye[(size_t)i * r + i] = 1.0;
+      CU(cudaMemcpyAsync(Z, eye.data(), rr * 8, cudaMemcpyHostToDevice, strm));
+      CU(cudaMemcpyAsync(pairs, sched.data(), sched.size() * 4, cudaMemcpyHostToDevice, strm));
+      const int r2 = r + (r & 1);
+      // ||X^||_F for the rounding floor of the column norms
+      sylv::launch_column_norms(strm, r, G, r, sig);
+      std::vector<double> c0(r);
+      CU(cudaMemcpyAsync(c0.data(), sig, (size_t)r * 8, cudaMemcpyDeviceToHost, strm));
+      CU(cudaStreamSynchronize(strm));
+      double fro2 = 0.0;
+      for (double v : c0) fro2 += v * v;
+      const double floor_ = (double)r * 2.220446049250313e-16 * std::sqrt(fro2), tau = floor_ * floor_;
+      int sweeps = 0;
+      for (; sweeps < kJacobiSweeps; ++sweeps) {  // one-sided Jacobi: sweep until no pair rotates
+        CU(cudaMemsetAsync(rotated, 0, 4, strm));
+        for (int round = 0; round < r2 - 1; ++round)
+          sylv::launch_jacobi_round(strm, r, G, Z, r, pairs + (size_t)round * r2, 1e-14, tau, rotated);
+        int hrot = 0;
+        CU(cudaMemcpyAsync(&hrot, rotated, 4, cudaMemcpyDeviceToHost, strm));
+        CU(cudaStreamSynchronize(strm));
+        if (hrot == 0) break;
+      }
+      if (sweeps == kJacobiSweeps) return fail(SYLV_ENOTCONV, "Jacobi SVD did not converge");
+      sylv::launch_column_norms(strm, r, G, r, sig);
+    }
+    std::vector<double> s(r);
+    if (r > 0) CU(cudaMemcpyAsync(s.data(), sig, (size_t)r * 8, cudaMemcpyDeviceToHost, strm));
+    CU(cudaStreamSynchronize(strm));
+    std::vector<int> perm(r);
+    for (int i = 0; i < r; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return s[a] > s[b]; });
+    // q: the smallest rank whose discarded singular values have norm <= tol * ||s||
+    std::vector<double> tail(r + 1, 0.0);
+    for (int i = r - 1; i >= 0; --i) tail[i] = tail[i + 1] + s[perm[i]] * s[perm[i]];
+    const double total = tail[0];  // the same sum, so tol >= 1 gives q = 0
+    int q = r;
+    for (int k = 0; k <= r; ++k)
+      if (std::sqrt(tail[k]) <= tol * std::sqrt(total)) {
+        q = k;
+        break;
+      }
+    std::vector<double> inv(q), ones(q, 1.0);
+    h->comp_s.resize(q);
+    for (int k = 0; k < q; ++k) {
+      h->comp_s[k] = s[perm[k]];
+      inv[k] = s[perm[k]] > 0.0 ? 1.0 / s[perm[k]] : 0.0;
+    }
+    const Side& sa = h->side[0];
+    const Side& sb = h->side[h->lyap ? 0 : 1];
+    if (cudaMalloc(&h->comp_V, std::max<size_t>((size_t)sa.n * q * 8, 256)) != cudaSuccess ||
+        cudaMalloc(&h->comp_W, std::max<size_t>((size_t)sb.n * q * 8, 256)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SYLV_ENOMEM, "compressed factors");
+    }
+    if (q > 0) {
+      CU(cudaMemcpyAsync(cols, perm.data(), (size_t)q * 4, cudaMemcpyHostToDevice, strm));
+      CU(cudaMemcpyAsync(scale, inv.data(), (size_t)q * 8, cudaMemcpyHostToDevice, strm));
+      sylv::launch_apply_blocks(strm, sa.n, (int)h->s, r, (const double*)sa.V, sa.n * h->s, G, r, cols, scale, q,
+                                h->comp_V);  // V U_q, U_q = G(:, kept) / s
+      CU(cudaMemcpyAsync(scale, ones.data(), (size_t)q * 8, cudaMemcpyHostToDevice, strm));
+      sylv::launch_apply_blocks(strm, sb.n, (int)h->s, r, (const double*)sb.V, sb.n * h->s, Z, r, cols, scale, q,
+                                h->comp_W);  // W Z_q
+      CU(cudaGetLastError());
+      CU(cudaStreamSynchronize(strm));
+    }
+    h->comp_q = q;
+    if (q_out) *q_out = q;
+    return SYLV_OK;
+  };
+  rc = run();
+  cleanup();
+  if (rc != SYLV_OK && h->comp_q < 0) {
+    if (h->comp_V) cudaFree(h->comp_V);
+    if (h->comp_W) cudaFree(h->comp_W);
+    h->comp_V = h->comp_W = nullptr;
+  }
+  return rc;
 }
 
 int sylv_get_history(sylv_handle* h, double* hist, int64_t cap, int64_t* len) {
@@ -1811,6 +1958,7 @@ void sylv_destroy(sylv_handle* h) {
   if (h->sk_host) cudaFreeHost(h->sk_host);
   free_subs(h);
   free_sketch(h);
+  free_compressed(h);
   free_solve(h);
   for (void* p : h->fixed_allocs) cudaFree(p);
   h->fixed_allocs.clear();

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -130,6 +131,15 @@ void launch_cg_p(cudaStream_t, const SmallCtx&, int rp);
 // Hessenberg H, G); with omega also reduces <Out(1:r,1:r), Z>, <Out, Out> and sets omega.
 // Returns the number of kernels launched.
 int launch_sylv_gemm(cudaStream_t, const SmallCtx&, int r, const double* Z, double* Out, bool omega);
+// Final low-rank compression (compress.cu): one-sided Jacobi SVD of the r x r core and the
+// products of the block-stored bases with the kept singular vectors.
+void jacobi_schedule(int r, std::vector<int>& pairs);  // (r2 - 1) rounds x r2 entries, r2 = r + r % 2
+int launch_jacobi_round(cudaStream_t, int r, double* G, double* Z, int64_t ld, const int* pairs_round, double eps,
+                        double tau, int* rotated);
+void launch_column_norms(cudaStream_t, int r, const double* G, int64_t ld, double* s);
+void launch_apply_blocks(cudaStream_t, int64_t rows, int su, int r, const double* V, int64_t bstride,
+                         const double* M, int64_t ldm, const int* cols, const double* scale, int q, double* Out);
+
 // The same operator in float64 accuracy on the tcgen05 tensor cores (kernels_ozaki.cu).
 size_t ozaki_scratch_bytes(int rmax);
 bool ozaki_setup();  // once per device: opt-in to the kernel's shared-memory size
