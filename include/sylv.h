@@ -77,6 +77,13 @@ typedef struct {
                           cores from order r = 448 on), 1 CUDA cores only (float64, or double-float in
                           SYLV_MIXED), 2 tensor cores at every order; the tensor-core form splits both
                           factors into BF16 digits (Ozaki scheme) and keeps float64 accuracy */
+  int32_t basis_gemm;  /* SYLV_FP64 block Arnoldi bases (BiCGSTAB, CGS, GPBiCG): the Gram products and block
+                          updates of eq. 3.4, 0 auto (tensor cores; CUDA cores if their digit planes do not
+                          fit in device memory), 1 CUDA cores (float64 FMAs), 2 tensor cores (SYLV_ENOMEM if
+                          they do not fit).  The tensor-core form holds each basis block, once it is built,
+                          as seven BF16 planes of 8-bit digits in two layouts (28 bytes per basis element
+                          besides the 8 of float64) and splits the other operand the same way; the products
+                          are exact sums of digit products, rounded once to float64 (Ozaki scheme) */
 } sylv_options;
 
 typedef struct {

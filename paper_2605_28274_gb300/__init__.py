@@ -43,7 +43,8 @@ class sylv_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("lyapunov", ctypes.c_int32), ("poll_every", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("deflate_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("no_true_residual", ctypes.c_int32), ("stream_mode", ctypes.c_int32), ("small_gemm", ctypes.c_int32)]
+                ("no_true_residual", ctypes.c_int32), ("stream_mode", ctypes.c_int32), ("small_gemm", ctypes.c_int32),
+                ("basis_gemm", ctypes.c_int32)]
 
 
 class sylv_kernel_stat(ctypes.Structure):
@@ -385,7 +386,7 @@ class Solver:
 
     def __init__(self, A, B, C1, C2, precision: str = "fp64", lyapunov: bool = False, poll_every: int = 0,
                  deflate_tol: float = 0.0, cuda_stream: int = 0, timeout_s: float = 0.0, refine_max: int = 0,
-                 profile: bool = False, stream_mode: int = 0, small_gemm: int = 0):
+                 profile: bool = False, stream_mode: int = 0, small_gemm: int = 0, basis_gemm: int = 0):
         o = sylv_default_options()
         o.precision = SYLV_MIXED if precision == "mixed" else SYLV_FP64
         o.lyapunov = 1 if lyapunov else 0
@@ -399,6 +400,7 @@ class Solver:
         o.profile = 1 if profile else 0
         o.stream_mode = stream_mode
         o.small_gemm = small_gemm
+        o.basis_gemm = basis_gemm
         self.n = _csr_arrays(A)[0]
         self.m = self.n if lyapunov else _csr_arrays(B)[0]
         self.s = C1.shape[1]

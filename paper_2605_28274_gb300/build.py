@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsylv.so")
 SOURCES = ["capi.cu", "kernels_basis.cu", "kernels_small.cu", "kernels_resid.cu", "kernels_batch.cu", "kernels_ozaki.cu",
-           "compress.cu", "noalloc.cu"]
+           "compress.cu", "noalloc.cu", "kernels_obasis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -66,6 +66,7 @@ struct Side {
   double* R1 = nullptr;
   double* Rinv = nullptr;
   void* RinvT = nullptr;
+  sylv::ObSide ob;  // float64 Arnoldi basis as tensor-core digit planes (G == nullptr: not used)
 };
 
 enum Method { M_NONE = 0, M_CG = 1, M_BICG = 2, M_CGS = 3, M_CR = 4, M_GPBICG = 5 };  // CR: Lanczos, others Arnoldi
@@ -76,12 +77,12 @@ inline bool lanczos_method(int m) { return m == M_CG || m == M_CR; }
 enum KClass {
   KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_SCALE, KC_SETUP,
   KC_SMALL_GEMM, KC_SMALL_OP, KC_SMALL_ELEM, KC_RESID, KC_RESID_TSG, KC_RESID_TSU, KC_RESID_SMALL,
-  KC_RESID_SPMM, KC_RESID_QR, KC_RESID_MISC, KC_NUM
+  KC_RESID_SPMM, KC_RESID_QR, KC_RESID_MISC, KC_BSPLIT, KC_NUM
 };
 const char* const kKcNames[KC_NUM] = {"spmm",         "gram",  "reduce_h",   "update",           "cholqr_chol",
                                       "cholqr_scale", "setup", "small_gemm", "small_op_tridiag", "small_elementwise",
                                       "true_residual", "resid_tsg", "resid_tsu", "resid_small", "resid_spmm",
-                                      "resid_qr", "resid_misc"};
+                                      "resid_qr", "resid_misc", "basis_split"};
 
 struct Prof {
   struct Rec {
@@ -130,6 +131,7 @@ struct sylv_handle {
   double *Hs = nullptr, *Gs = nullptr, *Zs = nullptr;
   int split_cols = 0;  // columns of H, G split so far in this solve
   void* oz_scratch = nullptr;  // digit planes of the tensor-core small products
+  bool ob_unavailable = false;  // the basis digit planes did not fit: CUDA-core basis kernels
   // sylv_compress: rank-q factors (column-major, device) that sylv_get_factors returns until the
   // next solve; comp_q < 0: not compressed
   double *comp_V = nullptr, *comp_W = nullptr;
@@ -218,6 +220,7 @@ void free_solve(sylv_handle* h) {
   for (auto& sd : h->side) {
     sd.V = nullptr;
     sd.H = nullptr;
+    sd.ob = sylv::ObSide{};
   }
   h->Hs = h->Gs = h->Zs = nullptr;
   h->Uh = nullptr;
@@ -373,7 +376,10 @@ constexpr int kOzakiMinR = 448;  // measured crossover with the CUDA-core float6
 
 int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   const bool want_oz = arnoldi_method(method) && h->opt.small_gemm != 1 && (int64_t)maxb * h->s >= kOzakiMinR;
+  // float64 Arnoldi bases: Gram products and updates on the tensor cores unless basis_gemm = 1
+  const bool want_ob = !h->mixed && arnoldi_method(method) && h->opt.basis_gemm != 1;
   if (h->maxb >= maxb && h->hist_cap >= hist_need && h->cap_method != M_NONE && (!want_oz || h->oz_scratch) &&
+      (!want_ob || h->side[0].ob.G || h->ob_unavailable) &&
       ((method != M_CGS && method != M_GPBICG) || h->Uh) && (method != M_GPBICG || h->gW))
     return SYLV_OK;
   free_solve(h);
@@ -428,6 +434,29 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
     TRY(alloc_solve(h, &p, sylv::ozaki_scratch_bytes((int)ldh)));
     h->oz_scratch = p;
   }
+  // digit planes of the float64 Arnoldi bases (twice 14 bytes per basis element per side);
+  // zero-filled once, so that padding rows and columns hold finite digits
+  h->ob_unavailable = false;
+  if (want_ob) {
+    if (!sylv::ob_setup()) return fail(SYLV_ECUDA, "tensor-core basis kernel setup");
+    const std::string err0 = g_err;
+    for (int i = 0; i < nsides(h); ++i) {
+      Side& sd = h->side[i];
+      const size_t bytes = sylv::ob_side_bytes(sd.n, (int)ldh, (int)s);
+      void* p = nullptr;
+      const int rc = dev_alloc(h, h->solve_allocs, &p, bytes);
+      if (rc != SYLV_OK) {
+        if (rc != SYLV_ENOMEM || h->opt.basis_gemm == 2) return rc;
+        // not enough device memory: the CUDA-core float64 kernels run instead
+        for (int j = 0; j < nsides(h); ++j) h->side[j].ob = sylv::ObSide{};
+        h->ob_unavailable = true;
+        g_err = err0;
+        break;
+      }
+      CU(cudaMemsetAsync(p, 0, bytes, h->stream));
+      sylv::ob_carve(p, sd.n, (int)ldh, (int)s, sd.ob);
+    }
+  }
   h->maxb = maxb;
   h->hist_cap = hist_need;
   h->cap_method = method;
@@ -471,6 +500,7 @@ void setup_qr(sylv_handle* h, int si) {
   a.Rout = sd.RQR;
   sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
   sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr);
+  if (sd.ob.G) sylv::launch_ob_split_basis(h->stream, h->st, sd.n, s, (const double*)V0, 0, sd.ob);
 }
 
 // One block Lanczos (lanczos=true) or BCGS2 block Arnoldi step on side si:
@@ -508,12 +538,24 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
          sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, nullptr, nullptr, 0));
   }
   const int passes = lanczos ? 1 : 2;  // block Lanczos: one projection; Arnoldi: BCGS2
+  // float64 Arnoldi: the Gram products and updates on the tensor cores, on the digit planes
+  const bool ob = !lanczos && sd.ob.G != nullptr;
+  const int js = nb * s;
   for (int pass = 0; pass < passes; ++pass) {
+    const bool last = pass == passes - 1;
+    if (ob) {
+      double* Yd = (double*)Y;
+      PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_ob_gram(st, h->st, n, s, js, Yd, sd.ob, gpart));
+      PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
+           sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1, false));
+      PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
+           nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr));
+      continue;
+    }
     PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));
     PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
          sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, lanczos ? (int64_t)q * s : 0,
                                (int64_t)q * s, Hc, pass == 1, sizeof(T) == 4));
-    const bool last = pass == passes - 1;
     PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
          nc = sylv::launch_update<T>(st, h->st, n, s, Vfirst, bstride, nb, Hc, Y, last ? spart : nullptr));
   }
@@ -537,6 +579,9 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   a.Hsup = lanczos ? sd.H + (int64_t)q * s + (int64_t)(q + 1) * s * ldh : nullptr;
   PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1), sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr));
+  if (ob)
+    PROF(h, KC_BSPLIT, 2.0 * ns * b + 28.0 * ns, 0.0,
+         sylv::launch_ob_split_basis(st, h->st, n, s, (const double*)Y, (q + 1) * s, sd.ob));
   h->prof_stream = nullptr;
 }
 
@@ -1537,6 +1582,7 @@ int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const do
   if (opt) o = *opt;
   if (s < 1 || s > 8) return fail(SYLV_EINVAL, "s must be in [1, 8]");
   if (o.precision != SYLV_FP64 && o.precision != SYLV_MIXED) return fail(SYLV_EINVAL, "unknown precision");
+  if (o.basis_gemm < 0 || o.basis_gemm > 2) return fail(SYLV_EINVAL, "basis_gemm must be 0, 1 or 2");
   TRY(check_csr(A, "A", -1));
   const bool lyap = o.lyapunov != 0;
   if (lyap) {

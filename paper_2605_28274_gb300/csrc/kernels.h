@@ -19,6 +19,36 @@ inline G counted(G grid) {
   return grid;
 }
 
+// ---------------------------------------------------------------- float64 basis products on the tensor cores
+// (kernels_obasis.cu) The Arnoldi basis of one side as seven BF16 planes of 8-bit digits, in a
+// Gram layout and an update layout, plus the digits of the block being orthogonalised (Y) and
+// of the coefficient block, and the column exponents.  One allocation of ob_side_bytes().
+struct ObSide {
+  uint16_t* G = nullptr;   // basis digit planes, Gram layout
+  uint16_t* U = nullptr;   // basis digit planes, update layout
+  uint16_t* YB = nullptr;  // digits of Y
+  uint16_t* HB = nullptr;  // digits of the coefficient block
+  int* vexp = nullptr;     // exponents of the basis columns
+  int* ey = nullptr;       // exponents of the columns of Y
+  int* eh = nullptr;       // exponents of the columns of the coefficient block
+  unsigned long long* mx = nullptr;  // column maxima: [0, 8) new basis block, [8, 16) Y
+  int64_t np = 0;          // basis rows padded to 128
+  int rp = 0;              // basis columns padded to 128
+  int64_t plane = 0;       // elements per digit plane
+};
+size_t ob_side_bytes(int64_t n, int R, int s);
+void ob_carve(void* mem, int64_t n, int R, int s, ObSide& o);
+bool ob_setup();
+// Digits of the new basis block Vb (n x s row-major; basis columns col0 .. col0 + s - 1).
+void launch_ob_split_basis(cudaStream_t, const DevState*, int64_t n, int s, const double* Vb, int col0, const ObSide&);
+// Per-split partial Gram products V^T Y over the first js basis columns (the partial layout of
+// launch_gram); returns the number of splits.
+int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Y, const ObSide&, double* partial);
+// Y -= V Hc over the first js basis columns (Hc: js x s, the layout launch_reduce_H writes),
+// with the optional per-CTA partial Y^T Y of the result; returns the number of CTAs.
+int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
+                     double* self_partial);
+
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

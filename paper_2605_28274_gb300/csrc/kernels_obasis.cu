@@ -1,0 +1,704 @@
+// Float64-accurate block Gram products and block updates of the Arnoldi bases on the tcgen05
+// tensor cores.
+//
+// In the float64 solve the basis kernels of eq. 3.4 -- H_{1:j,j} = V^T Y and Y -= V H_{1:j,j},
+// each twice per step in block classical Gram-Schmidt -- do 2 s flops per basis element they
+// read.  GB300 executes float64 FMAs at 1/64 of its FP32 rate, so on CUDA cores those kernels
+// are bound by the FP64 pipe at about a sixth of the memory bandwidth.  Here the basis is also
+// held, written once per block when the block is made, as seven BF16 planes of integer digits
+//
+//   v = 2^{e_c} sum_{p=0..6} d_p 2^{-8(p+1)},   d_0 in [-256, 256], d_p in [-128, 128] (p >= 1)
+//
+// (e_c: the exponent of the column's largest |v|; the digits are v rounded to 56 bits of that
+// scale), and the other operand -- the block Y, or the coefficient block with the basis
+// column scales folded in -- is split the same way for every product.  One MMA per basis
+// digit plane p takes all seven digit planes q of the other operand at once (MMA N = 7 s,
+// padded to a multiple of 16); every pair (p, q) accumulates integers in its own FP32 columns
+// of tensor memory.  A pair's sum over 64 values of k is at most 2^16 * 64 = 2^22 in
+// magnitude, so FP32 holds it exactly; every 64 values of k the pairs with p + q <= 6 are
+// added, as integers, into three int64 fixed-point words per output (levels 0-2, 3-5, 6).
+// The result is the exact product of the 56-bit operands, rounded once to float64; the
+// dropped pairs p + q > 6 weigh less than 2^-58 (scale of v)(scale of the other operand)
+// per term.  (Ozaki scheme I: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; its
+// tensor-core form: Mukunoki, Ozaki, Ogita, Imamura, ICCS 2020.)
+//
+// Layouts (BF16 elements).  A tile holds T rows x 32 values of k in the canonical no-swizzle
+// K-major layout of the tcgen05 shared-memory descriptor: 8-row x 16-byte core matrices, the
+// four core matrices of an 8-row group adjacent.  The basis is stored twice, so that each
+// kernel loads one chunk of a digit plane with one 1-D bulk copy (cp.async.bulk):
+//   Gram layout   (tile rows = basis columns m, k = basis rows i): tile (i / 32, m / 128)
+//   update layout (tile rows = basis rows i, k = basis columns m): tile (m / 32, i / 128)
+// Each kernel reads 14 bytes per basis element instead of 8, and is bound by memory
+// bandwidth instead of the FP64 pipe.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sylv {
+
+namespace {
+
+constexpr int OB_P = 7;           // digits per operand
+constexpr int OB_LMAX = 6;        // pairs p + q <= OB_LMAX are folded
+constexpr int OB_TM = 128;        // MMA M: tile rows
+constexpr int OB_KC = 32;         // k per chunk
+constexpr int OB_FOLD = 2;        // chunks per fold (64 values of k)
+constexpr int OB_STAGES = 3;      // chunks in flight
+constexpr int OB_THREADS = 128;   // four warps: TMEM lanes 0..127, one per tile row
+constexpr int OB_ATILE = OB_TM * OB_KC;  // BF16 elements of one basis digit tile (8 KB)
+constexpr int OB_WAIT_ITERS = 1 << 20;
+constexpr int OB_EXP_BAD = 1 << 20;      // exponent sentinel: a non-finite value
+
+template <int S>
+struct ObShape {
+  static constexpr int NP = (OB_P * S + 15) / 16 * 16;  // MMA N: digit columns of the other operand
+  static constexpr int BTILE = NP * OB_KC;              // BF16 elements of one of its tiles
+  static constexpr int TMEM_COLS = OB_P * NP <= 256 ? 256 : 512;
+  static constexpr uint32_t ABYTES = OB_ATILE * 2;
+  static constexpr uint32_t BBYTES = BTILE * 2;
+  static constexpr size_t STAGE = (size_t)OB_P * ABYTES + BBYTES;
+  static constexpr size_t SMEM = OB_STAGES * STAGE + 1024 + 128;  // + alignment, barriers
+};
+
+__device__ __forceinline__ uint32_t ob_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory descriptor, no swizzle: LBO 128 bytes (core matrices adjacent in k),
+// SBO 512 bytes (8-row groups), descriptor version of this architecture family.
+__device__ __forceinline__ uint64_t ob_sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+constexpr uint32_t ob_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Offset of element (row i, k) inside a T x 32 tile.
+__device__ __forceinline__ int ob_cm(int i, int k) {
+  return (((i >> 3) * 4 + (k >> 3)) << 6) + ((i & 7) << 3) + (k & 7);
+}
+
+// e = 1 + floor(log2 m) for the IEEE bits m of a non-negative double (0 for zero or
+// subnormal, OB_EXP_BAD for a non-finite value): every |x| <= m satisfies |x| < 2^e.
+__device__ __forceinline__ int ob_exponent(unsigned long long m) {
+  if (m >= 0x7FF0000000000000ull) return OB_EXP_BAD;
+  if (m < 0x0010000000000000ull) return 0;
+  return (int)(m >> 52) - 1023 + 1;
+}
+
+// The seven digits of x 2^sc on the scale 2^e (|x 2^sc| < 2^e): N = round(x 2^{sc+56-e})
+// (ties away from zero; |N| <= 2^56), sliced from the top with rounding to nearest, so that
+// x 2^sc = 2^e sum_p d_p 2^{-8(p+1)} up to 2^{e-57}.  Integer operations only (the FP64 pipe
+// is narrow on this GPU); zero and subnormal x give zero digits.
+__device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  long long N = 0;
+  if (ex != 0 && ex != 0x7FF && e != OB_EXP_BAD) {
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1075 + sc + 56 - e;  // N = mant 2^sh; |x 2^sc| < 2^e gives sh <= 3
+    unsigned long long u;
+    if (sh >= 0)
+      u = mant << sh;
+    else if (sh < -54)
+      u = 0;
+    else
+      u = (mant + (1ull << (-sh - 1))) >> (-sh);
+    N = (b >> 63) ? -(long long)u : (long long)u;
+  }
+#pragma unroll
+  for (int p = 0; p < OB_P - 1; ++p) {
+    const int s = 8 * (OB_P - 1 - p);
+    const long long dp = (N + (1ll << (s - 1))) >> s;
+    N -= dp << s;
+    d[p] = (int)dp;
+  }
+  d[OB_P - 1] = (int)N;
+}
+
+__device__ __forceinline__ __nv_bfloat16 ob_bf(int d) { return __float2bfloat16_rn((float)d); }  // |d| <= 256: exact
+
+// mx[t] = max over rows of |X[row][t]| as IEEE bits (X row-major n x S); mx zeroed beforehand.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_colmax_kernel(const DevState* st, int64_t n, const double* __restrict__ X,
+                                                       unsigned long long* __restrict__ mx) {
+  if (stopped(st)) return;
+  unsigned long long m[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) m[t] = 0;
+  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      m[t] = max(m[t], (unsigned long long)__double_as_longlong(X[row * S + t]) & 0x7FFFFFFFFFFFFFFFull);
+  }
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    unsigned long long v = m[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(mx + t, v);
+  }
+}
+
+// Digits of the new basis block (columns col0 .. col0 + S - 1, row-major n x S) into both
+// layouts, and its column exponents into vexp.  One thread per basis row.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Vb,
+                                                       int col0, const unsigned long long* __restrict__ mx,
+                                                       int* __restrict__ vexp, __nv_bfloat16* __restrict__ G,
+                                                       __nv_bfloat16* __restrict__ U, int64_t plane, int MT, int IT) {
+  if (stopped(st)) return;
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int e[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) e[t] = ob_exponent(mx[t]);
+  if (i == 0)
+    for (int t = 0; t < S; ++t) vexp[col0 + t] = e[t];
+  if (i >= n) return;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    int d[OB_P];
+    ob_digits(Vb[i * S + t], 0, e[t], d);
+    const int m = col0 + t;
+    const int64_t og = ((i >> 5) * MT + (m >> 7)) * OB_ATILE + ob_cm(m & 127, (int)(i & 31));
+    const int64_t ou = ((int64_t)(m >> 5) * IT + (i >> 7)) * OB_ATILE + ob_cm((int)(i & 127), m & 31);
+#pragma unroll
+    for (int p = 0; p < OB_P; ++p) {
+      G[p * plane + og] = ob_bf(d[p]);
+      U[p * plane + ou] = ob_bf(d[p]);
+    }
+  }
+}
+
+// Digits of the block Y (row-major n x S) as the Gram's other operand: digit column
+// q S + t of row (k =) i; exponents into ey.  One thread per row.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Y,
+                                                       const unsigned long long* __restrict__ mx, int* __restrict__ ey,
+                                                       __nv_bfloat16* __restrict__ YB) {
+  if (stopped(st)) return;
+  constexpr int NP = ObShape<S>::NP;
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int e[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) e[t] = ob_exponent(mx[t]);
+  if (i == 0)
+    for (int t = 0; t < S; ++t) ey[t] = e[t];
+  if (i >= n) return;
+  const int64_t base = (i >> 5) * (int64_t)(NP * OB_KC);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    int d[OB_P];
+    ob_digits(Y[i * S + t], 0, e[t], d);
+#pragma unroll
+    for (int p = 0; p < OB_P; ++p) YB[base + ob_cm(p * S + t, (int)(i & 31))] = ob_bf(d[p]);
+  }
+}
+
+// Digits of the coefficient block H'(m, t) = 2^{vexp[m]} Hc[m S + t] (m < js; zero up to the
+// next multiple of 32) as the update's other operand, exponents into eh.  One CTA: the column
+// maxima of H' come from integer keys bits(|Hc|) + vexp 2^52, which order like the values.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int js, const double* __restrict__ Hc,
+                                                       const int* __restrict__ vexp, int* __restrict__ eh,
+                                                       __nv_bfloat16* __restrict__ HB) {
+  if (stopped(st)) return;
+  constexpr int NP = ObShape<S>::NP;
+  __shared__ long long kmax[NT / 32][S];
+  __shared__ int esh[S];
+  long long km[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) km[t] = LLONG_MIN;
+  int bad = 0;
+  for (int m = threadIdx.x; m < js; m += NT) {
+    const int sc = vexp[m];
+    if (sc == OB_EXP_BAD) bad = 1;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(Hc[(int64_t)m * S + t]) & 0x7FFFFFFFFFFFFFFFull;
+      const int ex = (int)(b >> 52);
+      if (ex == 0x7FF) bad = 1;
+      else if (ex != 0 && sc != OB_EXP_BAD) km[t] = max(km[t], (long long)b + ((long long)sc << 52));
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    long long v = km[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (l == 0) kmax[w][t] = v;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x < S) {
+    long long v = LLONG_MIN;
+    for (int q = 0; q < NT / 32; ++q) v = max(v, kmax[q][threadIdx.x]);
+    const int e = bad ? OB_EXP_BAD : (v == LLONG_MIN ? 0 : (int)(v >> 52) - 1023 + 1);
+    esh[threadIdx.x] = e;
+    eh[threadIdx.x] = e;
+  }
+  __syncthreads();
+  const int kpad = (js + OB_KC - 1) / OB_KC * OB_KC;
+  for (int m = threadIdx.x; m < kpad; m += NT) {
+    const int sc = m < js ? vexp[m] : 0;
+    const int64_t base = (int64_t)(m >> 5) * (NP * OB_KC);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      int d[OB_P];
+      const double x = (m < js && sc != OB_EXP_BAD) ? Hc[(int64_t)m * S + t] : 0.0;
+      ob_digits(x, sc, esh[t], d);
+#pragma unroll
+      for (int p = 0; p < OB_P; ++p) HB[base + ob_cm(p * S + t, m & 31)] = ob_bf(d[p]);
+    }
+  }
+}
+
+__device__ __forceinline__ bool ob_wait(uint32_t bar, uint32_t phase) {
+  for (int it = 0; it < OB_WAIT_ITERS; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// v: an FP32 pair sum, an exact integer with |v| <= 2^22; its value from the bits of
+// v + 1.5 * 2^23 (exact in that range).
+__device__ __forceinline__ long long ob_int(uint32_t r) {
+  return (long long)(__float_as_int(__fadd_rn(__uint_as_float(r), 12582912.0f)) - 0x4B400000);
+}
+
+__device__ __forceinline__ double ob_pow2(int x) {  // 2^x as a float64 (0 or inf outside the normal range)
+  return x < -1022 ? 0.0 : (x > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
+                                     : __longlong_as_double((long long)(x + 1023) << 52));
+}
+
+struct ObArgs {
+  DevState* st;
+  const __nv_bfloat16* A;  // basis digit planes (Gram or update layout)
+  int64_t plane;           // elements per plane
+  int MT;                  // tiles per chunk row of that layout (Gram: Rp / 128, update: np / 128)
+  const __nv_bfloat16* B;  // digits of the other operand, one NP x 32 tile per chunk
+  int64_t n;               // basis rows
+  int js;                  // basis columns in use
+  int cps;                 // Gram: chunks per k split (blockIdx.y)
+  const int* ea;           // Gram: exponents of the basis columns
+  const int* eb;           // exponents of the other operand's columns
+  double* out;             // Gram: partials [split][m S + t]; update: Y (row-major n x S)
+  double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
+};
+
+// GRAM: CTA (m tile, k split) adds the partial V^T Y of its rows into out.  Update: CTA c
+// takes row tiles c, c + grid, ... and subtracts V H from those rows of Y.  Thread 0 issues
+// the bulk copies (OB_STAGES chunks in flight) and the MMAs; all threads fold the tensor
+// memory every OB_FOLD chunks.  A wait that gives up sets the solve status to ST_WAIT_TIMEOUT.
+template <int S, bool GRAM>
+__global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
+  using Sh = ObShape<S>;
+  constexpr int NP = Sh::NP;
+  if (stopped(a.st)) return;
+  extern __shared__ __align__(1024) unsigned char ob_smem[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)ob_smem + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + OB_STAGES * Sh::STAGE);  // full[STAGES], empty[STAGES], acc
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * OB_STAGES + 1);
+  __shared__ double shred[(OB_THREADS / 32) * S * S];
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  int ntiles, nch, c0 = 0, rg = OB_TM / 8;
+  if (GRAM) {
+    const int kcn = (int)((a.n + OB_KC - 1) / OB_KC);
+    c0 = (int)blockIdx.y * a.cps;
+    nch = max(0, min(a.cps, kcn - c0));
+    ntiles = 1;
+    rg = min(OB_TM / 8, (a.js - (int)blockIdx.x * OB_TM + 7) / 8);  // 8-row groups holding basis columns
+  } else {
+    const int it = (int)((a.n + OB_TM - 1) / OB_TM);
+    ntiles = (int)blockIdx.x < it ? (it - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    nch = (a.js + OB_KC - 1) / OB_KC;
+  }
+  const int NI = ntiles * nch;
+  const uint32_t abytes = (uint32_t)rg * 512;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ob_smem_u32(tmem_slot)),
+                 "r"(Sh::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const uint32_t bfull = ob_smem_u32(bars), bempty = ob_smem_u32(bars + OB_STAGES),
+                 bacc = ob_smem_u32(bars + 2 * OB_STAGES);
+  if (tid == 0) {
+    for (int i = 0; i < 2 * OB_STAGES + 1; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ob_smem_u32(bars + i)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  auto issue = [&](int i) {  // thread 0: bulk copies of item i into stage i % OB_STAGES
+    const int stg = i % OB_STAGES;
+    const int tile = i / nch, c = i - tile * nch;
+    unsigned char* sa = base + stg * Sh::STAGE;
+    unsigned char* sb = sa + OB_P * Sh::ABYTES;
+    const __nv_bfloat16* ga;
+    const __nv_bfloat16* gb;
+    if (GRAM) {
+      const int kc = c0 + c;
+      ga = a.A + ((int64_t)kc * a.MT + blockIdx.x) * OB_ATILE;
+      gb = a.B + (int64_t)kc * Sh::BTILE;
+    } else {
+      const int it = (int)blockIdx.x + tile * (int)gridDim.x;
+      ga = a.A + ((int64_t)c * a.MT + it) * OB_ATILE;
+      gb = a.B + (int64_t)c * Sh::BTILE;
+    }
+    const uint32_t bar = bfull + 8 * stg;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OB_P * abytes + Sh::BBYTES)
+                 : "memory");
+#pragma unroll 1
+    for (int p = 0; p < OB_P; ++p)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       ob_smem_u32(sa + p * Sh::ABYTES)),
+                   "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
+                   : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     ob_smem_u32(sb)),
+                 "l"(gb), "r"(Sh::BBYTES), "r"(bar)
+                 : "memory");
+  };
+
+  long long w0[S], w1[S], w2[S];  // levels 0-2 (unit 2^-16), 3-5 (2^-40), 6 (2^-48) of the pair sums
+  double acc[S][S];               // update: partial Y^T Y
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    w0[t] = w1[t] = w2[t] = 0;
+#pragma unroll
+    for (int u = 0; u < S; ++u) acc[u][t] = 0.0;
+  }
+  int issued = 0, consumed = 0;
+  bool ok0 = true;  // thread 0's waits
+  if (tid == 0)
+    for (; issued < min(OB_STAGES, NI); ++issued) issue(issued);
+  const uint32_t id = ob_idesc(OB_TM, NP);
+  uint32_t accph = 0;
+  bool ok = true;
+  for (int i = 0; i < NI; ++i) {
+    const int tile = i / nch, c = i - tile * nch;
+    if (tid == 0 && ok0) {
+      const int stg = i % OB_STAGES;
+      if (ob_wait(bfull + 8 * stg, (uint32_t)(i / OB_STAGES) & 1u)) {
+        ++consumed;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const bool first = (c % OB_FOLD) == 0;
+        const uint32_t sa = ob_smem_u32(base + stg * Sh::STAGE), sb = sa + OB_P * Sh::ABYTES;
+#pragma unroll 1
+        for (int p = 0; p < OB_P; ++p) {
+#pragma unroll
+          for (int ks = 0; ks < OB_KC / 16; ++ks) {
+            const uint64_t da = ob_sdesc(sa + p * Sh::ABYTES + ks * 256);
+            const uint64_t db = ob_sdesc(sb + ks * 256);
+            const uint32_t accf = (first && ks == 0) ? 0u : 1u;  // a fold period starts each plane afresh
+            asm volatile(
+                "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(tmem + (uint32_t)(p * NP)),
+                "l"(da), "l"(db), "r"(id), "r"(accf)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bempty + 8 * stg)
+                     : "memory");
+        if (i >= 1 && issued < NI) {  // refill the stage of item i - 1 once its MMAs are done
+          const int j = i - 1;
+          if (ob_wait(bempty + 8 * (j % OB_STAGES), (uint32_t)(j / OB_STAGES) & 1u)) {
+            issue(issued);
+            ++issued;
+          } else {
+            ok0 = false;
+          }
+        }
+      } else {
+        ok0 = false;
+      }
+    }
+    const bool fold = (c % OB_FOLD) == OB_FOLD - 1 || c == nch - 1;
+    if (!fold) continue;
+    if (tid == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bacc)
+                   : "memory");
+    const bool wok = ob_wait(bacc, accph);
+    accph ^= 1u;
+    ok = __syncthreads_and(wok && ok0);
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+    for (int p = 0; p < OB_P; ++p) {
+      constexpr int NCMAX = (OB_LMAX + 1) * S;
+#pragma unroll
+      for (int cb = 0; cb < NCMAX; cb += 32) {
+        if (cb < (OB_LMAX - p + 1) * S) {
+          uint32_t r[32];
+          const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * NP + cb);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(addr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = cb + j, q = col / S, t = col % S, L = p + q;
+            if (q <= OB_LMAX - p) {
+              const long long v = ob_int(r[j]);
+              if (L <= 2)
+                w0[t] += v << (8 * (2 - L));
+              else if (L <= 5)
+                w1[t] += v << (8 * (5 - L));
+              else
+                w2[t] += v;
+            }
+          }
+        }
+      }
+    }
+    if (!GRAM && c == nch - 1) {  // the tile is complete: Y -= V H on its rows
+      const int it = (int)blockIdx.x + tile * (int)gridDim.x;
+      const int64_t row = (int64_t)it * OB_TM + tid;
+      if (row < a.n) {
+        double y[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int f = a.eb[t];
+          double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
+          v = f == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll) : v * ob_pow2(f);
+          y[t] = a.out[row * S + t] - v;
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t) a.out[row * S + t] = y[t];
+        if (a.self) {
+#pragma unroll
+          for (int u = 0; u < S; ++u)
+#pragma unroll
+            for (int t = 0; t < S; ++t) acc[u][t] += y[u] * y[t];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < S; ++t) w0[t] = w1[t] = w2[t] = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // tensor memory is free for the next fold period
+  }
+
+  if (ok) {
+    if (GRAM) {
+      const int m = (int)blockIdx.x * OB_TM + tid;
+      if (m < a.js) {
+        const int e = a.ea[m];
+        double* o = a.out + (int64_t)blockIdx.y * ((int64_t)a.js * S) + (int64_t)m * S;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          const int f = a.eb[t];
+          double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
+          // 2^{e+f} in two steps: each factor stays in the normal range
+          v = (e == OB_EXP_BAD || f == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                   : v * ob_pow2(e) * ob_pow2(f);
+          o[t] = v;
+        }
+      }
+    } else if (a.self) {
+      const int wv = tid >> 5, l = tid & 31;
+#pragma unroll
+      for (int u = 0; u < S; ++u)
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+          double v = acc[u][t];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (l == 0) shred[wv * S * S + u * S + t] = v;
+        }
+      __syncthreads();
+      if (tid < S * S) {
+        double v = 0.0;
+        for (int q = 0; q < OB_THREADS / 32; ++q) v += shred[q * S * S + tid];
+        a.self[(int64_t)blockIdx.x * S * S + tid] = v;
+      }
+    }
+  } else {
+    if (tid == 0) {
+      a.st->breakdown_where = GRAM ? 210 : 211;
+      atomicExch(&a.st->status, (int)ST_WAIT_TIMEOUT);
+      // copies still in flight land in shared memory: wait for them (bounded), and for the MMAs
+      for (int j = consumed; j < issued; ++j) ob_wait(bfull + 8 * (j % OB_STAGES), (uint32_t)(j / OB_STAGES) & 1u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bacc)
+                   : "memory");
+      ob_wait(bacc, accph);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TMEM_COLS));
+}
+
+int ob_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+int ob_np(int64_t n) { return (int)((n + OB_TM - 1) / OB_TM * OB_TM); }
+int ob_rp(int R) { return (R + OB_TM - 1) / OB_TM * OB_TM; }
+int ob_NP(int s) { return (OB_P * s + 15) / 16 * 16; }
+
+template <typename F>
+bool ob_for_each_kernel(F f) {
+  bool ok = true;
+#define OB_CASE(SV) \
+  ok = ok && f((const void*)ob_kernel<SV, true>, ObShape<SV>::SMEM) && f((const void*)ob_kernel<SV, false>, ObShape<SV>::SMEM);
+  OB_CASE(1) OB_CASE(2) OB_CASE(3) OB_CASE(4) OB_CASE(5) OB_CASE(6) OB_CASE(7) OB_CASE(8)
+#undef OB_CASE
+  return ok;
+}
+
+}  // namespace
+
+size_t ob_side_bytes(int64_t n, int R, int s) {
+  const size_t np = (size_t)ob_np(n), rp = (size_t)ob_rp(R), NPs = (size_t)ob_NP(s);
+  return 256 + 2 * (size_t)OB_P * np * rp * 2  // Gram and update layouts
+         + np * NPs * 2 + rp * NPs * 2          // digits of Y and of the coefficient block
+         + rp * sizeof(int) + 16 * sizeof(int)  // basis column exponents, ey, eh
+         + 16 * sizeof(unsigned long long) + 1024;
+}
+
+void ob_carve(void* mem, int64_t n, int R, int s, ObSide& o) {
+  const size_t np = (size_t)ob_np(n), rp = (size_t)ob_rp(R), NPs = (size_t)ob_NP(s);
+  uintptr_t p = ((uintptr_t)mem + 255) & ~(uintptr_t)255;
+  auto take = [&](size_t bytes) {
+    void* q = (void*)p;
+    p = (p + bytes + 255) & ~(uintptr_t)255;
+    return q;
+  };
+  o.np = (int64_t)np;
+  o.rp = (int)rp;
+  o.plane = (int64_t)(np * rp);
+  o.G = (uint16_t*)take((size_t)OB_P * np * rp * 2);
+  o.U = (uint16_t*)take((size_t)OB_P * np * rp * 2);
+  o.YB = (uint16_t*)take(np * NPs * 2);
+  o.HB = (uint16_t*)take(rp * NPs * 2);
+  o.vexp = (int*)take(rp * sizeof(int));
+  o.ey = (int*)take(8 * sizeof(int));
+  o.eh = (int*)take(8 * sizeof(int));
+  o.mx = (unsigned long long*)take(16 * sizeof(unsigned long long));
+}
+
+bool ob_setup() {
+  return ob_for_each_kernel([](const void* fn, size_t smem) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+  });
+}
+
+#define SYLV_OB_S_CASES(MACRO) MACRO(1) MACRO(2) MACRO(3) MACRO(4) MACRO(5) MACRO(6) MACRO(7) MACRO(8)
+
+void launch_ob_split_basis(cudaStream_t strm, const DevState* st, int64_t n, int s, const double* Vb, int col0,
+                           const ObSide& o) {
+  if (n == 0) return;
+  cudaMemsetAsync(o.mx, 0, 8 * sizeof(unsigned long long), strm);
+  const int gmax = (int)std::min<int64_t>((n + NT - 1) / NT, 4 * ob_sms());
+  const unsigned gs = (unsigned)((n + NT - 1) / NT);
+  __nv_bfloat16* G = (__nv_bfloat16*)o.G;
+  __nv_bfloat16* U = (__nv_bfloat16*)o.U;
+  const int MT = o.rp / OB_TM, IT = (int)(o.np / OB_TM);
+#define CASE(SV)                                                                                           \
+  case SV:                                                                                                 \
+    ob_colmax_kernel<SV><<<counted(gmax), NT, 0, strm>>>(st, n, Vb, o.mx);                                 \
+    ob_vsplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Vb, col0, o.mx, o.vexp, G, U, o.plane, MT, IT); \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+}
+
+int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Y, const ObSide& o,
+                   double* partial) {
+  cudaMemsetAsync(o.mx + 8, 0, 8 * sizeof(unsigned long long), strm);
+  const int gmax = (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, 4 * ob_sms()));
+  const unsigned gs = (unsigned)std::max<int64_t>(1, (n + NT - 1) / NT);
+  const int mtv = (js + OB_TM - 1) / OB_TM;
+  const int kcn = (int)std::max<int64_t>(1, (n + OB_KC - 1) / OB_KC);
+  int ks = std::max(1, std::min(kcn, ob_sms() / mtv));
+  const int cps = (kcn + ks - 1) / ks;
+  ks = (kcn + cps - 1) / cps;  // no empty split
+  ObArgs a{};
+  a.st = st;
+  a.A = (const __nv_bfloat16*)o.G;
+  a.plane = o.plane;
+  a.MT = o.rp / OB_TM;
+  a.B = (const __nv_bfloat16*)o.YB;
+  a.n = n;
+  a.js = js;
+  a.cps = cps;
+  a.ea = o.vexp;
+  a.eb = o.ey;
+  a.out = partial;
+  a.self = nullptr;
+  const dim3 grid((unsigned)mtv, (unsigned)ks);
+#define CASE(SV)                                                                                                 \
+  case SV:                                                                                                       \
+    ob_colmax_kernel<SV><<<counted(gmax), NT, 0, strm>>>(st, n, Y, o.mx + 8);                                    \
+    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, o.mx + 8, o.ey, (__nv_bfloat16*)o.YB);          \
+    ob_kernel<SV, true><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                              \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+  return ks;
+}
+
+int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Hc, double* Y,
+                     const ObSide& o, double* self_partial) {
+  const int itn = (int)std::max<int64_t>(1, (n + OB_TM - 1) / OB_TM);
+  const int grid = std::min(itn, ob_sms());
+  ObArgs a{};
+  a.st = st;
+  a.A = (const __nv_bfloat16*)o.U;
+  a.plane = o.plane;
+  a.MT = (int)(o.np / OB_TM);
+  a.B = (const __nv_bfloat16*)o.HB;
+  a.n = n;
+  a.js = js;
+  a.cps = 0;
+  a.ea = nullptr;
+  a.eb = o.eh;
+  a.out = Y;
+  a.self = self_partial;
+#define CASE(SV)                                                                                              \
+  case SV:                                                                                                    \
+    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__nv_bfloat16*)o.HB);         \
+    ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+}  // namespace sylv
