@@ -7,18 +7,18 @@
 // are bound by the FP64 pipe at about a sixth of the memory bandwidth.  Here the basis is also
 // held, written once per block when the block is made, as seven BF16 planes of integer digits
 //
-//   v = 2^{e_c} sum_{p=0..6} d_p 2^{-8(p+1)},   d_0 in [-256, 256], d_p in [-128, 128] (p >= 1)
+//   v = 2^{e_c} sum_{p=0..6} d_p 2^{-8(p+1)},   d_p in [-128, 128]
 //
-// (e_c: the exponent of the column's largest |v|; the digits are v rounded to 56 bits of that
-// scale), and the other operand -- the block Y, or the coefficient block with the basis
-// column scales folded in -- is split the same way for every product.  One MMA per basis
-// digit plane p takes all seven digit planes q of the other operand at once (MMA N = 7 s,
-// padded to a multiple of 16); every pair (p, q) accumulates integers in its own FP32 columns
-// of tensor memory.  A pair's sum over 64 values of k is at most 2^16 * 64 = 2^22 in
-// magnitude, so FP32 holds it exactly; every 64 values of k the pairs with p + q <= 6 are
-// added, as integers, into three int64 fixed-point words per output (levels 0-2, 3-5, 6).
-// The result is the exact product of the 56-bit operands, rounded once to float64; the
-// dropped pairs p + q > 6 weigh less than 2^-58 (scale of v)(scale of the other operand)
+// (2^{e_c - 1}: the power of two above the column's largest |v|, so the digits are v rounded to
+// 55 bits of its largest entry), and the other operand -- the block Y, or the coefficient
+// block with the basis column scales folded in -- is split the same way for every product.
+// One MMA per basis digit plane p takes all seven digit planes q of the other operand at once
+// (MMA N = 7 s, padded to a multiple of 16); every pair (p, q) accumulates integers in its own
+// FP32 columns of tensor memory.  A pair's sum over 256 values of k is at most 2^14 * 256 =
+// 2^22 in magnitude, so FP32 holds it exactly; every 256 values of k the pairs with p + q <= 6
+// are added, as integers, into three int64 fixed-point words per output (levels 0-2, 3-5, 6).
+// The result is the exact product of the 55-bit operands, rounded once to float64; the
+// dropped pairs p + q > 6 weigh less than 2^-60 (scale of v)(scale of the other operand)
 // per term.  (Ozaki scheme I: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; its
 // tensor-core form: Mukunoki, Ozaki, Ogita, Imamura, ICCS 2020.)
 //
@@ -47,9 +47,11 @@ constexpr int OB_P = 7;           // digits per operand
 constexpr int OB_LMAX = 6;        // pairs p + q <= OB_LMAX are folded
 constexpr int OB_TM = 128;        // MMA M: tile rows
 constexpr int OB_KC = 32;         // k per chunk
-constexpr int OB_FOLD = 2;        // chunks per fold (64 values of k)
-constexpr int OB_STAGES = 3;      // chunks in flight
-constexpr int OB_THREADS = 128;   // four warps: TMEM lanes 0..127, one per tile row
+constexpr int OB_FOLD = 8;        // chunks per fold (256 values of k)
+constexpr int OB_STAGES = 3;      // chunks in flight for full 128-row tiles (more, smaller ones for narrow tiles)
+constexpr int OB_MAXSTAGES = 16;
+constexpr int OB_FOLD_THREADS = 128;  // warps 0-3 fold: TMEM lanes 0..127, one per tile row
+constexpr int OB_THREADS = OB_FOLD_THREADS + 64;  // + warp 4: bulk copies, warp 5: MMAs
 constexpr int OB_ATILE = OB_TM * OB_KC;  // BF16 elements of one basis digit tile (8 KB)
 constexpr int OB_WAIT_ITERS = 1 << 20;
 constexpr int OB_EXP_BAD = 1 << 20;      // exponent sentinel: a non-finite value
@@ -58,11 +60,14 @@ template <int S>
 struct ObShape {
   static constexpr int NP = (OB_P * S + 15) / 16 * 16;  // MMA N: digit columns of the other operand
   static constexpr int BTILE = NP * OB_KC;              // BF16 elements of one of its tiles
-  static constexpr int TMEM_COLS = OB_P * NP <= 256 ? 256 : 512;
+  static constexpr int NBUF = 2 * OB_P * NP <= 512 ? 2 : 1;  // accumulator buffers
+  static constexpr int TMEM_COLS = NBUF * OB_P * NP <= 256 ? 256 : 512;
   static constexpr uint32_t ABYTES = OB_ATILE * 2;
   static constexpr uint32_t BBYTES = BTILE * 2;
   static constexpr size_t STAGE = (size_t)OB_P * ABYTES + BBYTES;
-  static constexpr size_t SMEM = OB_STAGES * STAGE + 1024 + 128;  // + alignment, barriers
+  static constexpr size_t REGION = OB_STAGES * STAGE;  // stage slots
+  // + 8 KB: an MMA reads all 128 rows of a plane's tile, past a narrow slot's end
+  static constexpr size_t SMEM = REGION + 8192 + 1024 + 512;
 };
 
 __device__ __forceinline__ uint32_t ob_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,25 +92,26 @@ __device__ __forceinline__ int ob_cm(int i, int k) {
   return (((i >> 3) * 4 + (k >> 3)) << 6) + ((i & 7) << 3) + (k & 7);
 }
 
-// e = 1 + floor(log2 m) for the IEEE bits m of a non-negative double (0 for zero or
-// subnormal, OB_EXP_BAD for a non-finite value): every |x| <= m satisfies |x| < 2^e.
+// e = 2 + floor(log2 m) for the IEEE bits m of a non-negative double (0 for zero or
+// subnormal, OB_EXP_BAD for a non-finite value): every |x| <= m satisfies |x| < 2^{e-1}, one
+// bit of headroom that keeps every digit within [-128, 128].
 __device__ __forceinline__ int ob_exponent(unsigned long long m) {
   if (m >= 0x7FF0000000000000ull) return OB_EXP_BAD;
   if (m < 0x0010000000000000ull) return 0;
-  return (int)(m >> 52) - 1023 + 1;
+  return (int)(m >> 52) - 1023 + 2;
 }
 
-// The seven digits of x 2^sc on the scale 2^e (|x 2^sc| < 2^e): N = round(x 2^{sc+56-e})
-// (ties away from zero; |N| <= 2^56), sliced from the top with rounding to nearest, so that
-// x 2^sc = 2^e sum_p d_p 2^{-8(p+1)} up to 2^{e-57}.  Integer operations only (the FP64 pipe
-// is narrow on this GPU); zero and subnormal x give zero digits.
+// The seven digits of x 2^sc on the scale 2^e (|x 2^sc| < 2^{e-1}): N = round(x 2^{sc+56-e})
+// (ties away from zero; |N| <= 2^55), sliced from the top with rounding to nearest, so that
+// x 2^sc = 2^e sum_p d_p 2^{-8(p+1)} up to 2^{e-57}, every d_p in [-128, 128].  Integer
+// operations only (the FP64 pipe is narrow on this GPU); zero and subnormal x give zero digits.
 __device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P]) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   long long N = 0;
   if (ex != 0 && ex != 0x7FF && e != OB_EXP_BAD) {
     const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = ex - 1075 + sc + 56 - e;  // N = mant 2^sh; |x 2^sc| < 2^e gives sh <= 3
+    const int sh = ex - 1075 + sc + 56 - e;  // N = mant 2^sh; |x 2^sc| < 2^{e-1} gives sh <= 2
     unsigned long long u;
     if (sh >= 0)
       u = mant << sh;
@@ -125,7 +131,7 @@ __device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P
   d[OB_P - 1] = (int)N;
 }
 
-__device__ __forceinline__ __nv_bfloat16 ob_bf(int d) { return __float2bfloat16_rn((float)d); }  // |d| <= 256: exact
+__device__ __forceinline__ __nv_bfloat16 ob_bf(int d) { return __float2bfloat16_rn((float)d); }  // |d| <= 128: exact
 
 // mx[t] = max over rows of |X[row][t]| as IEEE bits (X row-major n x S); mx zeroed beforehand.
 template <int S>
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int j
   if (threadIdx.x < S) {
     long long v = LLONG_MIN;
     for (int q = 0; q < NT / 32; ++q) v = max(v, kmax[q][threadIdx.x]);
-    const int e = bad ? OB_EXP_BAD : (v == LLONG_MIN ? 0 : (int)(v >> 52) - 1023 + 1);
+    const int e = bad ? OB_EXP_BAD : (v == LLONG_MIN ? 0 : (int)(v >> 52) - 1023 + 2);
     esh[threadIdx.x] = e;
     eh[threadIdx.x] = e;
   }
@@ -275,7 +281,8 @@ __device__ __forceinline__ bool ob_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-// v: an FP32 pair sum, an exact integer with |v| <= 2^22; its value from the bits of
+// v: an FP32 pair sum, an exact integer with |v| <= 2^22 (at most 256 products of two digits
+// in [-128, 128]); its value from the bits of
 // v + 1.5 * 2^23 (exact in that range).
 __device__ __forceinline__ long long ob_int(uint32_t r) {
   return (long long)(__float_as_int(__fadd_rn(__uint_as_float(r), 12582912.0f)) - 0x4B400000);
@@ -301,119 +308,149 @@ struct ObArgs {
   double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
 };
 
-// GRAM: CTA (m tile, k split) adds the partial V^T Y of its rows into out.  Update: CTA c
-// takes row tiles c, c + grid, ... and subtracts V H from those rows of Y.  Thread 0 issues
-// the bulk copies (OB_STAGES chunks in flight) and the MMAs; all threads fold the tensor
-// memory every OB_FOLD chunks.  A wait that gives up sets the solve status to ST_WAIT_TIMEOUT.
+// GRAM: CTA (m tile, k split) writes the partial V^T Y of its rows.  Update: CTA c takes
+// row tiles c, c + grid, ... and subtracts V H from those rows of Y.  Warp 4 (one lane) issues
+// the bulk copies into the stage slots as they free up; warp 5 (one lane) issues the MMAs as the
+// chunks land; warps 0-3 fold the tensor memory once per OB_FOLD chunks (a fold period) and
+// write the results.  With two accumulator buffers the MMAs of a period run while the previous
+// period is folded.  A wait that gives up sets the solve status to ST_WAIT_TIMEOUT.
 template <int S, bool GRAM>
 __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
   using Sh = ObShape<S>;
   constexpr int NP = Sh::NP;
+  constexpr int NBUF = Sh::NBUF;
   if (stopped(a.st)) return;
   extern __shared__ __align__(1024) unsigned char ob_smem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)ob_smem + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(base + OB_STAGES * Sh::STAGE);  // full[STAGES], empty[STAGES], acc
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * OB_STAGES + 1);
-  __shared__ double shred[(OB_THREADS / 32) * S * S];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  // barriers: full[MAXSTAGES], empty[MAXSTAGES] (copies / MMAs of a stage), accf[2] (a
+  // buffer's period is accumulated), acce[2] (a buffer is folded), done (MMAs of a failed run)
+  uint64_t* bars = (uint64_t*)(base + Sh::REGION + 8192);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * OB_MAXSTAGES + 5);
+  __shared__ double shred[4 * S * S];
+  __shared__ int fail_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   int ntiles, nch, c0 = 0, rg = OB_TM / 8;
+  const int mt = (int)blockIdx.x;
   if (GRAM) {
+    // every split of every tile has the same number of chunks: the MMAs of a chunk cost the
+    // same for a narrow tile, and they bound a narrow tile's chunk, not its bytes
     const int kcn = (int)((a.n + OB_KC - 1) / OB_KC);
     c0 = (int)blockIdx.y * a.cps;
     nch = max(0, min(a.cps, kcn - c0));
     ntiles = 1;
-    rg = min(OB_TM / 8, (a.js - (int)blockIdx.x * OB_TM + 7) / 8);  // 8-row groups holding basis columns
+    rg = min(OB_TM / 8, (a.js - mt * OB_TM + 7) / 8);  // 8-row groups holding basis columns
   } else {
     const int it = (int)((a.n + OB_TM - 1) / OB_TM);
     ntiles = (int)blockIdx.x < it ? (it - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     nch = (a.js + OB_KC - 1) / OB_KC;
   }
   const int NI = ntiles * nch;
-  const uint32_t abytes = (uint32_t)rg * 512;
+  const int npt = (nch + OB_FOLD - 1) / OB_FOLD;  // fold periods per tile
+  const int NF = ntiles * npt;
+  const uint32_t abytes = (uint32_t)rg * 512;  // per digit plane and chunk: the tile's row groups
+  // stage slots: a narrow tile (Gram, few basis columns) gets more of them, so that about the
+  // same number of bytes stays in flight
+  const uint32_t slot = OB_P * abytes + Sh::BBYTES;
+  const int ns = min(OB_MAXSTAGES, (int)(Sh::REGION / slot));
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ob_smem_u32(tmem_slot)),
                  "r"(Sh::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  const uint32_t bfull = ob_smem_u32(bars), bempty = ob_smem_u32(bars + OB_STAGES),
-                 bacc = ob_smem_u32(bars + 2 * OB_STAGES);
+  const uint32_t bfull = ob_smem_u32(bars), bempty = ob_smem_u32(bars + OB_MAXSTAGES),
+                 baccf = ob_smem_u32(bars + 2 * OB_MAXSTAGES), bacce = ob_smem_u32(bars + 2 * OB_MAXSTAGES + 2),
+                 bdone = ob_smem_u32(bars + 2 * OB_MAXSTAGES + 4);
   if (tid == 0) {
-    for (int i = 0; i < 2 * OB_STAGES + 1; ++i)
+    for (int i = 0; i < 2 * OB_MAXSTAGES + 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ob_smem_u32(bars + i)));
+    for (int i = 0; i < 2; ++i)  // every fold thread arrives
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bacce + 8 * i), "r"(OB_FOLD_THREADS));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bdone));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    fail_sh = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
+  __shared__ int issued_sh, consumed_sh;  // items whose copies were issued / whose MMAs were issued
 
-  auto issue = [&](int i) {  // thread 0: bulk copies of item i into stage i % OB_STAGES
-    const int stg = i % OB_STAGES;
-    const int tile = i / nch, c = i - tile * nch;
-    unsigned char* sa = base + stg * Sh::STAGE;
-    unsigned char* sb = sa + OB_P * Sh::ABYTES;
-    const __nv_bfloat16* ga;
-    const __nv_bfloat16* gb;
-    if (GRAM) {
-      const int kc = c0 + c;
-      ga = a.A + ((int64_t)kc * a.MT + blockIdx.x) * OB_ATILE;
-      gb = a.B + (int64_t)kc * Sh::BTILE;
-    } else {
-      const int it = (int)blockIdx.x + tile * (int)gridDim.x;
-      ga = a.A + ((int64_t)c * a.MT + it) * OB_ATILE;
-      gb = a.B + (int64_t)c * Sh::BTILE;
-    }
-    const uint32_t bar = bfull + 8 * stg;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OB_P * abytes + Sh::BBYTES)
-                 : "memory");
+  if (warp == OB_FOLD_THREADS / 32) {
+    // ---------------------------------------------------------------- bulk copies
+    if (lane == 0) {
+      bool ok = true;
+      int i = 0;
+      for (; i < NI; ++i) {
+        const int stg = i % ns;
+        // the stage is free once the MMAs of its previous chunk are done
+        if (i >= ns && !ob_wait(bempty + 8 * stg, (uint32_t)(i / ns - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const int tile = i / nch, c = i - tile * nch;
+        unsigned char* sa = base + stg * slot;
+        unsigned char* sb = sa + OB_P * abytes;
+        const __nv_bfloat16* ga;
+        const __nv_bfloat16* gb;
+        if (GRAM) {
+          const int kc = c0 + c;
+          ga = a.A + ((int64_t)kc * a.MT + mt) * OB_ATILE;
+          gb = a.B + (int64_t)kc * Sh::BTILE;
+        } else {
+          const int it = (int)blockIdx.x + tile * (int)gridDim.x;
+          ga = a.A + ((int64_t)c * a.MT + it) * OB_ATILE;
+          gb = a.B + (int64_t)c * Sh::BTILE;
+        }
+        const uint32_t bar = bfull + 8 * stg;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(OB_P * abytes + Sh::BBYTES)
+                     : "memory");
 #pragma unroll 1
-    for (int p = 0; p < OB_P; ++p)
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       ob_smem_u32(sa + p * Sh::ABYTES)),
-                   "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
-                   : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     ob_smem_u32(sb)),
-                 "l"(gb), "r"(Sh::BBYTES), "r"(bar)
-                 : "memory");
-  };
-
-  long long w0[S], w1[S], w2[S];  // levels 0-2 (unit 2^-16), 3-5 (2^-40), 6 (2^-48) of the pair sums
-  double acc[S][S];               // update: partial Y^T Y
-#pragma unroll
-  for (int t = 0; t < S; ++t) {
-    w0[t] = w1[t] = w2[t] = 0;
-#pragma unroll
-    for (int u = 0; u < S; ++u) acc[u][t] = 0.0;
-  }
-  int issued = 0, consumed = 0;
-  bool ok0 = true;  // thread 0's waits
-  if (tid == 0)
-    for (; issued < min(OB_STAGES, NI); ++issued) issue(issued);
-  const uint32_t id = ob_idesc(OB_TM, NP);
-  uint32_t accph = 0;
-  bool ok = true;
-  for (int i = 0; i < NI; ++i) {
-    const int tile = i / nch, c = i - tile * nch;
-    if (tid == 0 && ok0) {
-      const int stg = i % OB_STAGES;
-      if (ob_wait(bfull + 8 * stg, (uint32_t)(i / OB_STAGES) & 1u)) {
-        ++consumed;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int p = 0; p < OB_P; ++p)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           ob_smem_u32(sa + p * abytes)),
+                       "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
+                       : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         ob_smem_u32(sb)),
+                     "l"(gb), "r"(Sh::BBYTES), "r"(bar)
+                     : "memory");
+      }
+      issued_sh = i;
+      if (!ok) fail_sh = 1;
+    }
+    __syncwarp();
+  } else if (warp == OB_FOLD_THREADS / 32 + 1) {
+    // ---------------------------------------------------------------- MMAs
+    if (lane == 0) {
+      const uint32_t id = ob_idesc(OB_TM, NP);
+      bool ok = true;
+      int i = 0;
+      for (; i < NI; ++i) {
+        const int tile = i / nch, c = i - tile * nch;
+        const int f = tile * npt + c / OB_FOLD, buf = f % NBUF;
         const bool first = (c % OB_FOLD) == 0;
-        const uint32_t sa = ob_smem_u32(base + stg * Sh::STAGE), sb = sa + OB_P * Sh::ABYTES;
+        const bool last = (c % OB_FOLD) == OB_FOLD - 1 || c == nch - 1;
+        // the accumulator buffer is free once the fold of its previous period is done
+        if (first && f >= NBUF && !ob_wait(bacce + 8 * buf, (uint32_t)(f / NBUF - 1) & 1u)) ok = false;
+        const int stg = i % ns;
+        if (ok && !ob_wait(bfull + 8 * stg, (uint32_t)(i / ns) & 1u)) ok = false;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sa = ob_smem_u32(base + stg * slot), sb = sa + OB_P * abytes;
+        const uint32_t dbase = tmem + (uint32_t)(buf * OB_P * NP);
 #pragma unroll 1
         for (int p = 0; p < OB_P; ++p) {
 #pragma unroll
           for (int ks = 0; ks < OB_KC / 16; ++ks) {
-            const uint64_t da = ob_sdesc(sa + p * Sh::ABYTES + ks * 256);
+            const uint64_t da = ob_sdesc(sa + p * abytes + ks * 256);
             const uint64_t db = ob_sdesc(sb + ks * 256);
-            const uint32_t accf = (first && ks == 0) ? 0u : 1u;  // a fold period starts each plane afresh
+            const uint32_t accf = (first && ks == 0) ? 0u : 1u;  // a period starts each plane afresh
             asm volatile(
                 "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(tmem + (uint32_t)(p * NP)),
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(dbase + (uint32_t)(p * NP)),
                 "l"(da), "l"(db), "r"(id), "r"(accf)
                 : "memory");
           }
@@ -421,109 +458,112 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          bempty + 8 * stg)
                      : "memory");
-        if (i >= 1 && issued < NI) {  // refill the stage of item i - 1 once its MMAs are done
-          const int j = i - 1;
-          if (ob_wait(bempty + 8 * (j % OB_STAGES), (uint32_t)(j / OB_STAGES) & 1u)) {
-            issue(issued);
-            ++issued;
-          } else {
-            ok0 = false;
-          }
-        }
-      } else {
-        ok0 = false;
+        if (last)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           baccf + 8 * buf)
+                       : "memory");
       }
+      consumed_sh = i;
+      if (!ok) fail_sh = 1;
     }
-    const bool fold = (c % OB_FOLD) == OB_FOLD - 1 || c == nch - 1;
-    if (!fold) continue;
-    if (tid == 0)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bacc)
-                   : "memory");
-    const bool wok = ob_wait(bacc, accph);
-    accph ^= 1u;
-    ok = __syncthreads_and(wok && ok0);
-    if (!ok) break;
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- folds and results
+    long long w0[S], w1[S], w2[S];  // levels 0-2 (unit 2^-16), 3-5 (2^-40), 6 (2^-48) of the pair sums
+    double acc[S][S];               // update: partial Y^T Y
 #pragma unroll
-    for (int p = 0; p < OB_P; ++p) {
-      constexpr int NCMAX = (OB_LMAX + 1) * S;
+    for (int t = 0; t < S; ++t) {
+      w0[t] = w1[t] = w2[t] = 0;
 #pragma unroll
-      for (int cb = 0; cb < NCMAX; cb += 32) {
-        if (cb < (OB_LMAX - p + 1) * S) {
-          uint32_t r[32];
-          const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * NP + cb);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(addr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int u = 0; u < S; ++u) acc[u][t] = 0.0;
+    }
+    bool ok = true;
+    for (int f = 0; f < NF; ++f) {
+      const int buf = f % NBUF;
+      if (!ob_wait(baccf + 8 * buf, (uint32_t)(f / NBUF) & 1u)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * OB_P * NP);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = cb + j, q = col / S, t = col % S, L = p + q;
-            if (q <= OB_LMAX - p) {
-              const long long v = ob_int(r[j]);
-              if (L <= 2)
-                w0[t] += v << (8 * (2 - L));
-              else if (L <= 5)
-                w1[t] += v << (8 * (5 - L));
-              else
-                w2[t] += v;
+      for (int p = 0; p < OB_P; ++p) {
+        constexpr int NCMAX = (OB_LMAX + 1) * S;
+#pragma unroll
+        for (int cb = 0; cb < NCMAX; cb += 32) {
+          if (cb < (OB_LMAX - p + 1) * S) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(tbase + (uint32_t)(p * NP + cb)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = cb + j, q = col / S, t = col % S, L = p + q;
+              if (q <= OB_LMAX - p) {
+                const long long v = ob_int(r[j]);
+                if (L <= 2)
+                  w0[t] += v << (8 * (2 - L));
+                else if (L <= 5)
+                  w1[t] += v << (8 * (5 - L));
+                else
+                  w2[t] += v;
+              }
             }
           }
         }
       }
-    }
-    if (!GRAM && c == nch - 1) {  // the tile is complete: Y -= V H on its rows
-      const int it = (int)blockIdx.x + tile * (int)gridDim.x;
-      const int64_t row = (int64_t)it * OB_TM + tid;
-      if (row < a.n) {
-        double y[S];
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bacce + 8 * buf) : "memory");
+      if (!GRAM && f % npt == npt - 1) {  // the tile is complete: Y -= V H on its rows
+        const int it = (int)blockIdx.x + (f / npt) * (int)gridDim.x;
+        const int64_t row = (int64_t)it * OB_TM + tid;
+        if (row < a.n) {
+          double y[S];
 #pragma unroll
-        for (int t = 0; t < S; ++t) {
-          const int f = a.eb[t];
-          double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
-          v = f == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll) : v * ob_pow2(f);
-          y[t] = a.out[row * S + t] - v;
+          for (int t = 0; t < S; ++t) {
+            const int fe = a.eb[t];
+            double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
+            v = fe == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll) : v * ob_pow2(fe);
+            y[t] = a.out[row * S + t] - v;
+          }
+#pragma unroll
+          for (int t = 0; t < S; ++t) a.out[row * S + t] = y[t];
+          if (a.self) {
+#pragma unroll
+            for (int u = 0; u < S; ++u)
+#pragma unroll
+              for (int t = 0; t < S; ++t) acc[u][t] += y[u] * y[t];
+          }
         }
 #pragma unroll
-        for (int t = 0; t < S; ++t) a.out[row * S + t] = y[t];
-        if (a.self) {
-#pragma unroll
-          for (int u = 0; u < S; ++u)
-#pragma unroll
-            for (int t = 0; t < S; ++t) acc[u][t] += y[u] * y[t];
-        }
+        for (int t = 0; t < S; ++t) w0[t] = w1[t] = w2[t] = 0;
       }
-#pragma unroll
-      for (int t = 0; t < S; ++t) w0[t] = w1[t] = w2[t] = 0;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // tensor memory is free for the next fold period
-  }
-
-  if (ok) {
-    if (GRAM) {
-      const int m = (int)blockIdx.x * OB_TM + tid;
+    if (!ok) fail_sh = 1;
+    if (ok && GRAM) {
+      const int m = mt * OB_TM + tid;
       if (m < a.js) {
         const int e = a.ea[m];
         double* o = a.out + (int64_t)blockIdx.y * ((int64_t)a.js * S) + (int64_t)m * S;
 #pragma unroll
         for (int t = 0; t < S; ++t) {
-          const int f = a.eb[t];
+          const int fe = a.eb[t];
           double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
           // 2^{e+f} in two steps: each factor stays in the normal range
-          v = (e == OB_EXP_BAD || f == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                   : v * ob_pow2(e) * ob_pow2(f);
+          v = (e == OB_EXP_BAD || fe == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                    : v * ob_pow2(e) * ob_pow2(fe);
           o[t] = v;
         }
       }
-    } else if (a.self) {
-      const int wv = tid >> 5, l = tid & 31;
+    }
+    if (!GRAM && a.self) {
 #pragma unroll
       for (int u = 0; u < S; ++u)
 #pragma unroll
@@ -531,25 +571,26 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
           double v = acc[u][t];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (l == 0) shred[wv * S * S + u * S + t] = v;
+          if (lane == 0) shred[warp * S * S + u * S + t] = v;
         }
-      __syncthreads();
-      if (tid < S * S) {
-        double v = 0.0;
-        for (int q = 0; q < OB_THREADS / 32; ++q) v += shred[q * S * S + tid];
-        a.self[(int64_t)blockIdx.x * S * S + tid] = v;
-      }
     }
-  } else {
-    if (tid == 0) {
+  }
+  __syncthreads();
+  if (fail_sh) {
+    if (tid == OB_FOLD_THREADS) {
       a.st->breakdown_where = GRAM ? 210 : 211;
       atomicExch(&a.st->status, (int)ST_WAIT_TIMEOUT);
-      // copies still in flight land in shared memory: wait for them (bounded), and for the MMAs
-      for (int j = consumed; j < issued; ++j) ob_wait(bfull + 8 * (j % OB_STAGES), (uint32_t)(j / OB_STAGES) & 1u);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bacc)
+      // copies still in flight land in shared memory: wait for them (bounded)
+      for (int j = consumed_sh; j < issued_sh; ++j) ob_wait(bfull + 8 * (j % ns), (uint32_t)(j / ns) & 1u);
+    } else if (tid == OB_FOLD_THREADS + 32) {  // the MMAs this thread issued (bounded)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bdone)
                    : "memory");
-      ob_wait(bacc, accph);
+      ob_wait(bdone, 0);
     }
+  } else if (!GRAM && a.self && tid < S * S) {
+    double v = 0.0;
+    for (int q = 0; q < 4; ++q) v += shred[q * S * S + tid];
+    a.self[(int64_t)blockIdx.x * S * S + tid] = v;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
