@@ -377,9 +377,12 @@ def max_over_ranks(x: float, dist=None) -> float:
     return float(t.item())
 
 
-# (kernel class, precision) -> (DRAM read + write MB, algorithmic MB, summary) of one ncu capture
+# (kernel class, precision, tensor-core basis) -> (DRAM read + write MB, algorithmic MB, summary)
+# of one ncu capture of that kernel
 NCU_DRAM_PER_ALGORITHMIC = {
-    ("gram", "fp64"): (318.5, 318.8, "profiles/gram_update_fp64_convdiff64x48_s4.md"),
+    ("gram", "fp64", False): (318.5, 318.8, "profiles/gram_update_fp64_convdiff64x48_s4.md"),
+    ("gram", "fp64", True): (788.8, 436.2, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
+    ("update", "fp64", True): (840.6, 444.6, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
 }
 
 
@@ -456,7 +459,15 @@ def run_ours(args):
     dname, d = dom
     ai = d["flops"] / max(d["bytes"], 1.0)
     ridge = FP64_NOMINAL_TFLOPS * 1e12 / (pk["hbm_gbs"] * 1e9)
-    if ai > ridge or dname.startswith("small_gemm"):
+    # the float64 Arnoldi basis on the tensor cores (its digit planes are written by the
+    # "basis_split" kernels): Gram and update are bound by HBM, not by the FP64 pipe
+    tensor_basis = "basis_split" in prof
+    if tensor_basis and dname in ("gram", "update"):
+        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "kernel": dname, "peak_src": f"{pk['src']} HBM copy",
+                "bytes_src": "algorithmic: the float64 basis (8 B per element) and the block Y, each read once; "
+                             "the kernel reads the basis as seven BF16 digit planes (14 B per element)"}
+    elif ai > ridge or dname.startswith("small_gemm"):
         roof = {"bound": "alu", "achieved": d["flops"] / (d["ms"] * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "kernel": dname,
                 "peak_src": "FP64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 figure in MEASURED_PEAKS)"}
@@ -467,9 +478,11 @@ def run_ours(args):
     # DRAM bytes per algorithmic byte from one ncu capture of the same kernel on a smaller case,
     # scaled to the average launch of this run by its algorithmic bytes (the kernel reads each
     # basis element once, so traffic grows in proportion)
-    ratio = NCU_DRAM_PER_ALGORITHMIC.get((dname, args.precision))
+    ratio = NCU_DRAM_PER_ALGORITHMIC.get((dname, args.precision, tensor_basis))
     roof["traffic"] = ratio[0] / ratio[1] * d["bytes"] / max(1, d["launches"]) if ratio else None
     roof["traffic_src"] = ratio[2] if ratio else None
+    if ratio and roof["unit"] == "GB/s":  # the fraction of the copy bandwidth on what the kernel moves
+        roof["frac_of_traffic"] = roof["achieved"] * ratio[0] / ratio[1] / roof["peak"]
     roof["launches"] = d["launches"]
     roof["avg_launch_us"] = d["ms"] * 1e3 / max(1, d["launches"])
     hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
