@@ -481,6 +481,8 @@ void setup_qr(sylv_handle* h, int si) {
   Side& sd = h->side[si];
   const int s = (int)h->s;
   T* V0 = (T*)sd.V;
+  // tensor-core basis: the column maxima are combined from zero (the last scale fills [0, 8))
+  if (sd.ob.G) cudaMemsetAsync(sd.ob.mx, 0, 16 * sizeof(unsigned long long), h->stream);
   sylv::launch_pack<T>(h->stream, sd.n, s, sd.C, V0);
   int nc = sylv::launch_selfgram<T>(h->stream, h->st, sd.n, s, V0, h->spart);
   sylv::CholArgs a{};
@@ -499,7 +501,7 @@ void setup_qr(sylv_handle* h, int si) {
   a.pass = 2;
   a.Rout = sd.RQR;
   sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
-  sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr);
+  sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr, sd.ob.G ? sd.ob.mx : nullptr);
   if (sd.ob.G) sylv::launch_ob_split_basis(h->stream, h->st, sd.n, s, (const double*)V0, 0, sd.ob);
 }
 
@@ -526,6 +528,8 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   const double spmm_flops = 2.0 * sd.nnz * s + (lanczos && q >= 1 ? 2.0 * ns * s : 0.0);
   const int nb = lanczos ? 1 : q + 1;
   const T* Vfirst = lanczos ? Vq : V;
+  // float64 Arnoldi: the Gram products and updates on the tensor cores, on the digit planes
+  const bool ob = !lanczos && sd.ob.G != nullptr;
   const double gram_bytes = ns * b * (nb + 1), gram_flops = 2.0 * ns * nb * s;
   const double upd_bytes = ns * b * (nb + 2), upd_flops = 2.0 * ns * nb * s;
   if (lanczos) {
@@ -535,11 +539,10 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
          sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, Vprev, M, ldh));
   } else {
     PROF(h, KC_SPMM, spmm_bytes, spmm_flops,
-         sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, nullptr, nullptr, 0));
+         sylv::launch_spmm<T>(st, h->st, n, s, sd.rp, sd.ci, op_val<T>(sd), Vq, Y, nullptr, nullptr, 0,
+                              ob ? sd.ob.mx + 8 : nullptr));
   }
   const int passes = lanczos ? 1 : 2;  // block Lanczos: one projection; Arnoldi: BCGS2
-  // float64 Arnoldi: the Gram products and updates on the tensor cores, on the digit planes
-  const bool ob = !lanczos && sd.ob.G != nullptr;
   const int js = nb * s;
   for (int pass = 0; pass < passes; ++pass) {
     const bool last = pass == passes - 1;
@@ -549,7 +552,7 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
       PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
            sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1, false));
       PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
-           nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr));
+           nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr, !last));
       continue;
     }
     PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));
@@ -578,7 +581,8 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   a.Hsub = sd.H + (int64_t)(q + 1) * s + (int64_t)q * s * ldh;
   a.Hsup = lanczos ? sd.H + (int64_t)q * s + (int64_t)(q + 1) * s * ldh : nullptr;
   PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
-  PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1), sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr));
+  PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1),
+       sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr, ob ? sd.ob.mx : nullptr));
   if (ob)
     PROF(h, KC_BSPLIT, 2.0 * ns * b + 28.0 * ns, 0.0,
          sylv::launch_ob_split_basis(st, h->st, n, s, (const double*)Y, (q + 1) * s, sd.ob));

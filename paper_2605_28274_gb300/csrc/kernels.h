@@ -31,7 +31,9 @@ struct ObSide {
   int* vexp = nullptr;     // exponents of the basis columns
   int* ey = nullptr;       // exponents of the columns of Y
   int* eh = nullptr;       // exponents of the columns of the coefficient block
-  unsigned long long* mx = nullptr;  // column maxima: [0, 8) new basis block, [8, 16) Y
+  // column maxima of |x| as IEEE bits, [0, 8) the new basis block (from the last CholQR scale),
+  // [8, 16) Y (from the SpMM and the first update); the coefficient-block split zeroes both
+  unsigned long long* mx = nullptr;
   int64_t np = 0;          // basis rows padded to 128
   int rp = 0;              // basis columns padded to 128
   int64_t plane = 0;       // elements per digit plane
@@ -39,15 +41,17 @@ struct ObSide {
 size_t ob_side_bytes(int64_t n, int R, int s);
 void ob_carve(void* mem, int64_t n, int R, int s, ObSide& o);
 bool ob_setup();
-// Digits of the new basis block Vb (n x s row-major; basis columns col0 .. col0 + s - 1).
+// Digits of the new basis block Vb (n x s row-major; basis columns col0 .. col0 + s - 1), whose
+// column maxima the last CholQR scale left in mx[0, 8).
 void launch_ob_split_basis(cudaStream_t, const DevState*, int64_t n, int s, const double* Vb, int col0, const ObSide&);
 // Per-split partial Gram products V^T Y over the first js basis columns (the partial layout of
-// launch_gram); returns the number of splits.
+// launch_gram), Y's column maxima in mx[8, 16); returns the number of splits.
 int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Y, const ObSide&, double* partial);
 // Y -= V Hc over the first js basis columns (Hc: js x s, the layout launch_reduce_H writes),
-// with the optional per-CTA partial Y^T Y of the result; returns the number of CTAs.
+// with the optional per-CTA partial Y^T Y of the result and, with ymax, the column maxima of
+// the result into mx[8, 16); returns the number of CTAs.
 int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
-                     double* self_partial);
+                     double* self_partial, bool ymax);
 
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
@@ -60,7 +64,8 @@ void set_last_error(const std::string& msg);
 // three-term recurrence of block Lanczos (M = H_{j-1,j}, s x s, column-major ld ldm).
 template <typename T>
 void launch_spmm(cudaStream_t, const DevState*, int64_t n, int s, const int32_t* rp, const int32_t* ci,
-                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm);
+                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm,
+                 unsigned long long* colmax = nullptr);
 
 // Per-CTA partial Gram products  P_c = sum over the CTA's rows of V_b^T Y  for
 // blocks b = 0..nb-1 (V points at the first block), written in the factor precision T
@@ -87,7 +92,8 @@ int launch_selfgram(cudaStream_t, const DevState*, int64_t n, int s, const T* Y,
 // Y <- Y Rinv (Rinv s x s upper triangular, column-major), optionally with partials of
 // the new Y^T Y.  Returns the number of CTAs.
 template <typename T>
-int launch_scale(cudaStream_t, const DevState*, int64_t n, int s, T* Y, const T* RinvT, double* self_partial);
+int launch_scale(cudaStream_t, const DevState*, int64_t n, int s, T* Y, const T* RinvT, double* self_partial,
+                 unsigned long long* colmax = nullptr);
 
 // One Cholesky pass of CholQR2 on the s x s Gram reduced from the partials.
 struct CholArgs {

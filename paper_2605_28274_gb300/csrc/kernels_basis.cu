@@ -107,27 +107,37 @@ __device__ __forceinline__ void block_reduce_tile(A (&acc)[S][S], double* out, d
 // ---------------------------------------------------------------- SpMM
 // One thread per (row, column t): Y[row][t] = sum_p val[p] X[col[p]][t] (- sum_u Xprev[row][u] M[u][t]).
 // The s threads of a row read the same (col, val) pair (broadcast) and s adjacent
-// values of the gathered row (one sector).
+// values of the gathered row (one sector).  colmax (float64 only, may be null): the column
+// maxima of |Y| as IEEE bits, combined with atomicMax (the digit split of the tensor-core basis).
 template <typename T, int S>
 __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ ci, const T* __restrict__ val,
                                                   const T* __restrict__ X, T* __restrict__ Y,
                                                   const T* __restrict__ Xprev, const double* __restrict__ M,
-                                                  int64_t ldm) {
+                                                  int64_t ldm, unsigned long long* __restrict__ colmax) {
   if (stopped(st)) return;
   const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int64_t row = gid / S;
   const int t = (int)(gid - row * S);
-  if (row >= n) return;
   using A = typename AccOf<T>::type;
   A acc = 0;
-  const int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
-  for (int p = p0; p < p1; ++p) acc += (A)__ldg(val + p) * (A)__ldg(X + (int64_t)__ldg(ci + p) * S + t);
-  if (Xprev != nullptr) {
+  if (row < n) {
+    const int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
+    for (int p = p0; p < p1; ++p) acc += (A)__ldg(val + p) * (A)__ldg(X + (int64_t)__ldg(ci + p) * S + t);
+    if (Xprev != nullptr) {
 #pragma unroll
-    for (int u = 0; u < S; ++u) acc -= (A)__ldg(Xprev + row * S + u) * (A)M[u + (int64_t)t * ldm];
+      for (int u = 0; u < S; ++u) acc -= (A)__ldg(Xprev + row * S + u) * (A)M[u + (int64_t)t * ldm];
+    }
+    Y[row * S + t] = (T)acc;
   }
-  Y[row * S + t] = (T)acc;
+  if (colmax != nullptr) {
+    __shared__ unsigned long long smx[S];
+    if (threadIdx.x < S) smx[threadIdx.x] = 0;
+    __syncthreads();
+    if (row < n) atomicMax(&smx[t], (unsigned long long)__double_as_longlong(fabs((double)acc)));
+    __syncthreads();
+    if (threadIdx.x < S && smx[threadIdx.x]) atomicMax(colmax + threadIdx.x, smx[threadIdx.x]);
+  }
 }
 
 // ---------------------------------------------------------------- Gram (TSGEMM)
@@ -330,12 +340,19 @@ __global__ void __launch_bounds__(NT) selfgram_kernel(const DevState* st, int64_
   block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
 }
 
+// colmax (float64 only, may be null): the column maxima of |result| as IEEE bits (atomicMax).
 template <typename T, int S, bool SELF>
 __global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n, T* __restrict__ Y,
-                                                   const T* __restrict__ Rinv, double* __restrict__ partial) {
+                                                   const T* __restrict__ Rinv, double* __restrict__ partial,
+                                                   unsigned long long* __restrict__ colmax) {
   if (stopped(st)) return;
   __shared__ T rs[S * S];
   __shared__ double sh[(NT / 32) * S * S];
+  __shared__ unsigned long long smx[S];
+  unsigned long long zmax[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) zmax[t] = 0;
+  if (threadIdx.x < S) smx[threadIdx.x] = 0;
   if (threadIdx.x < S * S) rs[threadIdx.x] = Rinv[threadIdx.x];
   __syncthreads();
   using A = typename AccOf<T>::type;
@@ -363,8 +380,24 @@ __global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n
 #pragma unroll
         for (int t = 0; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];
     }
+    if (colmax != nullptr) {
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        zmax[t] = max(zmax[t], (unsigned long long)__double_as_longlong(fabs((double)z[t])));
+    }
   }
   if constexpr (SELF) block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+  if (colmax != nullptr) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      unsigned long long v = zmax[t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((threadIdx.x & 31) == 0 && v) atomicMax(&smx[t], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < S && smx[threadIdx.x]) atomicMax(colmax + threadIdx.x, smx[threadIdx.x]);
+  }
 }
 
 // ---------------------------------------------------------------- CholQR pass
@@ -576,12 +609,13 @@ int grid_for(int64_t work, int64_t per, int cap) {
 
 template <typename T>
 void launch_spmm(cudaStream_t strm, const DevState* st, int64_t n, int s, const int32_t* rp, const int32_t* ci,
-                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm) {
+                 const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm,
+                 unsigned long long* colmax) {
   const int64_t threads = n * s;
   const int grid = (int)((threads + NT - 1) / NT);
   if (grid == 0) return;
 #define CASE(SV) \
-  case SV: spmm_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm); break;
+  case SV: spmm_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm, colmax); break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
 }
@@ -642,14 +676,15 @@ int launch_selfgram(cudaStream_t strm, const DevState* st, int64_t n, int s, con
 }
 
 template <typename T>
-int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, const T* RinvT, double* self_partial) {
+int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, const T* RinvT, double* self_partial,
+                 unsigned long long* colmax) {
   const int grid = grid_for(n, NT, 4 * num_sms());
 #define CASE(SV)                                                                               \
   case SV:                                                                                     \
     if (self_partial)                                                                          \
-      scale_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, self_partial);         \
+      scale_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, self_partial, colmax); \
     else                                                                                       \
-      scale_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, nullptr);             \
+      scale_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, nullptr, colmax);     \
     break;
   switch (s) { SYLV_S_CASES(CASE) }
 #undef CASE
@@ -685,13 +720,14 @@ void launch_convert(cudaStream_t strm, int64_t count, const double* src, T* dst)
 
 #define SYLV_INST(T)                                                                                              \
   template void launch_spmm<T>(cudaStream_t, const DevState*, int64_t, int, const int32_t*, const int32_t*,      \
-                               const T*, const T*, T*, const T*, const double*, int64_t);                        \
+                               const T*, const T*, T*, const T*, const double*, int64_t, unsigned long long*);   \
   template int launch_gram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, int64_t, int, const T*,     \
                               double*);                                                                          \
   template int launch_update<T>(cudaStream_t, const DevState*, int64_t, int, const T*, int64_t, int,             \
                                 const double*, T*, double*);                                                     \
   template int launch_selfgram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, double*);               \
-  template int launch_scale<T>(cudaStream_t, const DevState*, int64_t, int, T*, const T*, double*);              \
+  template int launch_scale<T>(cudaStream_t, const DevState*, int64_t, int, T*, const T*, double*,              \
+                                unsigned long long*);                                                            \
   template void launch_pack<T>(cudaStream_t, int64_t, int, const double*, T*);                                  \
   template void launch_unpack<T>(cudaStream_t, int64_t, int, int, const T*, int64_t, double*);                  \
   template void launch_convert<T>(cudaStream_t, int64_t, const double*, T*);

@@ -133,28 +133,6 @@ __device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P
 
 __device__ __forceinline__ __nv_bfloat16 ob_bf(int d) { return __float2bfloat16_rn((float)d); }  // |d| <= 128: exact
 
-// mx[t] = max over rows of |X[row][t]| as IEEE bits (X row-major n x S); mx zeroed beforehand.
-template <int S>
-__global__ void __launch_bounds__(NT) ob_colmax_kernel(const DevState* st, int64_t n, const double* __restrict__ X,
-                                                       unsigned long long* __restrict__ mx) {
-  if (stopped(st)) return;
-  unsigned long long m[S];
-#pragma unroll
-  for (int t = 0; t < S; ++t) m[t] = 0;
-  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
-#pragma unroll
-    for (int t = 0; t < S; ++t)
-      m[t] = max(m[t], (unsigned long long)__double_as_longlong(X[row * S + t]) & 0x7FFFFFFFFFFFFFFFull);
-  }
-#pragma unroll
-  for (int t = 0; t < S; ++t) {
-    unsigned long long v = m[t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0 && v) atomicMax(mx + t, v);
-  }
-}
-
 // Digits of the new basis block (columns col0 .. col0 + S - 1, row-major n x S) into both
 // layouts, and its column exponents into vexp.  One thread per basis row.
 template <int S>
@@ -213,11 +191,14 @@ __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64
 // Digits of the coefficient block H'(m, t) = 2^{vexp[m]} Hc[m S + t] (m < js; zero up to the
 // next multiple of 32) as the update's other operand, exponents into eh.  One CTA: the column
 // maxima of H' come from integer keys bits(|Hc|) + vexp 2^52, which order like the values.
+// Also zeroes the column maxima mx[0, 16): the ones of the update's result (the next Gram's Y)
+// and of the block that CholQR will scale are combined into them from zero.
 template <int S>
 __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int js, const double* __restrict__ Hc,
                                                        const int* __restrict__ vexp, int* __restrict__ eh,
-                                                       __nv_bfloat16* __restrict__ HB) {
+                                                       __nv_bfloat16* __restrict__ HB, unsigned long long* __restrict__ mx) {
   if (stopped(st)) return;
+  if (threadIdx.x < 16) mx[threadIdx.x] = 0;
   constexpr int NP = ObShape<S>::NP;
   __shared__ long long kmax[NT / 32][S];
   __shared__ int esh[S];
@@ -306,6 +287,7 @@ struct ObArgs {
   const int* eb;           // exponents of the other operand's columns
   double* out;             // Gram: partials [split][m S + t]; update: Y (row-major n x S)
   double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
+  unsigned long long* ymax;  // update: column maxima of |result| as IEEE bits (nullptr: none)
 };
 
 // GRAM: CTA (m tile, k split) writes the partial V^T Y of its rows.  Update: CTA c takes
@@ -327,6 +309,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
   uint64_t* bars = (uint64_t*)(base + Sh::REGION + 8192);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * OB_MAXSTAGES + 5);
   __shared__ double shred[4 * S * S];
+  __shared__ unsigned long long smx[4][S];
   __shared__ int fail_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -471,8 +454,10 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
     // ---------------------------------------------------------------- folds and results
     long long w0[S], w1[S], w2[S];  // levels 0-2 (unit 2^-16), 3-5 (2^-40), 6 (2^-48) of the pair sums
     double acc[S][S];               // update: partial Y^T Y
+    unsigned long long ym[S];       // update: column maxima of |result|
 #pragma unroll
     for (int t = 0; t < S; ++t) {
+      ym[t] = 0;
       w0[t] = w1[t] = w2[t] = 0;
 #pragma unroll
       for (int u = 0; u < S; ++u) acc[u][t] = 0.0;
@@ -534,7 +519,10 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
             y[t] = a.out[row * S + t] - v;
           }
 #pragma unroll
-          for (int t = 0; t < S; ++t) a.out[row * S + t] = y[t];
+          for (int t = 0; t < S; ++t) {
+            a.out[row * S + t] = y[t];
+            ym[t] = max(ym[t], (unsigned long long)__double_as_longlong(fabs(y[t])));
+          }
           if (a.self) {
 #pragma unroll
             for (int u = 0; u < S; ++u)
@@ -563,6 +551,15 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         }
       }
     }
+    if (!GRAM && a.ymax) {
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        unsigned long long v = ym[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) smx[warp][t] = v;
+      }
+    }
     if (!GRAM && a.self) {
 #pragma unroll
       for (int u = 0; u < S; ++u)
@@ -587,10 +584,17 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
                    : "memory");
       ob_wait(bdone, 0);
     }
-  } else if (!GRAM && a.self && tid < S * S) {
-    double v = 0.0;
-    for (int q = 0; q < 4; ++q) v += shred[q * S * S + tid];
-    a.self[(int64_t)blockIdx.x * S * S + tid] = v;
+  } else {
+    if (!GRAM && a.self && tid < S * S) {
+      double v = 0.0;
+      for (int q = 0; q < 4; ++q) v += shred[q * S * S + tid];
+      a.self[(int64_t)blockIdx.x * S * S + tid] = v;
+    }
+    if (!GRAM && a.ymax && tid < S) {
+      unsigned long long v = 0;
+      for (int q = 0; q < 4; ++q) v = max(v, smx[q][tid]);
+      if (v) atomicMax(a.ymax + tid, v);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -665,15 +669,12 @@ bool ob_setup() {
 void launch_ob_split_basis(cudaStream_t strm, const DevState* st, int64_t n, int s, const double* Vb, int col0,
                            const ObSide& o) {
   if (n == 0) return;
-  cudaMemsetAsync(o.mx, 0, 8 * sizeof(unsigned long long), strm);
-  const int gmax = (int)std::min<int64_t>((n + NT - 1) / NT, 4 * ob_sms());
   const unsigned gs = (unsigned)((n + NT - 1) / NT);
   __nv_bfloat16* G = (__nv_bfloat16*)o.G;
   __nv_bfloat16* U = (__nv_bfloat16*)o.U;
   const int MT = o.rp / OB_TM, IT = (int)(o.np / OB_TM);
 #define CASE(SV)                                                                                           \
   case SV:                                                                                                 \
-    ob_colmax_kernel<SV><<<counted(gmax), NT, 0, strm>>>(st, n, Vb, o.mx);                                 \
     ob_vsplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Vb, col0, o.mx, o.vexp, G, U, o.plane, MT, IT); \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
@@ -682,8 +683,6 @@ void launch_ob_split_basis(cudaStream_t strm, const DevState* st, int64_t n, int
 
 int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Y, const ObSide& o,
                    double* partial) {
-  cudaMemsetAsync(o.mx + 8, 0, 8 * sizeof(unsigned long long), strm);
-  const int gmax = (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, 4 * ob_sms()));
   const unsigned gs = (unsigned)std::max<int64_t>(1, (n + NT - 1) / NT);
   const int mtv = (js + OB_TM - 1) / OB_TM;
   const int kcn = (int)std::max<int64_t>(1, (n + OB_KC - 1) / OB_KC);
@@ -703,10 +702,10 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
   a.eb = o.ey;
   a.out = partial;
   a.self = nullptr;
+  a.ymax = nullptr;
   const dim3 grid((unsigned)mtv, (unsigned)ks);
 #define CASE(SV)                                                                                                 \
   case SV:                                                                                                       \
-    ob_colmax_kernel<SV><<<counted(gmax), NT, 0, strm>>>(st, n, Y, o.mx + 8);                                    \
     ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, o.mx + 8, o.ey, (__nv_bfloat16*)o.YB);          \
     ob_kernel<SV, true><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                              \
     break;
@@ -716,7 +715,7 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
 }
 
 int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Hc, double* Y,
-                     const ObSide& o, double* self_partial) {
+                     const ObSide& o, double* self_partial, bool ymax) {
   const int itn = (int)std::max<int64_t>(1, (n + OB_TM - 1) / OB_TM);
   const int grid = std::min(itn, ob_sms());
   ObArgs a{};
@@ -732,9 +731,10 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   a.eb = o.eh;
   a.out = Y;
   a.self = self_partial;
+  a.ymax = ymax ? o.mx + 8 : nullptr;
 #define CASE(SV)                                                                                              \
   case SV:                                                                                                    \
-    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__nv_bfloat16*)o.HB);         \
+    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__nv_bfloat16*)o.HB, o.mx);  \
     ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
