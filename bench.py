@@ -10,8 +10,10 @@ maxit 300.  Inputs are synthetic (``workloads``).
 Prints ONE JSON line.  ``value`` = device time per solve (CUDA events on the
 solve stream, inputs already in HBM); ``e2e`` = the same through the public C
 ABI with host buffers (create + solve + factors back, pinned host memory);
-``roofline`` = the dominant kernel class, timed live by the library's CUDA-event
-profiler; ``cpu_baseline`` = the CPU FP64 oracle on the host cores (a bounded,
+``roofline`` = the dominant kernel class, timed by the library's CUDA-event
+profiler on one more solve run on one stream (the timed solves overlap the two
+bases on concurrent streams; their own figure is kept as
+``achieved_in_timed_region``); ``cpu_baseline`` = the CPU FP64 oracle on the host cores (a bounded,
 measured sample of the same workload, extrapolated with the algorithm's cost
 structure; see ``oracle_time_to_tol``).
 
@@ -451,6 +453,21 @@ def run_ours(args):
     iters = infos[-1]["iters"]
     status = infos[-1]["status_name"]
     launches = int(sum(i["kernel_launches"] for i in infos))
+    prof_timed = prof
+
+    # The timed solves run the two bases on concurrent streams (the library's default where that
+    # pays), so a kernel's event interval there includes kernels running beside it.  The roofline
+    # takes per-kernel durations from one more profiled solve of the same workload on one stream
+    # (stream_mode 1), right after the timed region; the timed region's own figure is kept beside it.
+    svs = ps.Solver(p.A, p.B, p.C1, p.C2, precision=args.precision, profile=True, stream_mode=1,
+                    cuda_stream=stream.cuda_stream)
+    svs.bicgstab(p.tol, p.maxit)
+    svs.bicgstab(p.tol, p.maxit)
+    prof = {}
+    for e in svs.profile():
+        prof[e["name"]] = {key: e[key] for key in ("launches", "ms", "bytes", "flops")}
+    torch.cuda.synchronize()
+    svs.close()
 
     # roofline of the dominant kernel class (live CUDA-event timing inside the library)
     pk = peaks()
@@ -485,14 +502,20 @@ def run_ours(args):
         roof["frac_of_traffic"] = roof["achieved"] * ratio[0] / ratio[1] / roof["peak"]
     roof["launches"] = d["launches"]
     roof["avg_launch_us"] = d["ms"] * 1e3 / max(1, d["launches"])
+    roof["timing"] = ("one profiled solve on one stream after the timed region (the timed solves run the bases on "
+                      "concurrent streams, where a kernel's event interval includes the kernels beside it)")
+    dt = prof_timed.get(dname)
+    if dt and dt["ms"]:
+        roof["achieved_in_timed_region"] = (dt["bytes"] / (dt["ms"] * 1e-3) / 1e9 if roof["unit"] == "GB/s"
+                                            else dt["flops"] / (dt["ms"] * 1e-3) / 1e12)
     hb = [prof[k] for k in ("spmm", "gram", "update") if k in prof]
     hb_bytes, hb_ms = sum(x["bytes"] for x in hb), sum(x["ms"] for x in hb)
     spmm_gram = {"gbs": hb_bytes / (hb_ms * 1e-3) / 1e9 if hb_ms else None, "frac_of_measured_hbm":
                  (hb_bytes / (hb_ms * 1e-3) / 1e9 / pk["hbm_gbs"]) if hb_ms else None,
                  "tflops_fp64": sum(x["flops"] for x in hb) / (hb_ms * 1e-3) / 1e12 if hb_ms else None}
     total_ms = sum(x["ms"] for x in prof.values())
-    breakdown = {k: {"share": round(v["ms"] / total_ms, 4), "ms_per_solve": v["ms"] / args.steps,
-                     "launches_per_solve": v["launches"] // args.steps,
+    breakdown = {k: {"share": round(v["ms"] / total_ms, 4), "ms_per_solve": v["ms"],
+                     "launches_per_solve": v["launches"],
                      "gbs": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else None,
                      "tflops": v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] else None}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}

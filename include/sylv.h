@@ -70,9 +70,10 @@ typedef struct {
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a stream owned by the handle */
   int32_t profile;     /* 1: time every kernel launch with CUDA events (see sylv_get_profile) */
   int32_t no_true_residual; /* SYLV_FP64 only: 1 skips the float64 true-residual estimate after the solve */
-  int32_t stream_mode; /* 0: auto (SYLV_MIXED runs the two bases on their own streams, ahead of the small
-                          side; SYLV_FP64 uses one stream, where FP64-bound kernels gain nothing from
-                          overlap); 1: everything on one stream (clean per-kernel profiles); 2: concurrent */
+  int32_t stream_mode; /* 0: auto (SYLV_MIXED and SYLV_FP64 block Arnoldi bases on the tensor cores run the
+                          two bases on their own streams, ahead of the small side; the CUDA-core SYLV_FP64
+                          kernels use one stream, where FP64-bound kernels gain nothing from overlap);
+                          1: everything on one stream (clean per-kernel profiles); 2: concurrent */
   int32_t small_gemm;  /* products of the small Sylvester operator, eq. 3.7, in BiCGSTAB: 0 auto (tensor
                           cores from order r = 448 on), 1 CUDA cores only (float64, or double-float in
                           SYLV_MIXED), 2 tensor cores at every order; the tensor-core form splits both

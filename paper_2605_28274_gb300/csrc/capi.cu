@@ -688,10 +688,13 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   bool stopped = false;
   TRY(ensure_streams(h));
   const int ns_ = nsides(h);
-  // concurrent bases only where they pay (measured): the mixed mode's memory-bound
-  // basis sweeps overlap the small side; FP64 kernels all compete for the FP64 pipe
+  // concurrent bases only where they pay (measured): memory-bound basis sweeps -- the mixed
+  // mode's, and the float64 Arnoldi bases on the tensor cores (517 vs 660 ms per benchmarked
+  // solve) -- leave room for the other side's and the small side's kernels; the CUDA-core
+  // float64 kernels all compete for the FP64 pipe
   const int mode = h->opt.stream_mode;
-  const bool concurrent = mode == 2 || (mode == 0 && h->mixed);
+  const bool tensor_basis = arnoldi_method(method) && h->side[0].ob.G != nullptr;
+  const bool concurrent = mode == 2 || (mode == 0 && (h->mixed || tensor_basis));
   struct RestoreBasisStreams {  // the handle keeps owning its two streams on every exit path
     sylv_handle* h;
     cudaStream_t a, b;
