@@ -505,6 +505,12 @@ void setup_qr(sylv_handle* h, int si) {
   if (sd.ob.G) sylv::launch_ob_split_basis(h->stream, h->st, sd.n, s, (const double*)V0, 0, sd.ob);
 }
 
+// Digit planes of the basis in the second BCGS2 update Y2 = Y1 - V H2.  Y1 is already orthogonal
+// to V up to rounding, so |H2| ~ eps ||Y||: the basis's top two digit planes (16 bits) leave an
+// error below 2^-17 of that correction, far under the float64 rounding of Y2 -- the pass reads
+// 4 bytes per basis element instead of 14.  The Gram products and the first update use all 7.
+constexpr int kReorthPlanes = 2;
+
 // One block Lanczos (lanczos=true) or BCGS2 block Arnoldi step on side si:
 // from blocks 0..q build block q+1 and column block q of H (eq. 3.4).
 template <typename T>
@@ -552,7 +558,8 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
       PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
            sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1, false));
       PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
-           nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr, !last));
+           nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr, !last,
+                                       last ? kReorthPlanes : 7));
       continue;
     }
     PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));

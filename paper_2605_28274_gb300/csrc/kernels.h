@@ -49,9 +49,10 @@ void launch_ob_split_basis(cudaStream_t, const DevState*, int64_t n, int s, cons
 int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Y, const ObSide&, double* partial);
 // Y -= V Hc over the first js basis columns (Hc: js x s, the layout launch_reduce_H writes),
 // with the optional per-CTA partial Y^T Y of the result and, with ymax, the column maxima of
-// the result into mx[8, 16); returns the number of CTAs.
+// the result into mx[8, 16); V enters through its leading `planes` digit planes (7: all).
+// Returns the number of CTAs.
 int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
-                     double* self_partial, bool ymax);
+                     double* self_partial, bool ymax, int planes);
 
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

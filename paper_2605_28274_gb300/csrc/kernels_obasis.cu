@@ -288,6 +288,7 @@ struct ObArgs {
   double* out;             // Gram: partials [split][m S + t]; update: Y (row-major n x S)
   double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
   unsigned long long* ymax;  // update: column maxima of |result| as IEEE bits (nullptr: none)
+  int planes;              // basis digit planes used (the leading ones; OB_P: all)
 };
 
 // GRAM: CTA (m tile, k split) writes the partial V^T Y of its rows.  Update: CTA c takes
@@ -332,9 +333,9 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
   const int npt = (nch + OB_FOLD - 1) / OB_FOLD;  // fold periods per tile
   const int NF = ntiles * npt;
   const uint32_t abytes = (uint32_t)rg * 512;  // per digit plane and chunk: the tile's row groups
-  // stage slots: a narrow tile (Gram, few basis columns) gets more of them, so that about the
-  // same number of bytes stays in flight
-  const uint32_t slot = OB_P * abytes + Sh::BBYTES;
+  // stage slots: a narrow tile (Gram, few basis columns) or fewer digit planes get more of them,
+  // so that about the same number of bytes stays in flight
+  const uint32_t slot = a.planes * abytes + Sh::BBYTES;
   const int ns = min(OB_MAXSTAGES, (int)(Sh::REGION / slot));
 
   if (warp == 0) {
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         }
         const int tile = i / nch, c = i - tile * nch;
         unsigned char* sa = base + stg * slot;
-        unsigned char* sb = sa + OB_P * abytes;
+        unsigned char* sb = sa + a.planes * abytes;
         const __nv_bfloat16* ga;
         const __nv_bfloat16* gb;
         if (GRAM) {
@@ -388,10 +389,10 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         }
         const uint32_t bar = bfull + 8 * stg;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(OB_P * abytes + Sh::BBYTES)
+                     "r"(a.planes * abytes + Sh::BBYTES)
                      : "memory");
 #pragma unroll 1
-        for (int p = 0; p < OB_P; ++p)
+        for (int p = 0; p < a.planes; ++p)
           asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                            ob_smem_u32(sa + p * abytes)),
                        "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
@@ -422,10 +423,10 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         if (ok && !ob_wait(bfull + 8 * stg, (uint32_t)(i / ns) & 1u)) ok = false;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t sa = ob_smem_u32(base + stg * slot), sb = sa + OB_P * abytes;
+        const uint32_t sa = ob_smem_u32(base + stg * slot), sb = sa + a.planes * abytes;
         const uint32_t dbase = tmem + (uint32_t)(buf * OB_P * NP);
 #pragma unroll 1
-        for (int p = 0; p < OB_P; ++p) {
+        for (int p = 0; p < a.planes; ++p) {
 #pragma unroll
           for (int ks = 0; ks < OB_KC / 16; ++ks) {
             const uint64_t da = ob_sdesc(sa + p * abytes + ks * 256);
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         constexpr int NCMAX = (OB_LMAX + 1) * S;
 #pragma unroll
         for (int cb = 0; cb < NCMAX; cb += 32) {
-          if (cb < (OB_LMAX - p + 1) * S) {
+          if (p < a.planes && cb < (OB_LMAX - p + 1) * S) {
             uint32_t r[32];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -703,6 +704,7 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
   a.out = partial;
   a.self = nullptr;
   a.ymax = nullptr;
+  a.planes = OB_P;
   const dim3 grid((unsigned)mtv, (unsigned)ks);
 #define CASE(SV)                                                                                                 \
   case SV:                                                                                                       \
@@ -715,7 +717,7 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
 }
 
 int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Hc, double* Y,
-                     const ObSide& o, double* self_partial, bool ymax) {
+                     const ObSide& o, double* self_partial, bool ymax, int planes) {
   const int itn = (int)std::max<int64_t>(1, (n + OB_TM - 1) / OB_TM);
   const int grid = std::min(itn, ob_sms());
   ObArgs a{};
@@ -732,6 +734,7 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   a.out = Y;
   a.self = self_partial;
   a.ymax = ymax ? o.mx + 8 : nullptr;
+  a.planes = std::max(1, std::min(OB_P, planes));
 #define CASE(SV)                                                                                              \
   case SV:                                                                                                    \
     ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__nv_bfloat16*)o.HB, o.mx);  \
