@@ -28,8 +28,9 @@
 // kernel loads one chunk of a digit plane with one 1-D bulk copy (cp.async.bulk):
 //   Gram layout   (tile rows = basis columns m, k = basis rows i): tile (i / 32, m / 128)
 //   update layout (tile rows = basis rows i, k = basis columns m): tile (m / 32, i / 128)
-// Each kernel reads 14 bytes per basis element instead of 8, and is bound by memory
-// bandwidth instead of the FP64 pipe.
+// Each kernel reads 14 bytes per basis element instead of 8 (the second update of a step, whose
+// coefficients are at rounding level, only the two leading planes: 4 bytes), and is bound by
+// memory bandwidth instead of the FP64 pipe.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
