@@ -258,6 +258,15 @@ int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, in
 int sylv_apply(sylv_handle* h, int32_t side, const double* X, double* Y, int64_t k);
 
 /*
+ * Sets the host wait limit of the handle's later solves (sylv_options.timeout_s;
+ * 0: 3600 s).  A solve that runs past it returns SYLV_ETIMEOUT without waiting
+ * for the kernels it enqueued; they finish on the device, and every later call
+ * on the handle is ordered after them, so the handle stays usable.
+ * Errors: SYLV_EINVAL (NULL handle, negative or NaN limit).  Not in the paper.
+ */
+int sylv_set_timeout(sylv_handle* h, double timeout_s);
+
+/*
  * Kernel timing of the last solve, one entry per kernel class (only with
  * sylv_options.profile = 1; otherwise *count = 0).  Writes min(cap, count)
  * entries to out (may be NULL to query count).
@@ -277,6 +286,9 @@ int sylv_get_profile(sylv_handle* h, sylv_kernel_stat* out, int32_t cap, int32_t
  * no counterpart; this is a library facility.
  *   n, nnz, row_ptr, col_idx, val   A (n x n) in CSR form, all DEVICE pointers
  *   X, Y                            DEVICE pointers, n x k column-major; 1 <= k <= 8
+ * Every pointer must be device (or managed) memory of the CURRENT device; a host
+ * pointer or another device's memory returns SYLV_EINVAL (checked with
+ * cudaPointerGetAttributes, which allocates nothing).
  *   cuda_stream                     cudaStream_t (NULL: the legacy default stream)
  * Float64.  Asynchronous: returns once the kernels are enqueued on cuda_stream;
  * launch errors are returned, errors inside the kernels surface at the caller's
@@ -287,10 +299,14 @@ int sylv_get_profile(sylv_handle* h, sylv_kernel_stat* out, int32_t cap, int32_t
  *  - the first call on each device looks up the array's device address with
  *    cudaGetSymbolAddress (with that device current); make that first call
  *    before any stream capture;
+ *  - that address belongs to the device's primary context: after
+ *    cudaDeviceReset do not call this entry point again in the same process;
  *  - every call, on every stream, shares the one array: calls that can overlap
  *    on the GPU (different streams without ordering) race and corrupt each
  *    other's results; order them on one stream or with events.
- * Errors: SYLV_EINVAL (arguments, size limit), SYLV_ECUDA.
+ * Errors: SYLV_EINVAL (arguments, size limit, pointer not on the current
+ * device), SYLV_ECUDA (a launch failed, or a CUDA error left pending by earlier
+ * work, which is reported and left set rather than cleared).
  */
 int sylv_spmm_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
                       const double* X, double* Y, int64_t k, void* cuda_stream);

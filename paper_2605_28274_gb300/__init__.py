@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr",
            "sylv_gpbicg", "sylv_compress", "sylv_get_factors",
-           "sylv_get_history", "sylv_get_hessenberg", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
+           "sylv_get_history", "sylv_get_hessenberg", "sylv_set_timeout", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
            "sylv_create_batch", "sylv_batch_instance", "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
 
@@ -100,6 +100,8 @@ def load(path: Optional[str] = None):
     lib.sylv_get_history.restype = ctypes.c_int
     lib.sylv_get_hessenberg.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp, ctypes.c_int64, P(ctypes.c_int32)]
     lib.sylv_get_hessenberg.restype = ctypes.c_int
+    lib.sylv_set_timeout.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.sylv_set_timeout.restype = ctypes.c_int
     lib.sylv_apply.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp, dp, ctypes.c_int64]
     lib.sylv_apply.restype = ctypes.c_int
     lib.sylv_get_profile.argtypes = [ctypes.c_void_p, P(sylv_kernel_stat), ctypes.c_int32, P(ctypes.c_int32)]
@@ -270,6 +272,12 @@ def sylv_get_hessenberg(h, side: int, s: int) -> np.ndarray:
     return H
 
 
+def sylv_set_timeout(h, timeout_s: float) -> None:
+    rc = load().sylv_set_timeout(h, float(timeout_s))
+    if rc != SYLV_OK:
+        raise SylvError(rc, "sylv_set_timeout")
+
+
 def sylv_apply(h, side: int, X: np.ndarray) -> np.ndarray:
     Xf = np.asfortranarray(X, dtype=np.float64)
     Y = np.empty_like(Xf, order="F")
@@ -433,6 +441,9 @@ class Solver:
 
     def hessenberg(self, side: int) -> np.ndarray:
         return sylv_get_hessenberg(self.h, side, self.s)
+
+    def set_timeout(self, timeout_s: float) -> None:
+        sylv_set_timeout(self.h, timeout_s)
 
     def apply(self, side: int, X: np.ndarray) -> np.ndarray:
         return sylv_apply(self.h, side, X)

@@ -702,10 +702,18 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   const int mode = h->opt.stream_mode;
   const bool tensor_basis = arnoldi_method(method) && h->side[0].ob.G != nullptr;
   const bool concurrent = mode == 2 || (mode == 0 && (h->mixed || tensor_basis));
-  struct RestoreBasisStreams {  // the handle keeps owning its two streams on every exit path
+  // On every exit path (an early return after SYLV_ETIMEOUT or a CUDA error included) the main
+  // stream waits for the basis streams, so that the next call on the handle, which starts on the
+  // main stream, is ordered after every kernel this solve enqueued; the handle keeps owning its
+  // two streams.
+  struct RestoreBasisStreams {
     sylv_handle* h;
     cudaStream_t a, b;
     ~RestoreBasisStreams() {
+      for (int i = 0; i < 2; ++i)
+        if (h->sbas[i] != nullptr && h->sbas[i] != h->stream && h->ev_bas[i][0] != nullptr &&
+            cudaEventRecord(h->ev_bas[i][0], h->sbas[i]) == cudaSuccess)
+          cudaStreamWaitEvent(h->stream, h->ev_bas[i][0], 0);
       h->sbas[0] = a;
       h->sbas[1] = b;
     }
@@ -1928,6 +1936,14 @@ int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, in
                          cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }
+  return SYLV_OK;
+}
+
+int sylv_set_timeout(sylv_handle* h, double timeout_s) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (!(timeout_s >= 0.0)) return fail(SYLV_EINVAL, "timeout_s must be >= 0");
+  h->opt.timeout_s = timeout_s;
+  for (sylv_handle* b : h->batch) b->opt.timeout_s = timeout_s;
   return SYLV_OK;
 }
 

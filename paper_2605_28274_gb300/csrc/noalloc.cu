@@ -14,7 +14,8 @@
 // same for Y, 16 MiB in total) until the process exits.  In host code the
 // array's name is only a host-side stand-in; its device address is obtained
 // once per device with cudaGetSymbolAddress (with that device current) and
-// passed to the kernels.
+// passed to the kernels.  That address belongs to the device's primary context: after
+// cudaDeviceReset the process must not call this entry point again on that device.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -61,6 +62,36 @@ int scratch_address(double** out) {
   return SYLV_OK;
 }
 
+// Every pointer must be device (or managed) memory of the current device: the staging array is
+// the current device's, and a kernel given another device's or a host pointer would fault.
+// cudaPointerGetAttributes allocates nothing.
+int check_device_pointers(const int32_t* row_ptr, const int32_t* col_idx, const double* val, const double* X,
+                          const double* Y, int64_t nnz) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    sylv::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    return SYLV_ECUDA;
+  }
+  const void* ptrs[5] = {row_ptr, X, Y, nnz > 0 ? col_idx : nullptr, nnz > 0 ? val : nullptr};
+  for (const void* p : ptrs) {
+    if (p == nullptr) continue;
+    cudaPointerAttributes at{};
+    e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // this call's own error: cleared
+      sylv::set_last_error(std::string("sylv_spmm_noalloc: cudaPointerGetAttributes: ") + cudaGetErrorString(e));
+      return SYLV_EINVAL;
+    }
+    const bool on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (!on_device || (at.type == cudaMemoryTypeDevice && at.device != dev)) {
+      sylv::set_last_error("sylv_spmm_noalloc: every pointer must be device memory of the current device");
+      return SYLV_EINVAL;
+    }
+  }
+  return SYLV_OK;
+}
+
 }  // namespace
 
 extern "C" int sylv_spmm_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
@@ -78,8 +109,18 @@ extern "C" int sylv_spmm_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr,
                     std::to_string((int64_t)SYLV_NOALLOC_MAX_ELEMS) + "; use sylv_apply");
     return SYLV_EINVAL;
   }
+  // An error left pending by the caller's earlier CUDA work is reported, not cleared: after the
+  // launches below, cudaGetLastError then returns this call's own launch errors only.
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    sylv::set_last_error(std::string("sylv_spmm_noalloc: an earlier CUDA error is pending (left set): ") +
+                         cudaGetErrorString(e));
+    return SYLV_ECUDA;
+  }
+  int rc = check_device_pointers(row_ptr, col_idx, val, X, Y, nnz);
+  if (rc != SYLV_OK) return rc;
   double* scratch = nullptr;
-  int rc = scratch_address(&scratch);
+  rc = scratch_address(&scratch);
   if (rc != SYLV_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double* xb = scratch;
@@ -87,7 +128,7 @@ extern "C" int sylv_spmm_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr,
   sylv::launch_pack<double>(st, n, (int)k, X, xb);
   sylv::launch_spmm<double>(st, nullptr, n, (int)k, row_ptr, col_idx, val, xb, yb, nullptr, nullptr, 0);
   sylv::launch_unpack<double>(st, n, (int)k, 1, yb, n * k, Y);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
     sylv::set_last_error(std::string("sylv_spmm_noalloc launch: ") + cudaGetErrorString(e));
     return SYLV_ECUDA;

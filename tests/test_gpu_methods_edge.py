@@ -57,3 +57,24 @@ def test_exhausted_block_krylov_space_reaches_exact(method):
     assert info["status"] == ps.SYLV_OK, info
     X = exact.kron_solve(A.to_dense(), B.to_dense(), C1 @ C2.T)
     assert rel(V @ Xh @ W.T, X) < 1e-9
+
+
+def test_host_timeout_returns_etimeout_and_handle_stays_usable():
+    # The host's wall-clock limit (sylv_options.timeout_s, SYLV_ETIMEOUT): a solve of about a
+    # hundred milliseconds under a 0.1 ms limit gives up at its first status poll and returns
+    # without waiting for the kernels it enqueued.  The same handle, with the limit raised, then
+    # solves again and matches the oracle.
+    from oracle import factorized as fz
+
+    A, B = wl.convdiff_3d(40, 1), wl.convdiff_3d(30, 2)
+    C1, C2 = wl.rhs(A.nrows, B.nrows, 4, 0)
+    with ps.Solver(A, B, C1, C2, timeout_s=1e-4) as sv:
+        info = sv.bicgstab(0.0, 80)
+        assert info["status"] == ps.SYLV_ETIMEOUT, info
+        assert "timeout" in ps.last_error()
+        sv.set_timeout(600.0)
+        info = sv.bicgstab(0.0, 3)
+        assert info["status"] == ps.SYLV_ENOTCONV and info["iters"] == 3, info
+        V, Xh, W = sv.factors()
+    ref = fz.factorized_bicgstab(A.to_scipy(), B.to_scipy(), C1, C2, 0.0, 3)
+    assert rel(V @ Xh @ W.T, ref.X()) < 1e-10

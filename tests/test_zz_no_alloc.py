@@ -8,7 +8,9 @@ Y = A X with device pointers only, staging through a fixed array compiled into
 the library instead of per-call buffers.  This test calls it through the C ABI
 twice in a row and checks each result against the existing entry point
 sylv_apply (which allocates its staging), within the FP64 SpMM tolerance the
-other parity tests use, and checks that oversized requests are refused.
+other parity tests use; checks that a call leaves the device's free memory
+unchanged (after the first call, which may load the library's device image);
+and checks that oversized requests and host pointers are refused.
 """
 import numpy as np
 import pytest
@@ -43,10 +45,14 @@ def test_spmm_noalloc_matches_sylv_apply_on_two_calls():
             Xd = torch.from_numpy(np.ascontiguousarray(X.T)).to(dev)  # (k, n) rows = n x k column-major
             Yd = torch.full((k, n), float("nan"), dtype=torch.float64, device=dev)
             torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info(dev)[0]
             rc = ps.sylv_spmm_noalloc(n, A.nnz, rp.data_ptr(), ci.data_ptr(), val.data_ptr(), Xd.data_ptr(),
                                       Yd.data_ptr(), k, stream.cuda_stream)
             assert rc == ps.SYLV_OK, ps.last_error()
             stream.synchronize()
+            if call == 1:  # the array is resident after the first call: nothing more is taken
+                free_after = torch.cuda.mem_get_info(dev)[0]
+                assert free_after == free_before, (free_before, free_after)
             Y = Yd.cpu().numpy().T
             Y_ref = sv.apply(0, X)  # existing entry point
             assert np.all(np.isfinite(Y))
@@ -66,3 +72,20 @@ def test_spmm_noalloc_rejects_sizes_beyond_its_staging():
                               dummy_d.data_ptr(), k, 0)
     assert rc == ps.SYLV_EINVAL
     assert "staging" in ps.last_error()
+
+
+def test_spmm_noalloc_rejects_host_pointers():
+    import torch
+
+    dev = torch.device("cuda", 0)
+    n, k = 64, 2
+    A = wl.random_sparse(n, 3, 1)
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col_idx).to(dev)
+    val = torch.from_numpy(A.val).to(dev)
+    Xh = np.zeros((k, n))  # host memory
+    Yd = torch.zeros((k, n), dtype=torch.float64, device=dev)
+    rc = ps.sylv_spmm_noalloc(n, A.nnz, rp.data_ptr(), ci.data_ptr(), val.data_ptr(), Xh.ctypes.data,
+                              Yd.data_ptr(), k, 0)
+    assert rc == ps.SYLV_EINVAL
+    assert "current device" in ps.last_error()
