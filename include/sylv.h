@@ -31,7 +31,8 @@ extern "C" {
 #endif
 
 typedef enum {
-  SYLV_OK = 0,         /* converged: ||R^_k|| <= tol ||R^_0|| (Algorithms 4.1/4.2 test) */
+  SYLV_OK = 0,         /* converged: ||R^_k|| <= tol ||R^_0|| (Algorithms 4.1/4.2 test) and, with the
+                          true-residual certificate on (the default), true_rel_bound <= tol */
   SYLV_EINVAL = 1,     /* bad argument: shape, NULL, malformed CSR, s < 1, tol < 0 ... */
   SYLV_ENOMEM = 2,     /* device allocation failed */
   SYLV_ENOTCONV = 3,   /* maxit reached; the factors hold the last iterate */
@@ -64,12 +65,13 @@ typedef struct {
   int32_t precision;   /* sylv_precision */
   int32_t lyapunov;    /* 1: B = A^T and C2 = C1 (Sec. 4.3); pass B = NULL, C2 = NULL */
   int32_t poll_every;  /* iterations enqueued between host polls of the device status (0: 8) */
-  int32_t refine_max;  /* SYLV_MIXED: maximum outer refinement rounds (0: 8) */
+  int32_t refine_max;  /* SYLV_MIXED: maximum outer refinement rounds (0: 12) */
   double deflate_tol;  /* block Krylov exhaustion threshold delta (0: 1e-12 FP64, 1e-6 mixed) */
   double timeout_s;    /* host wait limit per solve (0: 3600 s) */
   void* cuda_stream;   /* cudaStream_t to run on, or NULL for a stream owned by the handle */
   int32_t profile;     /* 1: time every kernel launch with CUDA events (see sylv_get_profile) */
-  int32_t no_true_residual; /* SYLV_FP64 only: 1 skips the float64 true-residual estimate after the solve */
+  int32_t no_true_residual; /* SYLV_FP64 only: 1 skips the float64 true-residual certificate after the
+                               solve; the stop is then the test of Algorithms 4.1/4.2 alone */
   int32_t stream_mode; /* 0: auto (SYLV_MIXED and SYLV_FP64 block Arnoldi bases on the tensor cores run the
                           two bases on their own streams, ahead of the small side; the CUDA-core SYLV_FP64
                           kernels use one stream, where FP64-bound kernels gain nothing from overlap);
@@ -85,6 +87,10 @@ typedef struct {
                           as seven BF16 planes of 8-bit digits in two layouts (28 bytes per basis element
                           besides the 8 of float64) and splits the other operand the same way; the products
                           are exact sums of digit products, rounded once to float64 (Ozaki scheme) */
+  double stop_margin;  /* with the true-residual certificate on (SYLV_FP64 by default): the recurrence test of
+                          Algorithms 4.1/4.2 stops at ||R^_k|| <= stop_margin * tol * ||R^_0|| (0: 0.4), so
+                          that the certificate (sylv_info.true_rel_bound <= tol) holds at the first check.
+                          1.0 gives the printed test.  SYLV_MIXED inner solves are not affected */
 } sylv_options;
 
 typedef struct {
@@ -93,11 +99,17 @@ typedef struct {
   int64_t matvecs;      /* sparse block products A*V_j (equal count for B^T*W_j), all rounds */
   int64_t width;        /* r: columns of V and W returned; X^ is r x r */
   double rel_res;       /* ||R^_k|| / ||R^_0||, the monitored residual of Algorithms 4.1/4.2 */
-  double true_rel_res;  /* ||C1 C2^T - A X - X B||_F / ||C1 C2^T||_F in float64, or -1 if not computed */
+  double true_rel_res;  /* estimate of ||C1 C2^T - A X - X B||_F / ||C1 C2^T||_F in float64 (unbiased in
+                           its square, from Gaussian probes of the residual), or -1 if not computed */
   double solve_ms;      /* wall time of the solve call on the host */
   int32_t refinements;  /* SYLV_MIXED: outer refinement rounds used */
   int32_t reserved;
   int64_t kernel_launches; /* CUDA kernels this call enqueued (no-ops after a stop included) */
+  double true_rel_bound;   /* upper bound on the true relative residual that holds with probability
+                              >= 1 - 1e-4 over the probes, whatever the residual (or -1 if not computed).
+                              With the certificate on, SYLV_OK means true_rel_bound <= tol; a solve whose
+                              recurrence met its test but whose bound did not returns SYLV_ENOTCONV
+                              (SYLV_MIXED first runs more refinement rounds) */
 } sylv_info;
 
 /* Per-kernel-class totals of the last solve (sylv_options.profile = 1).
@@ -256,6 +268,21 @@ int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, in
  * (rows x k), 1 <= k <= 8, host memory.  Runs in the handle's precision.
  */
 int sylv_apply(sylv_handle* h, int32_t side, const double* X, double* Y, int64_t k);
+
+/*
+ * The factored Sylvester operator of eq. 3.7 on the bases of the last solve:
+ *   out = [H Z, 0] + [Z G^T; 0]
+ * with H = H_{k+1,k}, G = G_{k+1,k} ((r + s) x r leading parts of the Hessenberg matrices of
+ * eq. 3.4, G = H for the Lyapunov case) and Z r x r; the same device path the solver uses (the
+ * BiCGSTAB-type methods' dense operator: tensor cores from order 448 on unless
+ * sylv_options.small_gemm says otherwise; double-float products in SYLV_MIXED).
+ *   r    a positive multiple of s, at most (nblocks - 1) s of the last solve
+ *   Z    r x r column-major (host);  out  (r + s) x (r + s) column-major (host)
+ * The call uses the handle's small-matrix work space (the factors of the last solve are kept).
+ * Errors: SYLV_EINVAL (r, NULL pointers, batched handle), SYLV_ESTATE (no solve yet),
+ * SYLV_ENONFINITE, SYLV_ETIMEOUT, SYLV_ECUDA.
+ */
+int sylv_small_operator(sylv_handle* h, int64_t r, const double* Z, double* out);
 
 /*
  * Sets the host wait limit of the handle's later solves (sylv_options.timeout_s;

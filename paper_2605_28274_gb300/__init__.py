@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "converged", 1: "einval", 2: "enomem", 3: "maxit", 4: "breakd
 # every symbol include/sylv.h declares
 EXPORTS = ["sylv_default_options", "sylv_create", "sylv_cg", "sylv_bicgstab", "sylv_cgs", "sylv_cr",
            "sylv_gpbicg", "sylv_compress", "sylv_get_factors",
-           "sylv_get_history", "sylv_get_hessenberg", "sylv_set_timeout", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
+           "sylv_get_history", "sylv_get_hessenberg", "sylv_small_operator", "sylv_set_timeout", "sylv_apply", "sylv_get_profile", "sylv_spmm_noalloc",
            "sylv_create_batch", "sylv_batch_instance", "sylv_strerror", "sylv_last_error", "sylv_destroy"]
 
 
@@ -44,7 +44,7 @@ class sylv_options(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("deflate_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("no_true_residual", ctypes.c_int32), ("stream_mode", ctypes.c_int32), ("small_gemm", ctypes.c_int32),
-                ("basis_gemm", ctypes.c_int32)]
+                ("basis_gemm", ctypes.c_int32), ("stop_margin", ctypes.c_double)]
 
 
 class sylv_kernel_stat(ctypes.Structure):
@@ -56,7 +56,7 @@ class sylv_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("matvecs", ctypes.c_int64),
                 ("width", ctypes.c_int64), ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("refinements", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("true_rel_bound", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -100,6 +100,8 @@ def load(path: Optional[str] = None):
     lib.sylv_get_history.restype = ctypes.c_int
     lib.sylv_get_hessenberg.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp, ctypes.c_int64, P(ctypes.c_int32)]
     lib.sylv_get_hessenberg.restype = ctypes.c_int
+    lib.sylv_small_operator.argtypes = [ctypes.c_void_p, ctypes.c_int64, dp, dp]
+    lib.sylv_small_operator.restype = ctypes.c_int
     lib.sylv_set_timeout.argtypes = [ctypes.c_void_p, ctypes.c_double]
     lib.sylv_set_timeout.restype = ctypes.c_int
     lib.sylv_apply.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp, dp, ctypes.c_int64]
@@ -272,6 +274,17 @@ def sylv_get_hessenberg(h, side: int, s: int) -> np.ndarray:
     return H
 
 
+def sylv_small_operator(h, Z: np.ndarray, s: int) -> np.ndarray:
+    """[H Z, 0] + [Z G^T; 0] (eq. 3.7) with the last solve's H, G; Z is r x r."""
+    r = Z.shape[0]
+    Zf = np.asfortranarray(Z, dtype=np.float64)
+    out = np.zeros((r + s, r + s), order="F")
+    rc = load().sylv_small_operator(h, r, _dptr(Zf), _dptr(out))
+    if rc != SYLV_OK:
+        raise SylvError(rc, "sylv_small_operator")
+    return np.ascontiguousarray(out)
+
+
 def sylv_set_timeout(h, timeout_s: float) -> None:
     rc = load().sylv_set_timeout(h, float(timeout_s))
     if rc != SYLV_OK:
@@ -347,9 +360,10 @@ class BatchSolver:
     batched factorized CG: ``BatchSolver([A_0, ...], [C_0, ...]).cg(tol, maxit)``."""
 
     def __init__(self, As, C1s, poll_every: int = 0, cuda_stream: int = 0, timeout_s: float = 0.0,
-                 no_true_residual: bool = False):
+                 no_true_residual: bool = False, stop_margin: float = 0.0):
         o = sylv_default_options()
         o.lyapunov = 1
+        o.stop_margin = stop_margin
         if poll_every:
             o.poll_every = poll_every
         o.cuda_stream = cuda_stream or None
@@ -394,8 +408,11 @@ class Solver:
 
     def __init__(self, A, B, C1, C2, precision: str = "fp64", lyapunov: bool = False, poll_every: int = 0,
                  deflate_tol: float = 0.0, cuda_stream: int = 0, timeout_s: float = 0.0, refine_max: int = 0,
-                 profile: bool = False, stream_mode: int = 0, small_gemm: int = 0, basis_gemm: int = 0):
+                 profile: bool = False, stream_mode: int = 0, small_gemm: int = 0, basis_gemm: int = 0,
+                 no_true_residual: bool = False, stop_margin: float = 0.0):
         o = sylv_default_options()
+        o.no_true_residual = 1 if no_true_residual else 0
+        o.stop_margin = stop_margin
         o.precision = SYLV_MIXED if precision == "mixed" else SYLV_FP64
         o.lyapunov = 1 if lyapunov else 0
         if poll_every:
@@ -441,6 +458,9 @@ class Solver:
 
     def hessenberg(self, side: int) -> np.ndarray:
         return sylv_get_hessenberg(self.h, side, self.s)
+
+    def small_operator(self, Z: np.ndarray) -> np.ndarray:
+        return sylv_small_operator(self.h, Z, self.s)
 
     def set_timeout(self, timeout_s: float) -> None:
         sylv_set_timeout(self.h, timeout_s)

@@ -174,7 +174,8 @@ struct sylv_handle {
   std::vector<cudaStream_t> pool;  // streams for the per-instance true-residual sketches
   double tune_ms = 0.0;
   cudaGraphExec_t graph = nullptr;
-  double true_rel = -1.0;
+  double true_rel = -1.0;    // estimate of the float64 true relative residual
+  double true_bound = -1.0;  // its certified upper bound (probability >= 1 - kCertDelta)
   int refinements = 0;
   int64_t total_iters = 0, total_width = 0;
 };
@@ -881,6 +882,7 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     info->width = h->width;
     info->rel_res = ds.r0 > 0 ? ds.rnorm / ds.r0 : 0.0;
     info->true_rel_res = -1.0;
+    info->true_rel_bound = -1.0;
     info->solve_ms = (now_s() - t0) * 1e3;
     info->kernel_launches = h->launches;
   }
@@ -893,10 +895,40 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
 // blocks only, with float64 accumulation:
 //   R Om   = C1 (C2^T Om) - A (X Om) - X (B Om)
 //   R^T Q  = C2 (C1^T Q)  - X^T (A^T Q) - B^T (X^T Q)
-// A rank-8 randomised range finder with one power iteration gives R ~ Q Z^T with Q
-// orthonormal; ||R||_F^2 = ||Z||_F^2 + ||(I - Q Q^T) R||_F^2, the second term from a
-// second Gaussian probe block (unbiased).  Q, Z are also the right-hand side factors of
-// the next refinement round.
+// SYLV_MIXED: a rank-8 randomised range finder with one power iteration gives R ~ Q Z^T with
+// Q orthonormal (Q, Z are the right-hand side factors of the next refinement round), and
+// ||R||_F^2 = ||Z||_F^2 + ||T||_F^2 with T = (I - Q Q^T) R exactly.  SYLV_FP64: T = R.
+//
+// Certificate.  A Gaussian block Om (m x k, k = SKT, independent of Q) gives
+// ||T Om||_F^2 = sum_i sigma_i(T)^2 X_i with X_i i.i.d. chi-square(k), so ||T Om||^2 / k is
+// unbiased for ||T||^2, and for any T and 0 < q < 1 (Chernoff: E exp(-t sum w_i X_i) =
+// prod (1 + 2 t w_i)^{-k/2} <= (1 + 2 t sum w_i)^{-k/2})
+//   P( ||T Om||^2 <= q k ||T||^2 ) <= (q e^{1-q})^{k/2}.
+// With q chosen so that the right side is kCertDelta, the bound
+//   ||R||^2 <= ||Z||^2 + ||T Om||^2 / (q k)
+// holds with probability at least 1 - kCertDelta over Om, whatever the residual.
+
+constexpr int SKK = 8;  // columns of the sketch blocks
+constexpr int SKT = 32;  // columns of the tail probe: SKT / SKK blocks
+constexpr double kCertDelta = 1e-4;  // probability that the certified bound fails
+
+// The q of the certificate: the root in (0, 1) of (q e^{1-q})^{SKT/2} = kCertDelta (the left
+// side increases on (0, 1)); bisection.
+double cert_q() {
+  static const double q = [] {
+    const double target = std::pow(kCertDelta, 2.0 / SKT);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid * std::exp(1.0 - mid) < target)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    return lo;  // the lower end: the bound stays on the safe side
+  }();
+  return q;
+}
 
 double* sk_buf(sylv_handle* h, size_t idx, size_t bytes, int* rc) {
   if (h->sk.size() <= idx) h->sk.resize(idx + 1, {nullptr, 0});
@@ -940,7 +972,7 @@ int prepare_residual_ops(sylv_handle* h, const sylv_csr* A, const sylv_csr* B) {
   sylv::launch_pack<double>(h->stream, n, s, h->side[0].C, h->C1rm);
   sylv::launch_pack<double>(h->stream, m, s, h->lyap ? h->side[0].C : h->side[1].C, h->C2rm);
   // Gaussian probes: SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller, fixed seed
-  std::vector<double> om((size_t)m * 16);
+  std::vector<double> om((size_t)m * (SKK + SKT));  // range block, then the tail probe blocks
   uint64_t state = 0x5eedc0de12345678ull;
   auto next = [&state]() {
     uint64_t z = (state += 0x9E3779B97F4A7C15ull);
@@ -957,7 +989,7 @@ int prepare_residual_ops(sylv_handle* h, const sylv_csr* A, const sylv_csr* B) {
   TRY(alloc_fixed(h, &h->Om, om.size()));
   CU(cudaMemcpyAsync(h->Om, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   TRY(alloc_fixed(h, &h->st_sk, 1));
-  CU(cudaMallocHost(&h->sk_host, 4 * sizeof(double) + sizeof(DevState)));
+  CU(cudaMallocHost(&h->sk_host, 8 * sizeof(double) + sizeof(DevState)));
   CU(cudaStreamSynchronize(h->stream));
   return SYLV_OK;
 }
@@ -983,7 +1015,7 @@ std::vector<RoundView> round_views(const sylv_handle* h) {
   return out;
 }
 
-constexpr int SKK = 8;  // columns of the sketch blocks
+
 
 // Yout (rows x k) = X Min (trans = false; Min is m x k) or X^T Min (trans = true; Min is n x k).
 template <typename T>
@@ -1111,25 +1143,26 @@ void qr8_impl(sylv_handle* h, int64_t n, double* Y, double* Rout) {
   sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, nullptr);
 }
 
-// Enqueues the ||R||_F estimate on h->stream; leaves Q (n x 8, buffer 11) and Z
-// (m x 8, buffer 12) with R ~ Q Z^T.  sketch_finish waits and reads the result.
+// Enqueues the ||R||_F estimate and its certified bound on h->stream; in SYLV_MIXED also leaves
+// Q (n x 8, buffer 11) and Z (m x 8, buffer 12) with R ~ Q Z^T.  sketch_finish waits and reads
+// the result.  Host sums: [0] ||Z||^2, [1] ||T Om||^2, [2] ||C1 C2^T||^2, [3] ||R Om||^2.
 template <typename T>
 int sketch_enqueue(sylv_handle* h) {
   int rc = SYLV_OK;
   const int s = (int)h->s;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
-  double* Q = sk_buf(h, 11, (size_t)n * SKK * sizeof(double), &rc);
-  double* Z = sk_buf(h, 12, (size_t)m * SKK * sizeof(double), &rc);
-  double* Y3 = sk_buf(h, 13, (size_t)n * SKK * sizeof(double), &rc);
-  double* Rk = sk_buf(h, 14, 256 * sizeof(double), &rc);
+  double* Y3 = sk_buf(h, 13, (size_t)n * SKT * sizeof(double), &rc);
   double* sums = sk_buf(h, 15, 8 * sizeof(double), &rc);
   double* part = sk_buf(h, 16, (size_t)256 * sizeof(double) + 64, &rc);
-  double* P = sk_buf(h, 17, 64 * sizeof(double), &rc);
   double* part2 = sk_buf(h, 18, (size_t)sylv::tsg_partial_elems(64, 16) * sizeof(double), &rc);
+  // R times the tail probe blocks: persistent across the refinement rounds of one solve and
+  // updated with the newest correction only
+  double* RO2 = sk_buf(h, 23, (size_t)n * SKT * sizeof(double), &rc);
   if (rc) return rc;
   unsigned int* ticket = (unsigned int*)(part + 256);
   CU(cudaMemsetAsync(h->st_sk, 0, sizeof(DevState), h->stream));
   CU(cudaMemsetAsync(ticket, 0, 16, h->stream));
+  CU(cudaMemsetAsync(sums, 0, 8 * sizeof(double), h->stream));
   if (h->cnorm < 0) {
     // ||C1 C2^T||_F^2 = tr((C1^T C1)(C2^T C2))
     double* G1 = sk_buf(h, 19, 128 * sizeof(double), &rc);
@@ -1138,48 +1171,59 @@ int sketch_enqueue(sylv_handle* h) {
     sylv::launch_tsg<double>(h->stream, m, h->C2rm, m * s, s, 1, h->C2rm, s, part2, 0, G1 + 64);
     sylv::launch_trace_prod(h->stream, s, G1, G1 + 64, sums + 2);
   }
-  const double* Om1 = h->Om;
-  const double* Om2 = h->Om + m * SKK;
-  // R Om1 and R Om2 persist across the refinement rounds of one solve and are updated
-  // with the newest correction only
-  double* RO1 = sk_buf(h, 22, (size_t)n * SKK * sizeof(double), &rc);
-  double* RO2 = sk_buf(h, 23, (size_t)n * SKK * sizeof(double), &rc);
-  if (rc) return rc;
   const size_t newest = h->subs.size();  // round index of the newest correction (0: none)
-  TRY(sketch_R<T>(h, Om1, RO1, newest));
-  TRY(sketch_R<T>(h, Om2, RO2, newest));
-  CU(cudaMemcpyAsync(Q, RO1, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  qr8(h, n, Q, Rk);
-  TRY(sketch_Rt<T>(h, Q, Z));   // Z1 = R^T Q1
-  TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1 (a rank-8 range without it is too
-  qr8(h, n, Q, Rk);             // poor for the refinement rounds to converge)
-  TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
-  CU(cudaMemcpyAsync(Y3, RO2, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));  // tail probe
-  sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Y3, SKK, part2, 0, P);
-  sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Y3);
-  sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
-  sylv::launch_sumsq(h->stream, n * SKK, Y3, part, ticket + 1, sums + 1);
-  CU(cudaMemcpyAsync(h->sk_host, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaMemcpyAsync(h->sk_host + 4, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  for (int b = 0; b < SKT / SKK; ++b)
+    TRY(sketch_R<T>(h, h->Om + (size_t)(1 + b) * m * SKK, RO2 + (size_t)b * n * SKK, newest));
+  sylv::launch_sumsq(h->stream, n * SKT, RO2, part, ticket + 2, sums + 3);  // ||R Om||^2
+  if (h->mixed) {
+    double* Q = sk_buf(h, 11, (size_t)n * SKK * sizeof(double), &rc);
+    double* Z = sk_buf(h, 12, (size_t)m * SKK * sizeof(double), &rc);
+    double* Rk = sk_buf(h, 14, 256 * sizeof(double), &rc);
+    double* P = sk_buf(h, 17, 64 * sizeof(double), &rc);
+    double* RO1 = sk_buf(h, 22, (size_t)n * SKK * sizeof(double), &rc);
+    if (rc) return rc;
+    TRY(sketch_R<T>(h, h->Om, RO1, newest));
+    CU(cudaMemcpyAsync(Q, RO1, (size_t)n * SKK * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    qr8(h, n, Q, Rk);
+    TRY(sketch_Rt<T>(h, Q, Z));   // Z1 = R^T Q1
+    TRY(sketch_R<T>(h, Z, Q));    // power step: Y = R Z1 (a rank-8 range without it is too
+    qr8(h, n, Q, Rk);             // poor for the refinement rounds to converge)
+    TRY(sketch_Rt<T>(h, Q, Z));   // Z = R^T Q
+    // tail probe with the range projected out: T Om = (I - Q Q^T) R Om
+    CU(cudaMemcpyAsync(Y3, RO2, (size_t)n * SKT * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    for (int b = 0; b < SKT / SKK; ++b) {
+      double* Yb = Y3 + (size_t)b * n * SKK;
+      sylv::launch_tsg<double>(h->stream, n, Q, n * SKK, SKK, 1, Yb, SKK, part2, 0, P);
+      sylv::launch_tsu<double>(h->stream, n, Q, n * SKK, SKK, 1, P, SKK, -1.0, 1.0, Yb);
+    }
+    sylv::launch_sumsq(h->stream, m * SKK, Z, part, ticket, sums);
+    sylv::launch_sumsq(h->stream, n * SKT, Y3, part, ticket + 1, sums + 1);
+  }
+  CU(cudaMemcpyAsync(h->sk_host, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(h->sk_host + 8, h->st_sk, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   return SYLV_OK;
 }
 
-int sketch_finish(sylv_handle* h, double* est, bool* ok) {
+// Waits for sketch_enqueue and returns ||R||_F's estimate and certified upper bound.
+int sketch_finish(sylv_handle* h, double* est, double* bound, bool* ok) {
   CU(cudaStreamSynchronize(h->stream));
   const double* hs = h->sk_host;
   DevState dst;
-  std::memcpy(&dst, h->sk_host + 4, sizeof(DevState));
+  std::memcpy(&dst, h->sk_host + 8, sizeof(DevState));
   if (h->cnorm < 0) h->cnorm = std::sqrt(std::max(0.0, hs[2]));
-  *ok = dst.status == sylv::ST_RUNNING;
-  // with a rank-deficient sketch (R of rank < 8) the probe estimate alone is used
-  *est = *ok ? std::sqrt(hs[0] + hs[1] / SKK) : std::sqrt(hs[1] / SKK);
+  const double q = cert_q();
+  // the range part is used only when the range finder's CholQR succeeded (R of rank >= 8)
+  *ok = h->mixed && dst.status == sylv::ST_RUNNING;
+  const double z2 = *ok ? hs[0] : 0.0, t2 = *ok ? hs[1] : hs[3];
+  *est = std::sqrt(z2 + t2 / SKT);
+  *bound = std::sqrt(z2 + t2 / (q * SKT));
   return SYLV_OK;
 }
 
 template <typename T>
-int sketch(sylv_handle* h, double* est, bool* ok) {
+int sketch(sylv_handle* h, double* est, double* bound, bool* ok) {
   TRY(sketch_enqueue<T>(h));
-  return sketch_finish(h, est, ok);
+  return sketch_finish(h, est, bound, ok);
 }
 
 // A correction solve A dX + dX B = Q Z^T on the same operators (s = 8).
@@ -1237,28 +1281,34 @@ void prof_add(sylv_handle* dst, const sylv_handle* src) {
   }
 }
 
-// Outer driver: the factorized solve, then (unless disabled) the float64 true residual;
-// in the mixed mode, refinement rounds A dX + dX B = (rank-8 part of R) until the true
-// residual meets tol.
+// Recurrence stop factor of a certified solve (sylv_options.stop_margin).
+double stop_margin(const sylv_handle* h) { return h->opt.stop_margin > 0 ? h->opt.stop_margin : 0.4; }
+
+// Outer driver: the factorized solve, then (unless disabled) the float64 true-residual
+// certificate; SYLV_OK needs its bound <= tol.  In SYLV_FP64 the recurrence test of Algorithms
+// 4.1/4.2 runs at stop_margin * tol, so that the bound holds at the first check; in SYLV_MIXED,
+// refinement rounds A dX + dX B = (rank-8 part of R) until the bound meets tol.
 template <typename T>
 int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info) {
   const double t0 = now_s();
   const int64_t launches0 = sylv::launch_counter();
   free_subs(h);
   h->true_rel = -1.0;
+  h->true_bound = -1.0;
   h->refinements = 0;
-  int rc = run_inner<T>(h, method, tol, maxit, info);
+  const bool check = !h->is_sub && (h->mixed || !h->opt.no_true_residual) && h->C1rm != nullptr;
+  const double tol_in = (check && !h->mixed) ? tol * stop_margin(h) : tol;
+  int rc = run_inner<T>(h, method, tol_in, maxit, info);
   h->total_iters = h->iters;
   h->total_width = h->width;
-  const bool check = !h->is_sub && (h->mixed || !h->opt.no_true_residual) && h->C1rm != nullptr;
   if (check && (rc == SYLV_OK || rc == SYLV_ENOTCONV) && h->width > 0) {
-    const int refine_max = h->opt.refine_max > 0 ? h->opt.refine_max : 8;
+    const int refine_max = h->opt.refine_max > 0 ? h->opt.refine_max : 12;
     const double tol_c = 0.05;  // a correction only has to beat the rank-8 truncation of R
     for (int round = 0;; ++round) {
-      double est = 0.0;
+      double est = 0.0, bound = 0.0;
       bool ok = false;
       cudaEvent_t pa = prof_begin(h);
-      TRY(sketch<T>(h, &est, &ok));
+      TRY(sketch<T>(h, &est, &bound, &ok));
       if (pa) {
         cudaEvent_t pb = prof_event(h);
         if (pb) {
@@ -1274,8 +1324,17 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       h->prof.cur_k = -1;
       prof_finish(h, 1 << 30);
       h->true_rel = h->cnorm > 0 ? est / h->cnorm : 0.0;
-      if (!h->mixed) break;
-      if (h->true_rel <= tol) {
+      h->true_bound = h->cnorm > 0 ? bound / h->cnorm : 0.0;
+      if (!h->mixed) {
+        if (rc == SYLV_OK && h->true_bound > tol) {
+          rc = SYLV_ENOTCONV;
+          g_err = "the recurrence met its test but the float64 true residual is not certified below tol (bound " +
+                  std::to_string(h->true_bound) + ", estimate " + std::to_string(h->true_rel) +
+                  "); a smaller sylv_options.stop_margin runs further";
+        }
+        break;
+      }
+      if (h->true_bound <= tol) {
         rc = SYLV_OK;
         break;
       }
@@ -1305,6 +1364,7 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
     info->iters = (int32_t)h->total_iters;
     info->width = h->total_width;
     info->true_rel_res = h->true_rel;
+    info->true_rel_bound = h->true_bound;
     info->refinements = h->refinements;
     info->solve_ms = (now_s() - t0) * 1e3;
     info->kernel_launches = sylv::launch_counter() - launches0;
@@ -1360,7 +1420,9 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     CU(cudaMemsetAsync(x->side[0].H, 0, l2, strm));
     setup_qr<double>(x, 0);
     sylv::SmallCtx c = small_ctx(x);
-    sylv::launch_init_small(strm, c, x->side[0].RQR, x->side[0].RQR, tol, 0);
+    // certified instances stop their recurrence at stop_margin * tol (see run_solve)
+    const double tol_in = h->opt.no_true_residual ? tol : tol * stop_margin(h);
+    sylv::launch_init_small(strm, c, x->side[0].RQR, x->side[0].RQR, tol_in, 0);
     sylv::BatchInst& I = insts[i];
     std::memset(&I, 0, sizeof(I));
     I.n = x->side[0].n;
@@ -1494,6 +1556,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
              : ds.status == sylv::ST_WAIT_TIMEOUT ? SYLV_ETIMEOUT : SYLV_ENONFINITE;
     x->status = rc;
     x->true_rel = -1.0;
+    x->true_bound = -1.0;
     if (agg == SYLV_OK && rc != SYLV_OK) agg = rc;
     worst = std::max(worst, ds.r0 > 0 ? ds.rnorm / ds.r0 : 0.0);
     width += x->width;
@@ -1502,7 +1565,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
   }
   // float64 true residual of every instance (unless disabled), instances spread
   // over a pool of streams so the small ones run side by side
-  double worst_true = -1.0;
+  double worst_true = -1.0, worst_bound = -1.0;
   if (!h->opt.no_true_residual) {
     if (h->pool.empty()) {
       h->pool.resize(16, nullptr);
@@ -1517,13 +1580,24 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     }
     int rc_all = SYLV_OK;
     for (sylv_handle* x : todo) {
-      double est = 0.0;
+      double est = 0.0, bound = 0.0;
       bool ok = false;
-      const int rc = sketch_finish(x, &est, &ok);
+      const int rc = sketch_finish(x, &est, &bound, &ok);
       x->stream = h->stream;
       if (rc != SYLV_OK && rc_all == SYLV_OK) rc_all = rc;
       x->true_rel = x->cnorm > 0 ? est / x->cnorm : 0.0;
+      x->true_bound = x->cnorm > 0 ? bound / x->cnorm : 0.0;
       worst_true = std::max(worst_true, x->true_rel);
+      worst_bound = std::max(worst_bound, x->true_bound);
+      // an instance whose recurrence converged is certified only if its bound meets tol
+      if (x->status == SYLV_OK && x->true_bound > tol) {
+        x->status = SYLV_ENOTCONV;
+        if (agg == SYLV_OK) {
+          agg = SYLV_ENOTCONV;
+          g_err = "an instance's float64 true residual is not certified below tol (bound " +
+                  std::to_string(x->true_bound) + ")";
+        }
+      }
     }
     if (rc_all != SYLV_OK) return rc_all;
   }
@@ -1537,6 +1611,7 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     info->width = width;
     info->rel_res = worst;
     info->true_rel_res = worst_true;
+    info->true_rel_bound = worst_bound;
     info->solve_ms = (now_s() - t0) * 1e3;
     info->kernel_launches = sylv::launch_counter() - launches0;
   }
@@ -1590,7 +1665,7 @@ void sylv_default_options(sylv_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = SYLV_FP64;
   opt->poll_every = 8;
-  opt->refine_max = 8;
+  opt->refine_max = 12;
   opt->timeout_s = 3600.0;
 }
 
@@ -1937,6 +2012,40 @@ int sylv_get_hessenberg(sylv_handle* h, int32_t side, double* H, int64_t cap, in
     CU(cudaStreamSynchronize(h->stream));
   }
   return SYLV_OK;
+}
+
+int sylv_small_operator(sylv_handle* h, int64_t r, const double* Z, double* out) {
+  if (!h) return fail(SYLV_EINVAL, "NULL handle");
+  if (!h->batch.empty()) return fail(SYLV_EINVAL, "not available on a batched handle");
+  if (h->method == M_NONE || h->Qh == nullptr) return fail(SYLV_ESTATE, "no solve yet");
+  const int64_t s = h->s, rp = r + s;
+  // H_{k+1,k} and G_{k+1,k} must be built: r columns and r + s rows of the last solve's bases
+  if (r < 1 || r % s != 0 || r > (int64_t)(h->nblocks - 1) * s || rp > h->lds || !Z || !out)
+    return fail(SYLV_EINVAL, "r must be a positive multiple of s within the last solve's basis width");
+  DevState* st = nullptr;
+  CU(cudaMalloc(&st, sizeof(DevState)));  // a status word of its own: the solve's may say "stopped"
+  int rc = SYLV_OK;
+  const size_t ld = (size_t)h->lds * sizeof(double);
+  sylv::SmallCtx c = small_ctx(h);
+  c.st = st;
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevState), h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(h->Ph, ld, Z, r * sizeof(double), r * sizeof(double), r,
+                                              cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Qh, 0, (size_t)h->lds * rp * sizeof(double), h->stream);
+  if (e == cudaSuccess) {
+    sylv::launch_sylv_gemm(h->stream, c, (int)r, h->Ph, h->Qh, false);
+    e = cudaGetLastError();
+  }
+  DevState ds{};
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(out, rp * sizeof(double), h->Qh, ld, rp * sizeof(double), rp,
+                                              cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ds, st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) rc = fail(SYLV_ECUDA, std::string("sylv_small_operator: ") + cudaGetErrorString(e));
+  else if (ds.status == sylv::ST_WAIT_TIMEOUT) rc = fail(SYLV_ETIMEOUT, "a device-side wait gave up");
+  else if (ds.status != sylv::ST_RUNNING) rc = fail(SYLV_ENONFINITE, "non-finite value in the small operator");
+  cudaFree(st);
+  return rc;
 }
 
 int sylv_set_timeout(sylv_handle* h, double timeout_s) {

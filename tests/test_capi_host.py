@@ -41,7 +41,7 @@ def test_strerror_and_defaults(lib):
     assert lib.sylv_strerror(0) == b"converged"
     assert b"breakdown" in lib.sylv_strerror(4)
     o = ps.sylv_default_options()
-    assert o.precision == 0 and o.poll_every == 8 and o.timeout_s == 3600.0 and o.refine_max == 8
+    assert o.precision == 0 and o.poll_every == 8 and o.timeout_s == 3600.0 and o.refine_max == 12
     assert o.small_gemm == 0 and o.basis_gemm == 0
 
 

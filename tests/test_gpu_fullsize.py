@@ -7,8 +7,10 @@ The full oracle run takes ~16 minutes, so its residual history is stored
 tests/golden/make_golden.py from oracle/ only) and compared iteration by
 iteration while rounding has not yet separated the two; the rest is checked
 through properties that hold at any size: sampled orthonormality of V, the
-Arnoldi relation A V_k = V_{k+1} H_{k+1,k} on sampled rows, and the FP64 true
-residual.
+Arnoldi relation A V_k = V_{k+1} H_{k+1,k} on sampled rows, and the certified
+bound on the FP64 true residual (the solve's recurrence test runs at 0.4 tol, the
+default sylv_options.stop_margin, so it takes a few more iterations than the
+oracle's run at tol).
 """
 import os
 
@@ -38,7 +40,7 @@ def test_convdiff64x48_bicgstab_fp64_full_size():
     oracle_iters = len(g) - 1
     assert abs(info["iters"] - oracle_iters) <= max(3, oracle_iters // 10), (info["iters"], oracle_iters)
     np.testing.assert_allclose(hist[:21], g[:21], rtol=1e-6)
-    assert info["true_rel_res"] <= 1.05e-8
+    assert info["true_rel_res"] <= info["true_rel_bound"] <= 1e-8, info
     rng = np.random.default_rng(0)
     w = V.shape[1]
     cols = rng.choice(w, 96, replace=False)

@@ -4,6 +4,9 @@ FP64 mode: the factored solution X = V X^ W^T must match the oracle's to a
 relative Frobenius error of 1e-10 (the stated bar), the residual histories must
 agree iteration by iteration, and the block Hessenberg matrices (unique under
 the diag(R) > 0 convention) must match while the bases are still orthonormal.
+A default (certified) solve runs the printed recurrence test at STOP_MARGIN * tol,
+so it is compared with the oracle at that tolerance; its result must also meet
+tol on the oracle's direct true residual.
 Sizes span several CTAs / tiles and end in ragged tails (n not a multiple of
 the 256-thread CTA or the 64-wide small-matrix tile).
 """
@@ -12,11 +15,12 @@ import pytest
 
 import paper_2605_28274_gb300 as ps
 import workloads as wl
-from oracle import exact, factorized as fz
+from oracle import exact, factorized as fz, residual
 
 pytestmark = pytest.mark.gpu
 
 TOL_X = 1e-10  # relative Frobenius error of X in FP64 mode
+STOP_MARGIN = 0.4  # default sylv_options.stop_margin of a certified FP64 solve
 
 
 def rel(a, b):
@@ -76,9 +80,14 @@ def test_spmm_parity(k, precision):
 
 
 # ------------------------------------------------------------------ factorized CG
+def direct_rel(A, B, C1, C2, V, Xh, W):
+    return residual.direct(A.to_scipy(), B.to_scipy(), C1, C2, V, Xh, W) / np.linalg.norm(C1 @ C2.T)
+
+
 def test_cg_laplacian_400_matches_oracle_and_closed_form():
+    # the printed stop test of Algorithm 4.1 (no certificate): same iterations as the oracle
     p = wl.cfg_laplace_cg(N=20, s=1)
-    info, V, Xh, W, hist, H = gpu_solve(p.A, p.B, p.C1, p.C2, "cg", 1e-8, 200)
+    info, V, Xh, W, hist, H = gpu_solve(p.A, p.B, p.C1, p.C2, "cg", 1e-8, 200, no_true_residual=True)
     ref = oracle_solve(p.A, p.B, p.C1, p.C2, "cg", 1e-8, 200)
     assert info["status"] == ps.SYLV_OK and ref.status == "converged"
     assert info["iters"] == ref.iters
@@ -92,6 +101,21 @@ def test_cg_laplacian_400_matches_oracle_and_closed_form():
     assert rel(H, Ho) < 1e-12
 
 
+def test_cg_laplacian_400_certified_stop_meets_tol():
+    # the default solve: recurrence test at STOP_MARGIN * tol, then the float64 true-residual
+    # certificate; the oracle's direct residual of the returned factors is below tol
+    p = wl.cfg_laplace_cg(N=20, s=1)
+    tol = 1e-8
+    info, V, Xh, W, hist, H = gpu_solve(p.A, p.B, p.C1, p.C2, "cg", tol, 200)
+    ref = oracle_solve(p.A, p.B, p.C1, p.C2, "cg", tol * STOP_MARGIN, 200)
+    assert info["status"] == ps.SYLV_OK and ref.status == "converged"
+    assert info["iters"] == ref.iters
+    assert rel(V @ Xh @ W.T, ref.X()) < TOL_X
+    assert 0 < info["true_rel_bound"] <= tol
+    t = direct_rel(p.A, p.B, p.C1, p.C2, V, Xh, W)
+    assert t <= tol and info["true_rel_res"] <= info["true_rel_bound"]
+
+
 @pytest.mark.parametrize("s", [2, 3, 5])
 def test_cg_sylvester_ragged_iterates(s):
     A = wl.laplacian_2d(23, 0.3)  # n = 529
@@ -103,8 +127,8 @@ def test_cg_sylvester_ragged_iterates(s):
         assert info["status"] == ps.SYLV_ENOTCONV and info["iters"] == maxit
         assert rel(V @ Xh @ W.T, ref.X()) < TOL_X
     info, V, Xh, W, hist, H = gpu_solve(A, B, C1, C2, "cg", 1e-9, 300)
-    ref = oracle_solve(A, B, C1, C2, "cg", 1e-9, 300)
-    assert info["status"] == ps.SYLV_OK
+    ref = oracle_solve(A, B, C1, C2, "cg", 1e-9 * STOP_MARGIN, 300)
+    assert info["status"] == ps.SYLV_OK and info["true_rel_bound"] <= 1e-9
     assert abs(info["iters"] - ref.iters) <= 1
     assert rel(V @ Xh @ W.T, ref.X()) < TOL_X * 10 if info["iters"] != ref.iters else rel(V @ Xh @ W.T, ref.X()) < TOL_X
 
@@ -113,7 +137,7 @@ def test_lyapunov_cg_symmetric_and_matches_oracle():
     A = wl.laplacian_2d(30, 0.25)  # n = 900
     C1, _ = wl.rhs(900, None, 2, 4)
     info, V, Xh, W, hist, H = gpu_solve(A, None, C1, None, "cg", 1e-10, 400, lyapunov=True)
-    ref = oracle_solve(A, None, C1, None, "cg", 1e-10, 400, lyapunov=True)
+    ref = oracle_solve(A, None, C1, None, "cg", 1e-10 * STOP_MARGIN, 400, lyapunov=True)
     assert info["status"] == ps.SYLV_OK and ref.status == "converged"
     assert info["iters"] == ref.iters
     assert np.array_equal(Xh, Xh.T)
@@ -135,8 +159,9 @@ def test_bicgstab_convdiff_matches_oracle(NA, NB, s):
         assert rel(V @ Xh @ W.T, ref.X()) < TOL_X
         assert rel(H, ref.basisA.Hk(2 * maxit + 1, 2 * maxit)) < 1e-12
     info, V, Xh, W, hist, H = gpu_solve(A, B, C1, C2, "bicgstab", 1e-8, 300)
-    ref = oracle_solve(A, B, C1, C2, "bicgstab", 1e-8, 300)
+    ref = oracle_solve(A, B, C1, C2, "bicgstab", 1e-8 * STOP_MARGIN, 300)
     assert info["status"] == ps.SYLV_OK and ref.status == "converged"
+    assert info["true_rel_bound"] <= 1e-8 and direct_rel(A, B, C1, C2, V, Xh, W) <= 1e-8
     assert abs(info["iters"] - ref.iters) <= max(2, ref.iters // 10)
     k = min(info["iters"], ref.iters, 10)
     np.testing.assert_allclose(hist[: k + 1], ref.history[: k + 1], rtol=1e-7)
