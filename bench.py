@@ -64,6 +64,8 @@ def config_of(p):
             "method": "factorized BiCGSTAB (Algorithm 4.2)",
             "n": p.A.nrows, "m": p.B.nrows, "nnzA": p.A.nnz, "nnzB": p.B.nnz, "s": p.s, "tol": p.tol,
             "maxit": p.maxit, "precision": p.precision,
+            "stop": ("certified: float64 true relative residual bound <= tol with probability >= 1 - 1e-4 "
+                     "(recurrence test at 0.4 tol, then a 32-column Gaussian probe of the residual)"),
             "l2": "inputs larger than L2: the basis grows to ~2 GB per side per solve (L2 = 126 MB)"}
 
 
@@ -222,14 +224,29 @@ def golden_iterations():
         return None
 
 
+def model_check():
+    """The cost model of ``oracle_time_to_tol`` against a real oracle solve timed to completion, on
+    a smaller workload of the same kind (CD 24^3 x 18^3, s = 4, tol 1e-8: a few seconds)."""
+    from oracle import factorized as fz
+
+    q = wl.cfg_convdiff_bicgstab(24, 18, 4, tol=1e-8, maxit=300)
+    t = time.perf_counter()
+    ref = fz.factorized_bicgstab(q.A.to_scipy(), q.B.to_scipy(), q.C1, q.C2, q.tol, q.maxit)
+    measured = time.perf_counter() - t
+    model, sample, _ = oracle_time_to_tol(q, ref.iters)
+    return {"workload": "convdiff3d_24^3_x_18^3_s4_bicgstab_fp64", "iters": ref.iters, "measured_s": measured,
+            "model_s": model, "model_over_measured": model / measured, "model_sample_s": sample}
+
+
 def cpu_baseline(p, iters):
     t, sample, det = oracle_time_to_tol(p, iters)
-    return {"value": t, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+    return {"value": t, "unit": "s", "cores": blas_threads(), "kind": "oracle", "extrapolated": True,
             "sample": (f"measured {sample:.1f} s of the CPU FP64 oracle on this workload (BCGS2 Arnoldi steps of both "
                        f"bases at widths 2 and {2 * iters} blocks, small-matrix iterations at orders "
                        f"{(2 * det['small_iter_s']['k_lo'] + 1) * p.s} and {(2 * det['small_iter_s']['k_hi'] + 1) * p.s})"
-                       f", summed over {iters} iterations with the per-step cost structure"),
-            "details": det}
+                       f", summed over {iters} iterations with the per-step cost structure (extrapolated; "
+                       f"model_check times a full oracle solve of a smaller case against the same model)"),
+            "details": det, "model_check": model_check()}
 
 
 # ----------------------------------------------------------------------------- variants
@@ -270,16 +287,58 @@ def timed_solves(p, stream, precision, steps, warmup, method="bicgstab"):
     return e0.elapsed_time(e1) / steps / 1e3, info
 
 
-def measure_mixed(p, stream, steps, warmup):
+def factored_rel_diff_gpu(F1, F2):
+    """||V1 X1 W1^T - V2 X2 W2^T||_F / ||V2 X2 W2^T||_F without forming X: Householder QR (torch,
+    on the GPU, float64) of the stacked factors [V1, V2] and [W1, W2], then the small core."""
+    import torch
+
+    (V1, X1, W1), (V2, X2, W2) = F1, F2
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    RL = torch.linalg.qr(torch.cat([t(V1), t(V2)], 1), mode="r")[1]
+    RR = torch.linalg.qr(torch.cat([t(W1), t(W2)], 1), mode="r")[1]
+    r1, r2 = X1.shape[0], X2.shape[0]
+    D = torch.zeros((r1 + r2, r1 + r2), dtype=torch.float64, device=dev)
+    D[:r1, :r1] = t(X1)
+    D[r1:, r1:] = -t(X2)
+    R2L = torch.linalg.qr(t(V2), mode="r")[1]
+    R2R = torch.linalg.qr(t(W2), mode="r")[1]
+    num = torch.linalg.norm(RL @ D @ RR.T)
+    den = torch.linalg.norm(R2L @ t(X2) @ R2R.T)
+    return float(num / den)
+
+
+def measure_mixed(p, stream, steps, warmup, fp64_factors=None):
     """Same operators and tolerance in the mixed mode (FP32 factors, FP64 small side,
-    FP64 true-residual refinement): time to a TRUE relative residual of p.tol."""
+    FP64 true-residual refinement): time to a certified TRUE relative residual of p.tol, and
+    the relative error of X against the FP64 solve of the same workload."""
+    import paper_2605_28274_gb300 as ps
+
     t, info = timed_solves(p, stream, "mixed", steps, warmup)
     gbs, frac, per = profiled_breakdown(p, stream, "mixed", p.maxit)
-    return {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_mixed", "value": t, "unit": "s",
-            "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
-            "true_rel_res": info["true_rel_res"], "width": info["width"],
-            "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
-            "kernel_profile_one_stream": per}
+    out = {"workload": "convdiff3d_64^3_x_48^3_s4_bicgstab_mixed", "value": t, "unit": "s",
+           "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
+           "true_rel_res": info["true_rel_res"], "true_rel_bound": info["true_rel_bound"], "width": info["width"],
+           "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
+           "kernel_profile_one_stream": per}
+    if fp64_factors is not None:
+        with ps.Solver(p.A, p.B, p.C1, p.C2, precision="mixed", cuda_stream=stream.cuda_stream) as sv:
+            sv.bicgstab(p.tol, p.maxit)
+            fm = sv.factors()
+        out["rel_error_vs_fp64_solve"] = factored_rel_diff_gpu(fm, fp64_factors)
+        out["rel_error_how"] = ("||X_mixed - X_fp64||_F / ||X_fp64||_F through the QR of the stacked factors; "
+                                "X_fp64 = the certified FP64 solve of the timed line")
+    return out
+
+
+def measure_exhaustion(stream, steps, warmup):
+    """The 400-unknown Laplacian with s = 8 in mixed precision (CG): the block Krylov space has
+    n / s = 50 blocks, so the bases fill up; time to a certified true residual of 1e-8."""
+    p = wl.cfg_laplace_cg(N=20, s=8, precision="mixed")
+    t, info = timed_solves(p, stream, "mixed", steps, warmup, "cg")
+    return {"workload": "laplace2d_20^2_s8_cg_mixed", "value": t, "unit": "s", "status": info["status_name"],
+            "iters_total": info["iters"], "refinements": info["refinements"], "true_rel_res": info["true_rel_res"],
+            "true_rel_bound": info["true_rel_bound"], "width": info["width"]}
 
 
 def measure_methods(p, stream, steps, warmup):
@@ -293,7 +352,7 @@ def measure_methods(p, stream, steps, warmup):
             t, info = timed_solves(p, stream, prec, steps, warmup, meth)
             out[f"{meth}_{prec}_convdiff3d_64^3_x_48^3_s4"] = {
                 "value": t, "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
-                "width": info["width"], "true_rel_res": info["true_rel_res"]}
+                "width": info["width"], "true_rel_res": info["true_rel_res"], "true_rel_bound": info["true_rel_bound"]}
     A, B = wl.laplacian_2d(512, 0.5), wl.laplacian_2d(384, 0.5)
     C1, C2 = wl.rhs(A.nrows, B.nrows, 4, 0)
     q = wl.Problem(name="laplace2d_512x384_s4", A=A, B=B, C1=C1, C2=C2, s=4, method="cg", tol=1e-8, maxit=300)
@@ -302,7 +361,7 @@ def measure_methods(p, stream, steps, warmup):
             t, info = timed_solves(q, stream, prec, steps, warmup, meth)
             out[f"{meth}_{prec}_laplace2d_512^2_x_384^2_shift0.5_s4"] = {
                 "value": t, "unit": "s", "status": info["status_name"], "iters_total": info["iters"],
-                "width": info["width"], "true_rel_res": info["true_rel_res"]}
+                "width": info["width"], "true_rel_res": info["true_rel_res"], "true_rel_bound": info["true_rel_bound"]}
     return out
 
 
@@ -342,7 +401,8 @@ def measure_batched(stream, steps, warmup):
     return {"workload": "batched_lyapunov_64x_laplace2d_N64-256_s124_cg_fp64", "value": t_batch, "unit": "s",
             "status": info["status_name"], "instances": len(probs), "sum_n": int(sum(q.A.nrows for q in probs)),
             "iters_min_median_max": [int(min(its)), int(np.median(its)), int(max(its))],
-            "true_rel_res_max": info["true_rel_res"], "kernel_launches": info["kernel_launches"],
+            "true_rel_res_max": info["true_rel_res"], "true_rel_bound_max": info["true_rel_bound"],
+            "kernel_launches": info["kernel_launches"],
             "plain_fp64_sequential_s": t_seq, "speedup_vs_plain_fp64": t_seq / t_batch}
 
 
@@ -354,7 +414,9 @@ def measure_large(stream, steps, warmup):
     gbs, frac, per = profiled_breakdown(p, stream, "mixed", p.maxit)
     return {"workload": "convdiff3d_128^3_x_96^3_s8_bicgstab_mixed", "value": t, "unit": "s",
             "status": info["status_name"], "iters_total": info["iters"], "refinements": info["refinements"],
-            "true_rel_res": info["true_rel_res"], "width": info["width"],
+            "true_rel_res": info["true_rel_res"], "true_rel_bound": info["true_rel_bound"], "width": info["width"],
+            "error_vs_fp64": ("not formed: an FP64 solve of this workload holds ~150 GB of float64 bases; the "
+                              "mixed-vs-FP64 error is measured on the 64^3 x 48^3 workload (variants.mixed)"),
             "spmm_gram_update_fp32_gbs": gbs, "frac_of_measured_hbm": frac,
             "kernel_profile_one_stream": per}
 
@@ -555,16 +617,19 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         d2h = V.nbytes + X.nbytes + W.nbytes
     e2e_s = max_over_ranks(statistics.mean(e2e_times), dist)
-    sv.close()
 
     variants = {}
     if not args.no_variants:
-        variants["mixed"] = measure_mixed(p, stream, args.steps, 2)
+        fp64_factors = sv.factors() if args.precision == "fp64" else None
+        variants["mixed"] = measure_mixed(p, stream, args.steps, 2, fp64_factors)
+        del fp64_factors
         variants["mixed"]["speedup_vs_fp64"] = (ms_step / 1e3) / variants["mixed"]["value"]
+        variants["exhaustion_mixed"] = measure_exhaustion(stream, args.steps, 2)
         variants["batched"] = measure_batched(stream, args.steps, 2)
         variants["methods"] = measure_methods(p, stream, max(1, min(args.steps, 2)), 1)
-    if args.large:
-        variants["large_mixed"] = measure_large(stream, 1, 1)
+        if not args.no_large:
+            variants["large_mixed"] = measure_large(stream, 1, 1)
+    sv.close()
 
     line = {"metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -572,7 +637,7 @@ def run_ours(args):
             "iters": iters, "status": status, "rel_res": infos[-1]["rel_res"],
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "status": STATUS(inf2)},
-            "true_rel_res": infos[-1]["true_rel_res"],
+            "true_rel_res": infos[-1]["true_rel_res"], "true_rel_bound": infos[-1]["true_rel_bound"],
             "roofline": roof, "spmm_gram_hbm": spmm_gram, "kernel_breakdown": breakdown,
             "gpu_launches": launches, "clocks": clocks, "variants": variants}
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -604,15 +669,18 @@ def run_reference(args):
         samples.append(smp)
     wall = time.perf_counter() - t0
     v = statistics.mean(vals)
+    check = model_check()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(p),
             "iters": iters,
-            "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "s", "cores": blas_threads(), "kind": "oracle", "extrapolated": True,
                              "sample": (f"each step measures {statistics.mean(samples):.1f} s of the CPU FP64 oracle "
                                         f"on this workload (Arnoldi steps at 2 and {2 * iters} blocks, small-matrix "
                                         f"iterations at two orders) and sums the fitted costs over the oracle's "
-                                        f"{iters} iterations (tests/golden)")},
+                                        f"{iters} iterations (tests/golden); model_check times a full oracle solve "
+                                        f"of a smaller case against the same model"),
+                             "model_check": check},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -628,8 +696,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
                     help="precision of the timed line (the variants are always measured)")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed and batched variant timings")
-    ap.add_argument("--large", action="store_true",
-                    help="also time the large mixed-precision workload (CD 128^3 x 96^3, s = 8; ~60 GB of HBM)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large mixed-precision workload (CD 128^3 x 96^3, s = 8; ~60 GB of HBM, ~40 s)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

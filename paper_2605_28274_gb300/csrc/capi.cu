@@ -1344,8 +1344,10 @@ int run_solve(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
       TRY(make_sub(h, &sub));
       h->subs.push_back(sub);
       sylv_info si;
-      // a correction only has to reach tol_c; its basis is sized for at most 100 iterations
-      const int src = run_inner<T>(sub, method, tol_c, std::min(maxit, 100), &si);
+      // a correction only has to reach tol_c (measured: 7-15 iterations); its basis is sized for
+      // at most 40, so that a dozen rounds of a large workload fit in device memory beside the
+      // main bases (an unconverged correction is still a correction)
+      const int src = run_inner<T>(sub, method, tol_c, std::min(maxit, 40), &si);
       prof_add(h, sub);
       h->total_iters += sub->iters;
       h->total_width += sub->width;
