@@ -21,8 +21,11 @@
 // pairs p + q > 9, below 2^-56 of (max |row of A|)(max |column of B|) per term.
 //
 // Digits are stored in the canonical no-swizzle K-major layout of the tcgen05 shared-memory
-// matrix descriptor (8-row x 16-byte core matrices), one 128 x 64 (A) or 64 x 64 (B) block
-// per (digit, row tile, k chunk), so plain 1-D bulk copies (cp.async.bulk) load each block.
+// matrix descriptor (8-row x 16-byte core matrices), one 128 x 32 (A) or 64 x 32 (B) block
+// per (digit, row tile, k stage), so plain 1-D bulk copies (cp.async.bulk) load each block.
+// A CTA owns a 128 x 64 output tile and a range of its fold periods (exact k splits fill the
+// GPU at small orders); two stage buffers let the copies of the next 32 values of k run during
+// the MMAs of the current ones.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -40,10 +43,10 @@ constexpr int OZ_L = OZ_P + 1;        // pairs with p + q <= OZ_L are kept
 constexpr int OZ_NLEV = OZ_L - 1;     // levels 2..OZ_L
 constexpr int OZ_TM = 128;            // output rows per CTA (MMA M)
 constexpr int OZ_TN = 64;             // output columns per CTA (MMA N)
-constexpr int OZ_KC = 64;             // k per loaded chunk
-constexpr int OZ_FOLD = 2;            // chunks per fold (128 values of k)
-constexpr int OZ_ABLK = OZ_TM * OZ_KC;  // BF16 elements of one A digit block (16 KB)
-constexpr int OZ_BBLK = OZ_TN * OZ_KC;  // BF16 elements of one B digit block (8 KB)
+constexpr int OZ_KC = 32;             // k per stage (one bulk copy per digit plane and operand)
+constexpr int OZ_FOLD = 4;            // stages per fold (128 values of k)
+constexpr int OZ_ABLK = OZ_TM * OZ_KC;  // BF16 elements of one A digit block (8 KB)
+constexpr int OZ_BBLK = OZ_TN * OZ_KC;  // BF16 elements of one B digit block (4 KB)
 constexpr int OZ_THREADS = 256;     // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; each takes half the columns
 constexpr int OZ_CPT = OZ_TN / 2;    // output columns per thread
 constexpr int OZ_TMEM_COLS = OZ_NLEV * OZ_TN;  // one FP32 accumulator tile per level
@@ -51,7 +54,9 @@ static_assert(OZ_TMEM_COLS == 512, "tensor memory holds 512 columns");
 constexpr int OZ_EXP_BAD = 1 << 20;   // exponent sentinel: the row holds a non-finite value
 constexpr int OZ_OMEGA_CTAS = 1024;  // grid of the omega reduction (its partials live in the scratch)
 constexpr int OZ_WAIT_ITERS = 1 << 20;
-constexpr size_t OZ_SMEM = (size_t)OZ_P * (OZ_ABLK + OZ_BBLK) * 2 + 2048;  // + 1 KB alignment, barriers
+constexpr size_t OZ_STAGE = (size_t)OZ_P * (OZ_ABLK + OZ_BBLK) * 2;  // 96 KB
+constexpr size_t OZ_SMEM = 2 * OZ_STAGE + 2048;  // two stages + 1 KB alignment, barriers
+constexpr int OZ_MAX_SPLIT_CTAS = 4 * 152;  // k-split partials are kept for at most this many CTAs
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -124,8 +129,28 @@ __global__ void __launch_bounds__(NT) oz_split_kernel(const DevState* st, const 
     const int k = kg * 8 + j;
     double x = 0.0;
     if (i < R && k < K && e != OZ_EXP_BAD) x = X[(int64_t)i * si + (int64_t)k * sk];
-    // |x| < 2^e, so |x 2^{56-e}| < 2^56: an exact integer after rounding
-    Nv[j] = (e == OZ_EXP_BAD) ? 0 : __double2ll_rn(scalbn(x, 56 - e));
+    // N = x 2^{56-e} rounded to the nearest integer (ties to even); |x| < 2^e, so |N| <= 2^56.
+    // Integer operations on the IEEE bits only: the FP64 pipe of this GPU is narrow.
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    long long N = 0;
+    if (ex != 0x7FF && (bits & 0x7FFFFFFFFFFFFFFFull) != 0) {
+      // x = mant 2^{ex - 1075} (a subnormal x: no implicit bit, exponent field 1)
+      const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (ex != 0 ? (1ull << 52) : 0ull);
+      const int sh = (ex != 0 ? ex : 1) - 1075 + 56 - e;  // N = mant 2^sh, sh <= 3
+      unsigned long long u;
+      if (sh >= 0) {
+        u = mant << sh;
+      } else if (sh < -54) {
+        u = 0;
+      } else {
+        const int rs = -sh;
+        const unsigned long long q = mant >> rs, rem = mant & ((1ull << rs) - 1), half = 1ull << (rs - 1);
+        u = q + ((rem > half || (rem == half && (q & 1))) ? 1ull : 0ull);
+      }
+      N = (bits >> 63) ? -(long long)u : (long long)u;
+    }
+    Nv[j] = N;
   }
   const int nkc = Kp / OZ_KC;
   const int64_t blk = ((int64_t)(i / T) * nkc + (kg * 8) / OZ_KC) * ((int64_t)T * OZ_KC);
@@ -143,7 +168,7 @@ __global__ void __launch_bounds__(NT) oz_split_kernel(const DevState* st, const 
       } else {
         d = Nv[j];
       }
-      v[j] = __float2bfloat16_rn((float)d);  // |d| <= 128: exact
+      v[j] = __float2bfloat16_rn(__int2float_rn((int)d));  // |d| <= 128: exact
     }
     *reinterpret_cast<uint4*>(dig + (int64_t)(p - 1) * plane + blk + inb) = *reinterpret_cast<const uint4*>(v);
   }
@@ -170,20 +195,24 @@ __device__ __forceinline__ int oz_int(float v) {
 
 // Out[a + b*ldo] (= or +=) 2^{e_a + f_b} sum_k A(a, k) B(b, k) over the tile's k range.
 // A digits: planes of Mp x Kp (tiles of 128 rows), B digits: Np x Kp (tiles of 64 rows).
-// hess: 0 all k chunks; 1 start at the block-Hessenberg bound of the tile's first row
+// hess: 0 all k stages; 1 start at the block-Hessenberg bound of the tile's first row
 // (A = H); 2 the same for the tile's first column (B = G^T).  Valid outputs a < Mv, b < Nv.
+// blockIdx.z splits the tile's fold periods into gridDim.z ranges; with more than one, each CTA
+// writes its exact int64 fixed-point sums to part (oz_reduce_kernel adds them and writes Out).
+// Stages of 32 values of k are double-buffered: the bulk copies of the next stage run during
+// this stage's MMAs.  One thread issues the 72 MMAs of a stage from descriptors computed once
+// and advanced by constant offsets (issuing, not the tensor pipe, bounds MMAs this narrow).
 // A wait that gives up sets the solve status to ST_WAIT_TIMEOUT.
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
     DevState* st, const __nv_bfloat16* __restrict__ Ad, int64_t planeA, const __nv_bfloat16* __restrict__ Bd,
     int64_t planeB, int nkc, const int* __restrict__ ea, const int* __restrict__ fb, int hess, int s, double* Out,
-    int64_t ldo, int Mv, int Nv, int add) {
+    int64_t ldo, int Mv, int Nv, int add, long long* __restrict__ part) {
   if (stopped(st)) return;
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   unsigned char* base = (unsigned char*)(((uintptr_t)oz_smem + 1023) & ~(uintptr_t)1023);
-  __nv_bfloat16* sA = (__nv_bfloat16*)base;                       // 8 x 16 KB
-  __nv_bfloat16* sB = sA + (size_t)OZ_P * OZ_ABLK;                // 8 x 8 KB
-  uint64_t* bars = (uint64_t*)(sB + (size_t)OZ_P * OZ_BBLK);      // [0] loads, [1] MMAs
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  // stage b: A planes at base + b * OZ_STAGE, B planes after them
+  uint64_t* bars = (uint64_t*)(base + 2 * OZ_STAGE);  // [0], [1] loads of stage 0 / 1, [2] MMAs
+  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mt = blockIdx.x, nt = blockIdx.y;
   const int a0 = mt * OZ_TM, b0 = nt * OZ_TN;
@@ -191,17 +220,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
   int kc0 = 0;
   if (hess == 1) kc0 = max(0, (a0 / s - 1) * s) / OZ_KC;
   if (hess == 2) kc0 = max(0, (b0 / s - 1) * s) / OZ_KC;
-  // fold periods start at even chunks, so each covers at most OZ_FOLD chunks
+  // fold periods start at multiples of OZ_FOLD stages, so each covers at most OZ_FOLD stages
   kc0 -= kc0 % OZ_FOLD;
+  // this CTA's fold periods
+  const int periods = (nkc - kc0 + OZ_FOLD - 1) / OZ_FOLD;
+  const int per_split = (periods + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int kb = kc0 + (int)blockIdx.z * per_split * OZ_FOLD;
+  const int ke = min(nkc, kb + per_split * OZ_FOLD);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(OZ_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  const uint32_t bar_ld = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  const uint32_t bar_ld0 = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[2]);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_ld0 + 8));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -217,69 +252,80 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
 
   const uint32_t id = oz_idesc(OZ_TM, OZ_TN);
   const uint32_t lbo = 128, sbo = (OZ_KC / 8) * 128;
-  const uint32_t abytes = OZ_ABLK * 2, bbytes = OZ_BBLK * 2;
-  uint32_t phase = 0;
-  bool ok = true;
-  uint32_t stuck_bar = 0;  // barrier whose wait gave up (0: none)
-  for (int kc = kc0; kc < nkc && ok; ++kc) {
-    const bool first_of_fold = ((kc - kc0) % OZ_FOLD) == 0;
-    const bool last_of_fold = ((kc - kc0) % OZ_FOLD) == OZ_FOLD - 1 || kc == nkc - 1;
-    if (tid == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld),
-                   "r"(OZ_P * (abytes + bbytes))
-                   : "memory");
+  constexpr uint32_t abytes = OZ_ABLK * 2, bbytes = OZ_BBLK * 2;
+  // stage kc's copies into buffer (kc - kb) & 1 (thread 0)
+  auto load = [&](int kc) {
+    const int b = (kc - kb) & 1;
+    unsigned char* sA = base + (size_t)b * OZ_STAGE;
+    unsigned char* sB = sA + (size_t)OZ_P * abytes;
+    const uint32_t bar = bar_ld0 + 8 * b;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OZ_P * (abytes + bbytes))
+                 : "memory");
 #pragma unroll 1
-      for (int p = 0; p < OZ_P; ++p) {
-        const __nv_bfloat16* ga = Ad + (int64_t)p * planeA + ((int64_t)mt * nkc + kc) * OZ_ABLK;
-        const __nv_bfloat16* gb = Bd + (int64_t)p * planeB + ((int64_t)nt * nkc + kc) * OZ_BBLK;
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sA + (size_t)p * OZ_ABLK)),
-            "l"(ga), "r"(abytes), "r"(bar_ld)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sB + (size_t)p * OZ_BBLK)),
-            "l"(gb), "r"(bbytes), "r"(bar_ld)
-            : "memory");
-      }
+    for (int p = 0; p < OZ_P; ++p) {
+      const __nv_bfloat16* ga = Ad + (int64_t)p * planeA + ((int64_t)mt * nkc + kc) * OZ_ABLK;
+      const __nv_bfloat16* gb = Bd + (int64_t)p * planeB + ((int64_t)nt * nkc + kc) * OZ_BBLK;
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sA + (size_t)p * abytes)),
+                   "l"(ga), "r"(abytes), "r"(bar)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sB + (size_t)p * bbytes)),
+                   "l"(gb), "r"(bbytes), "r"(bar)
+                   : "memory");
     }
-    ok = __syncthreads_and(oz_wait(bar_ld, phase));
+  };
+  if (tid == 0 && kb < ke) load(kb);
+  bool ok = true;
+  uint32_t stuck_bar = 0, stuck_phase = 0;  // barrier whose wait gave up (0: none)
+  int next_stage = -1;                      // thread 0: the stage whose copies it issued ahead
+  for (int kc = kb; kc < ke && ok; ++kc) {
+    const int i = kc - kb, b = i & 1;
+    const bool first_of_fold = (i % OZ_FOLD) == 0;
+    const bool last_of_fold = (i % OZ_FOLD) == OZ_FOLD - 1 || kc == ke - 1;
+    // the other buffer is free: the MMAs of stage kc - 1 completed in the previous iteration
+    if (tid == 0 && kc + 1 < ke) {
+      load(kc + 1);
+      next_stage = kc + 1;
+    }
+    const uint32_t ph_ld = (uint32_t)(i >> 1) & 1u;
+    ok = __syncthreads_and(oz_wait(bar_ld0 + 8 * b, ph_ld));
     if (!ok) {
-      stuck_bar = bar_ld;
+      stuck_bar = bar_ld0 + 8 * b;
+      stuck_phase = ph_ld;
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (tid == 0) {
       // level l = p + q accumulates in TMEM columns (l - 2) * 64 ..; its first MMA of a fold
       // period overwrites (p = 1 comes first for every level)
-#pragma unroll 1
-      for (int p = 1; p <= OZ_P; ++p) {
-#pragma unroll 1
-        for (int q = 1; q <= OZ_L - p; ++q) {
-          const uint32_t dcol = tmem + (uint32_t)((p + q - 2) * OZ_TN);
-#pragma unroll 1
+      const uint32_t sA = smem_u32(base + (size_t)b * OZ_STAGE);
+      const uint64_t dA = oz_sdesc(sA, lbo, sbo), dB = oz_sdesc(sA + OZ_P * abytes, lbo, sbo);
+#pragma unroll
+      for (int p = 1; p <= OZ_P; ++p)
+#pragma unroll
+        for (int q = 1; q <= OZ_L - p; ++q)
+#pragma unroll
           for (int ks = 0; ks < OZ_KC / 16; ++ks) {
-            const uint64_t da = oz_sdesc(smem_u32(sA + (size_t)(p - 1) * OZ_ABLK) + ks * 256, lbo, sbo);
-            const uint64_t db = oz_sdesc(smem_u32(sB + (size_t)(q - 1) * OZ_BBLK) + ks * 256, lbo, sbo);
             const uint32_t acc = (first_of_fold && p == 1 && ks == 0) ? 0u : 1u;
             asm volatile(
                 "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(dcol),
-                "l"(da), "l"(db), "r"(id), "r"(acc)
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(
+                    tmem + (uint32_t)((p + q - 2) * OZ_TN)),
+                "l"(dA + (uint64_t)(((p - 1) * abytes + ks * 256) >> 4)),
+                "l"(dB + (uint64_t)(((q - 1) * bbytes + ks * 256) >> 4)), "r"(id), "r"(acc)
                 : "memory");
           }
-        }
-      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
                    : "memory");
     }
-    ok = __syncthreads_and(oz_wait(bar_mma, phase));
+    const uint32_t ph_mma = (uint32_t)i & 1u;
+    ok = __syncthreads_and(oz_wait(bar_mma, ph_mma));
     if (!ok) {
       stuck_bar = bar_mma;
+      stuck_phase = ph_mma;
       break;
     }
-    phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (last_of_fold) {
 #pragma unroll
@@ -308,12 +354,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // shared buffers and tensor memory are free for the next chunk
+    __syncthreads();  // tensor memory and this stage's buffer are free for the next stages
   }
 
   if (ok) {
-    const int a = a0 + quarter * 32 + lane;
-    if (a < Mv) {
+    const int arow = quarter * 32 + lane, a = a0 + arow;
+    if (gridDim.z > 1) {
+      // exact partial sums of this k range: [split][tile][column][row] x (w1, w2), rows fastest
+      // (the lanes of a warp hold consecutive rows: coalesced here and in oz_reduce_kernel)
+      const int64_t tile = (int64_t)blockIdx.z * gridDim.x * gridDim.y + (int64_t)mt * gridDim.y + nt;
+#pragma unroll
+      for (int j = 0; j < OZ_CPT; ++j) {
+        longlong2* o = (longlong2*)part + (tile * OZ_TN + col0 + j) * OZ_TM + arow;
+        *o = make_longlong2(w1[j], w2[j]);
+      }
+    } else if (a < Mv) {
       const int e = ea[a];
 #pragma unroll
       for (int j = 0; j < OZ_CPT; ++j) {
@@ -335,13 +390,46 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(
       st->breakdown_where = 200;
       atomicExch(&st->status, (int)ST_WAIT_TIMEOUT);
     }
-    // copies or MMAs that timed out may still be in flight: a second bounded wait before
-    // the shared memory and the tensor memory are given up
-    oz_wait(stuck_bar, phase);
+    // copies or MMAs that timed out may still be in flight: a second bounded wait before the
+    // shared memory and the tensor memory are given up, and one for the copies of the stage
+    // issued ahead
+    oz_wait(stuck_bar, stuck_phase);
+    if (tid == 0 && next_stage >= 0) {
+      const int j = next_stage - kb;
+      oz_wait(bar_ld0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1u);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+}
+
+// Out (= or +=) the sum over the k splits of the exact partial sums, scaled by 2^{e_a + f_b}.
+__global__ void __launch_bounds__(NT) oz_reduce_kernel(DevState* st, const long long* __restrict__ part, int splits,
+                                                       int tm, int tn, const int* __restrict__ ea,
+                                                       const int* __restrict__ fb, double* Out, int64_t ldo, int Mv,
+                                                       int Nv, int add) {
+  if (stopped(st)) return;
+  const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (t >= (int64_t)Mv * Nv) return;
+  const int a = (int)(t % Mv), b = (int)(t / Mv);  // consecutive threads: consecutive rows (Out is column-major)
+  const int64_t tile = (int64_t)(a / OZ_TM) * tn + b / OZ_TN;
+  const int64_t idx = (tile * OZ_TN + b % OZ_TN) * OZ_TM + a % OZ_TM;
+  const int64_t stride = (int64_t)tm * tn * OZ_TM * OZ_TN;
+  long long w1 = 0, w2 = 0;
+  for (int z = 0; z < splits; ++z) {
+    const longlong2 v = ((const longlong2*)part)[z * stride + idx];
+    w1 += v.x;
+    w2 += v.y;
+  }
+  const int e = ea[a], f = fb[b];
+  const int x = e + f;
+  const double sc = x < -1022 ? 0.0 : (x > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
+                                                : __longlong_as_double((long long)(x + 1023) << 52));
+  double v = fma((double)w1, 0x1p-35, (double)w2 * 0x1p-63) * sc;
+  if (e == OZ_EXP_BAD || f == OZ_EXP_BAD) v = __longlong_as_double(0x7FF8000000000000ll);
+  double* o = Out + a + (int64_t)b * ldo;
+  *o = add ? (*o + v) : v;
 }
 
 // <Out(1:r,1:r), Z> and <Out, Out> over the rp x rp extent; the last CTA sets omega.
@@ -389,9 +477,11 @@ int oz_pad(int x, int t) { return (x + t - 1) / t * t; }
 
 size_t ozaki_scratch_bytes(int rmax) {
   const int Mp = oz_pad(rmax, OZ_TM), Kp = oz_pad(rmax, OZ_KC * OZ_FOLD);
-  // two digit sets (A and B operand) of Mp x Kp BF16 x 8 planes, exponents, omega partials
+  // two digit sets (A and B operand) of Mp x Kp BF16 x 8 planes, exponents, omega partials,
+  // k-split partial sums (two int64 per output of at most OZ_MAX_SPLIT_CTAS tiles)
   return (size_t)2 * OZ_P * Mp * Kp * 2 + (size_t)2 * Mp * sizeof(int) + (size_t)4 * Mp * sizeof(unsigned long long) +
-         (size_t)2 * OZ_OMEGA_CTAS * sizeof(double) + 256;
+         (size_t)2 * OZ_OMEGA_CTAS * sizeof(double) + (size_t)OZ_MAX_SPLIT_CTAS * OZ_TM * OZ_TN * 2 * sizeof(long long) +
+         512;
 }
 
 bool ozaki_setup() {
@@ -415,7 +505,29 @@ int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const 
   int* fb = ea + Mp;
   unsigned long long* mx = (unsigned long long*)(((uintptr_t)(fb + Mp) + 15) & ~(uintptr_t)15);  // 4 x Mp
   double* partials = (double*)(mx + 4 * (size_t)Mp);
-  const dim3 grid(Mp / OZ_TM, Np / OZ_TN);
+  long long* kpart = (long long*)(((uintptr_t)(partials + 2 * OZ_OMEGA_CTAS) + 255) & ~(uintptr_t)255);
+  // k splits: the tiles alone leave SMs idle at most orders (28 tiles at r = 448); split each
+  // tile's fold periods so that the CTAs fill the GPU in whole waves, within the partial buffer
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const int tm = Mp / OZ_TM, tn = Np / OZ_TN, tiles = tm * tn;
+  const int periods = Kp / (OZ_KC * OZ_FOLD);
+  int ks = 1;
+  double best = 1e30;
+  for (int z = 1; z <= 8 && z <= periods && z * tiles <= OZ_MAX_SPLIT_CTAS; ++z) {
+    const double waves = (double)((tiles * z + sms - 1) / sms) / z + 0.02 * z;  // per unit of tile work
+    if (waves < best) {
+      best = waves;
+      ks = z;
+    }
+  }
+  const dim3 grid(tm, tn, ks);
+  const unsigned gr = (unsigned)(((int64_t)rp * rp + NT - 1) / NT);
   const dim3 gmA((unsigned)((rp + 31) / 32), (unsigned)((r + 63) / 64));
   const dim3 gmZ((unsigned)((r + 31) / 32), (unsigned)((r + 63) / 64));
   const unsigned gsA = (unsigned)(((int64_t)Mp * (Kp / 8) + NT - 1) / NT);
@@ -427,15 +539,17 @@ int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const 
   oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, H, 1, ldh, rp, r, Mp, Kp, OZ_TM, mx, ea, Ad, planeA);
   oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, Z, lds, 1, r, r, Np, Kp, OZ_TN, mx + Mp, fb, Bd, planeB);
   oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 1, s, Out, lds, rp,
-                                                       rp, 0);
+                                                               rp, 0, kpart);
+  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea, fb, Out, lds, rp, rp, 0);
   // pass 2: Out += Z G^T  (A(a, c) = Z[a + c lds], B(b, c) = G[b + c ldh]), rows a < r
   oz_max_kernel<<<counted(gmZ), NT, 0, strm>>>(st, Z, 1, lds, r, r, mx + 2 * (size_t)Mp);
   oz_max_kernel<<<counted(gmA), NT, 0, strm>>>(st, G, 1, ldh, rp, r, mx + 3 * (size_t)Mp);
   oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, Z, 1, lds, r, r, Mp, Kp, OZ_TM, mx + 2 * (size_t)Mp, ea, Ad, planeA);
   oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, G, 1, ldh, rp, r, Np, Kp, OZ_TN, mx + 3 * (size_t)Mp, fb, Bd, planeB);
   oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 2, s, Out, lds, r,
-                                                       rp, 1);
-  int launched = 10;
+                                                               rp, 1, kpart);
+  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea, fb, Out, lds, r, rp, 1);
+  int launched = ks > 1 ? 12 : 10;
   if (omega) {
     const int64_t E = (int64_t)rp * rp;
     const unsigned g = (unsigned)std::min<int64_t>((E + NT - 1) / NT, OZ_OMEGA_CTAS);
