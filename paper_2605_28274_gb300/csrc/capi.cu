@@ -125,7 +125,8 @@ struct sylv_handle {
   DevState* st_host = nullptr;  // pinned, 2 slots
   double* hist = nullptr;
   int hist_cap = 0;
-  double* spart = nullptr;  // self-Gram partials
+  double* spart = nullptr;   // self-Gram partials
+  double* spart2 = nullptr;  // the same, written by a fused CholQR pass that reads spart
   double* psmall = nullptr;
   // mixed mode: hi/lo float pairs of H, G and of the small operand (8 bytes per entry)
   double *Hs = nullptr, *Gs = nullptr, *Zs = nullptr;
@@ -144,6 +145,7 @@ struct sylv_handle {
   // the two block Krylov bases run on their own streams, ahead of the small side
   cudaStream_t sbas[2] = {nullptr, nullptr};
   double *gpart_s[2] = {nullptr, nullptr}, *spart_s[2] = {nullptr, nullptr}, *Hc_s[2] = {nullptr, nullptr};
+  double* spart2_s[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_bas[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, ev_small[8] = {};
   // last solve
   int method = M_NONE;
@@ -415,9 +417,11 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   TRY(alloc_solve(h, &h->spart, (size_t)(4 * sms) * 64));
+  TRY(alloc_solve(h, &h->spart2, (size_t)(4 * sms) * 64));
   for (int i = 0; i < nsides(h); ++i) {
     TRY(alloc_solve(h, &h->gpart_s[i], (size_t)(4 * sms) * maxb * s * s));
     TRY(alloc_solve(h, &h->spart_s[i], (size_t)(4 * sms) * 64));
+    TRY(alloc_solve(h, &h->spart2_s[i], (size_t)(4 * sms) * 64));
     TRY(alloc_solve(h, &h->Hc_s[i], (size_t)maxb * s * s));
   }
   const int64_t gtiles = (h->lds + 31) / 32;
@@ -497,12 +501,10 @@ void setup_qr(sylv_handle* h, int si) {
   a.setup = 1;
   a.pass = 1;
   a.ldh = 0;
-  sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
-  nc = sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, h->spart);
+  nc = sylv::launch_cholscale<T>(h->stream, h->st, h->spart, nc, a, sd.n, V0, h->spart2, nullptr);
   a.pass = 2;
   a.Rout = sd.RQR;
-  sylv::launch_chol(h->stream, h->st, h->spart, nc, a);
-  sylv::launch_scale<T>(h->stream, h->st, sd.n, s, V0, (const T*)sd.RinvT, nullptr, sd.ob.G ? sd.ob.mx : nullptr);
+  sylv::launch_cholscale<T>(h->stream, h->st, h->spart2, nc, a, sd.n, V0, nullptr, sd.ob.G ? sd.ob.mx : nullptr);
   if (sd.ob.G) sylv::launch_ob_split_basis(h->stream, h->st, sd.n, s, (const double*)V0, 0, sd.ob);
 }
 
@@ -582,15 +584,15 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   a.RinvT = sd.RinvT;
   a.factor_is_float = h->mixed ? 1 : 0;
   a.pass = 1;
-  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
+  // each CholQR pass is one launch: Cholesky of the s x s Gram (in every CTA) and the scaling
+  double* spart2 = h->spart2_s[si];
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1) + ns * s,
-       nc = sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, spart));
+       nc = sylv::launch_cholscale<T>(st, h->st, spart, nc, a, n, Y, spart2, nullptr));
   a.pass = 2;
   a.Hsub = sd.H + (int64_t)(q + 1) * s + (int64_t)q * s * ldh;
   a.Hsup = lanczos ? sd.H + (int64_t)q * s + (int64_t)(q + 1) * s * ldh : nullptr;
-  PROF(h, KC_CHOL, 0.0, 0.0, sylv::launch_chol(st, h->st, spart, nc, a));
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1),
-       sylv::launch_scale<T>(st, h->st, n, s, Y, (const T*)sd.RinvT, nullptr, ob ? sd.ob.mx : nullptr));
+       sylv::launch_cholscale<T>(st, h->st, spart2, nc, a, n, Y, nullptr, ob ? sd.ob.mx : nullptr));
   if (ob)
     PROF(h, KC_BSPLIT, 2.0 * ns * b + 28.0 * ns, 0.0,
          sylv::launch_ob_split_basis(st, h->st, n, s, (const double*)Y, (q + 1) * s, sd.ob));
@@ -1135,12 +1137,10 @@ void qr8_impl(sylv_handle* h, int64_t n, double* Y, double* Rout) {
   a.setup = 1;
   a.pass = 1;
   int nc = sylv::launch_selfgram<double>(h->stream, h->st_sk, n, SKK, Y, h->spart);
-  sylv::launch_chol(h->stream, h->st_sk, h->spart, nc, a);
-  nc = sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, h->spart);
+  nc = sylv::launch_cholscale<double>(h->stream, h->st_sk, h->spart, nc, a, n, Y, h->spart2, nullptr);
   a.pass = 2;
   a.Rout = Rout;
-  sylv::launch_chol(h->stream, h->st_sk, h->spart, nc, a);
-  sylv::launch_scale<double>(h->stream, h->st_sk, n, SKK, Y, RinvT, nullptr);
+  sylv::launch_cholscale<double>(h->stream, h->st_sk, h->spart2, nc, a, n, Y, nullptr, nullptr);
 }
 
 // Enqueues the ||R||_F estimate and its certified bound on h->stream; in SYLV_MIXED also leaves

@@ -114,6 +114,14 @@ struct CholArgs {
   int setup;          // QR of C1/C2: any loss of rank is a breakdown
 };
 void launch_chol(cudaStream_t, DevState*, const double* self_partial, int ncta, const CholArgs&);
+// One CholQR pass in one launch: Cholesky of the s x s Gram summed from partial_in (ncta_in
+// partials, as launch_chol) in every CTA, then Y <- Y R^{-1} over the n x s block, with the
+// optional per-CTA partial Y^T Y of the result into partial_out (a different buffer from
+// partial_in, at least 2 x SMs x s^2 doubles) and column maxima into colmax.  The factors are
+// stored as by launch_chol.  Returns the number of CTAs (the partial_out count).
+template <typename T>
+int launch_cholscale(cudaStream_t, DevState*, const double* partial_in, int ncta_in, const CholArgs&, int64_t n, T* Y,
+                     double* partial_out, unsigned long long* colmax);
 
 // Copy a column-major n x s float64 matrix into block-row-major factor storage.
 template <typename T>

@@ -105,10 +105,16 @@ __device__ __forceinline__ void block_reduce_tile(A (&acc)[S][S], double* out, d
 }
 
 // ---------------------------------------------------------------- SpMM
-// One thread per (row, column t): Y[row][t] = sum_p val[p] X[col[p]][t] (- sum_u Xprev[row][u] M[u][t]).
-// The s threads of a row read the same (col, val) pair (broadcast) and s adjacent
-// values of the gathered row (one sector).  colmax (float64 only, may be null): the column
-// maxima of |Y| as IEEE bits, combined with atomicMax (the digit split of the tensor-core basis).
+// Y = A X (- Xprev M, the three-term Lanczos term) over an s-wide block, one thread per row
+// computing its s outputs.  A CTA of NT rows first stages its slice of the CSR arrays (column
+// indices and values, read once and coalesced) in shared memory; each thread then walks its
+// row there, gathers the s-wide rows of X as 16-byte vectors (X is small enough to stay in L2)
+// and keeps s accumulators.  The s x s block M of the Lanczos term is staged in shared memory.
+// A slice longer than SPMM_STAGE entries (long rows) is read from global memory instead.
+// colmax (float64 only, may be null): the column maxima of |Y| as IEEE bits, combined with
+// atomicMax (the digit split of the tensor-core basis).
+constexpr int SPMM_STAGE = 3584;  // staged CSR entries per CTA (42 KB with float64 values: under the 48 KB static limit)
+
 template <typename T, int S>
 __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n, const int32_t* __restrict__ rp,
                                                   const int32_t* __restrict__ ci, const T* __restrict__ val,
@@ -116,25 +122,62 @@ __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n,
                                                   const T* __restrict__ Xprev, const double* __restrict__ M,
                                                   int64_t ldm, unsigned long long* __restrict__ colmax) {
   if (stopped(st)) return;
-  const int64_t gid = (int64_t)blockIdx.x * NT + threadIdx.x;
-  const int64_t row = gid / S;
-  const int t = (int)(gid - row * S);
-  using A = typename AccOf<T>::type;
-  A acc = 0;
-  if (row < n) {
-    const int p0 = __ldg(rp + row), p1 = __ldg(rp + row + 1);
-    for (int p = p0; p < p1; ++p) acc += (A)__ldg(val + p) * (A)__ldg(X + (int64_t)__ldg(ci + p) * S + t);
-    if (Xprev != nullptr) {
-#pragma unroll
-      for (int u = 0; u < S; ++u) acc -= (A)__ldg(Xprev + row * S + u) * (A)M[u + (int64_t)t * ldm];
+  __shared__ int32_t s_ci[SPMM_STAGE];
+  __shared__ T s_val[SPMM_STAGE];
+  __shared__ double s_m[S * S];
+  __shared__ unsigned long long smx[S];
+  const int64_t r0 = (int64_t)blockIdx.x * NT;
+  const int64_t r1 = min(n, r0 + NT);
+  const int64_t row = r0 + threadIdx.x;
+  const int32_t p_lo = __ldg(rp + r0), p_hi = __ldg(rp + r1);
+  const bool staged = p_hi - p_lo <= SPMM_STAGE;
+  if (staged)
+    for (int32_t p = p_lo + (int32_t)threadIdx.x; p < p_hi; p += NT) {
+      s_ci[p - p_lo] = __ldg(ci + p);
+      s_val[p - p_lo] = __ldg(val + p);
     }
-    Y[row * S + t] = (T)acc;
+  if (Xprev != nullptr && threadIdx.x < S * S) s_m[threadIdx.x] = M[threadIdx.x % S + (int64_t)(threadIdx.x / S) * ldm];
+  if (colmax != nullptr && threadIdx.x < S) smx[threadIdx.x] = 0;
+  __syncthreads();
+  using A = typename AccOf<T>::type;
+  A acc[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) acc[t] = 0;
+  if (row < n) {
+    const int32_t q0 = __ldg(rp + row), q1 = __ldg(rp + row + 1);
+    T x[S];
+    if (staged) {
+      for (int32_t p = q0 - p_lo; p < q1 - p_lo; ++p) {
+        ld_row_ro<T, S>(X + (int64_t)s_ci[p] * S, x);
+        const A v = (A)s_val[p];
+#pragma unroll
+        for (int t = 0; t < S; ++t) acc[t] += v * (A)x[t];
+      }
+    } else {
+      for (int32_t p = q0; p < q1; ++p) {
+        ld_row_ro<T, S>(X + (int64_t)__ldg(ci + p) * S, x);
+        const A v = (A)__ldg(val + p);
+#pragma unroll
+        for (int t = 0; t < S; ++t) acc[t] += v * (A)x[t];
+      }
+    }
+    if (Xprev != nullptr) {
+      ld_row_ro<T, S>(Xprev + row * S, x);
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+#pragma unroll
+        for (int u = 0; u < S; ++u) acc[t] -= (A)x[u] * (A)s_m[u + t * S];
+    }
+    T y[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) y[t] = (T)acc[t];
+    st_row<T, S>(Y + row * S, y);
   }
   if (colmax != nullptr) {
-    __shared__ unsigned long long smx[S];
-    if (threadIdx.x < S) smx[threadIdx.x] = 0;
-    __syncthreads();
-    if (row < n) atomicMax(&smx[t], (unsigned long long)__double_as_longlong(fabs((double)acc)));
+    if (row < n) {
+#pragma unroll
+      for (int t = 0; t < S; ++t) atomicMax(&smx[t], (unsigned long long)__double_as_longlong(fabs((double)acc[t])));
+    }
     __syncthreads();
     if (threadIdx.x < S && smx[threadIdx.x]) atomicMax(colmax + threadIdx.x, smx[threadIdx.x]);
   }
@@ -406,9 +449,11 @@ __global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n
 // (upper R, positive diagonal); a pivot <= (delta nu)^2 on pass 1 is a partial loss
 // of rank (breakdown).  Writes R^{-1} for the scale kernel and, on pass 2,
 // H_{j+1,j} = R2 R1.
-__global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __restrict__ partial, int ncta,
-                                                  CholArgs a) {
-  if (stopped(st)) return;
+// CTA-level: every CTA that calls it computes the same factors (same inputs, same order of
+// operations); `writer` CTAs also store them.  Leaves R^{-1} in Ri_out (shared memory) and
+// returns 1 when the block is to be scaled (0 after a breakdown or a non-finite value).
+__device__ int chol_block(DevState* st, const double* __restrict__ partial, int ncta, const CholArgs& a, bool writer,
+                          double* Ri_out) {
   __shared__ double G[64], R[64], Ri[64], sh[32];
   __shared__ double gsum[NT];
   const int s = a.s, E = s * s;
@@ -553,19 +598,97 @@ __global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __
   }
   __syncthreads();
   const int e = threadIdx.x;
-  if (out_sh == 0 || e >= E) return;
-  a.Rinv[e] = Ri[e];
-  if (a.factor_is_float)
-    ((float*)a.RinvT)[e] = (float)Ri[e];
-  else
-    ((double*)a.RinvT)[e] = Ri[e];
-  if (a.pass == 1) {
-    a.R1[e] = R[e];
-  } else {
-    const int i = e % s, j = e / s;
-    if (a.Hsub) a.Hsub[i + j * a.ldh] = Pm[e];
-    if (a.Hsup) a.Hsup[j + i * a.ldh] = Pm[e];
-    if (a.Rout) a.Rout[e] = Pm[e];
+  const int out = out_sh;
+  if (e < 64) Ri_out[e] = Ri[e];
+  if (writer && out != 0 && e < E) {
+    a.Rinv[e] = Ri[e];
+    if (a.factor_is_float)
+      ((float*)a.RinvT)[e] = (float)Ri[e];
+    else
+      ((double*)a.RinvT)[e] = Ri[e];
+    if (a.pass == 1) {
+      a.R1[e] = R[e];
+    } else {
+      const int i = e % s, j = e / s;
+      if (a.Hsub) a.Hsub[i + j * a.ldh] = Pm[e];
+      if (a.Hsup) a.Hsup[j + i * a.ldh] = Pm[e];
+      if (a.Rout) a.Rout[e] = Pm[e];
+    }
+  }
+  __syncthreads();
+  return out;
+}
+
+__global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __restrict__ partial, int ncta,
+                                                  CholArgs a) {
+  if (stopped(st)) return;
+  __shared__ double Ri[64];
+  chol_block(st, partial, ncta, a, true, Ri);
+}
+
+// One CholQR pass in one launch: every CTA forms the s x s Gram from the partials of the
+// previous kernel and factors it (chol_block: the same factors in every CTA; CTA 0 stores
+// them), then scales its rows, Y <- Y R^{-1}, with the optional partial Y^T Y of the result
+// (SELF, into partial_out, which must not be partial_in) and column maxima (colmax).
+template <typename T, int S, bool SELF>
+__global__ void __launch_bounds__(NT) cholscale_kernel(DevState* st, const double* __restrict__ partial_in,
+                                                       int ncta_in, CholArgs a, int64_t n, T* __restrict__ Y,
+                                                       double* __restrict__ partial_out,
+                                                       unsigned long long* __restrict__ colmax) {
+  if (stopped(st)) return;
+  __shared__ double Rid[64];
+  __shared__ T rs[S * S];
+  __shared__ double sh[(NT / 32) * S * S];
+  __shared__ unsigned long long smx[S];
+  if (!chol_block(st, partial_in, ncta_in, a, blockIdx.x == 0, Rid)) return;  // uniform in the CTA
+  if (threadIdx.x < S * S) rs[threadIdx.x] = (T)Rid[(threadIdx.x % S) + (threadIdx.x / S) * S];
+  if (threadIdx.x < S) smx[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long zmax[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) zmax[t] = 0;
+  using A = typename AccOf<T>::type;
+  A acc[S][S];
+  if constexpr (SELF) {
+#pragma unroll
+    for (int u = 0; u < S; ++u)
+#pragma unroll
+      for (int t = 0; t < S; ++t) acc[u][t] = 0;
+  }
+  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
+    T y[S], z[S];
+    ld_row<T, S>(Y + row * S, y);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      T v = 0;
+#pragma unroll
+      for (int u = 0; u <= t; ++u) v += y[u] * rs[u + t * S];
+      z[t] = v;
+    }
+    st_row<T, S>(Y + row * S, z);
+    if constexpr (SELF) {
+#pragma unroll
+      for (int u = 0; u < S; ++u)
+#pragma unroll
+        for (int t = 0; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];
+    }
+    if (colmax != nullptr) {
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        zmax[t] = max(zmax[t], (unsigned long long)__double_as_longlong(fabs((double)z[t])));
+    }
+  }
+  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial_out + (int64_t)blockIdx.x * S * S, sh);
+  if (colmax != nullptr) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      unsigned long long v = zmax[t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if ((threadIdx.x & 31) == 0 && v) atomicMax(&smx[t], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < S && smx[threadIdx.x]) atomicMax(colmax + threadIdx.x, smx[threadIdx.x]);
   }
 }
 
@@ -611,8 +734,7 @@ template <typename T>
 void launch_spmm(cudaStream_t strm, const DevState* st, int64_t n, int s, const int32_t* rp, const int32_t* ci,
                  const T* val, const T* X, T* Y, const T* Xprev, const double* M, int64_t ldm,
                  unsigned long long* colmax) {
-  const int64_t threads = n * s;
-  const int grid = (int)((threads + NT - 1) / NT);
+  const int grid = (int)((n + NT - 1) / NT);  // one thread per row
   if (grid == 0) return;
 #define CASE(SV) \
   case SV: spmm_kernel<T, SV><<<counted(grid), NT, 0, strm>>>(st, n, rp, ci, val, X, Y, Xprev, M, ldm, colmax); break;
@@ -696,6 +818,25 @@ void launch_chol(cudaStream_t strm, DevState* st, const double* self_partial, in
 }
 
 template <typename T>
+int launch_cholscale(cudaStream_t strm, DevState* st, const double* partial_in, int ncta_in, const CholArgs& a,
+                     int64_t n, T* Y, double* partial_out, unsigned long long* colmax) {
+  // two CTAs per SM: every CTA also reduces the ncta_in partials and factors the s x s Gram
+  const int grid = grid_for(n, NT, 2 * num_sms());
+#define CASE(SV)                                                                                                    \
+  case SV:                                                                                                          \
+    if (partial_out)                                                                                                \
+      cholscale_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, partial_in, ncta_in, a, n, Y, partial_out,  \
+                                                                    colmax);                                        \
+    else                                                                                                            \
+      cholscale_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, partial_in, ncta_in, a, n, Y, nullptr,     \
+                                                                     colmax);                                       \
+    break;
+  switch (a.s) { SYLV_S_CASES(CASE) }
+#undef CASE
+  return grid;
+}
+
+template <typename T>
 void launch_pack(cudaStream_t strm, int64_t n, int s, const double* Ccol, T* Vblk) {
   const int grid = (int)((n * s + NT - 1) / NT);
   if (grid == 0) return;
@@ -728,6 +869,8 @@ void launch_convert(cudaStream_t strm, int64_t count, const double* src, T* dst)
   template int launch_selfgram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, double*);               \
   template int launch_scale<T>(cudaStream_t, const DevState*, int64_t, int, T*, const T*, double*,              \
                                 unsigned long long*);                                                            \
+  template int launch_cholscale<T>(cudaStream_t, DevState*, const double*, int, const CholArgs&, int64_t, T*,    \
+                                   double*, unsigned long long*);                                                \
   template void launch_pack<T>(cudaStream_t, int64_t, int, const double*, T*);                                  \
   template void launch_unpack<T>(cudaStream_t, int64_t, int, int, const T*, int64_t, double*);                  \
   template void launch_convert<T>(cudaStream_t, int64_t, const double*, T*);
