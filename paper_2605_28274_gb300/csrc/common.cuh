@@ -42,8 +42,14 @@ struct DevState {
 
 constexpr int NT = 256;  // threads per CTA for the streaming kernels
 
+// The same answer in every thread of the CTA, which must all call it (every kernel does, as its
+// first statement).  Kernels on the two basis streams run while the small side (or the other
+// basis) writes the status word, so two threads of one CTA can read different values; a CTA
+// split between "stopped" and "running" would run its cooperative parts (shared-memory staging,
+// barriers, tensor-memory allocation, bulk copies issued by one thread) with threads missing.
 __device__ __forceinline__ bool stopped(const DevState* st) {
-  return st != nullptr && *((volatile const int*)&st->status) != ST_RUNNING;
+  const bool mine = st != nullptr && *((volatile const int*)&st->status) != ST_RUNNING;
+  return __syncthreads_or(mine ? 1 : 0) != 0;
 }
 
 // Deterministic block-wide sum of one double per thread (NT threads).

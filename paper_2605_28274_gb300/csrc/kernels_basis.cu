@@ -143,19 +143,37 @@ __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n,
   A acc[S];
 #pragma unroll
   for (int t = 0; t < S; ++t) acc[t] = 0;
+  // Guards (the operators are square, n x n, with CSR checked on the host): a row range outside
+  // the CTA's slice or a column index outside [0, n) is recorded in the status word (site 300,
+  // 301) and the entry is skipped, never dereferenced.
+  bool bad = false;
   if (row < n) {
     const int32_t q0 = __ldg(rp + row), q1 = __ldg(rp + row + 1);
     T x[S];
     if (staged) {
-      for (int32_t p = q0 - p_lo; p < q1 - p_lo; ++p) {
-        ld_row_ro<T, S>(X + (int64_t)s_ci[p] * S, x);
-        const A v = (A)s_val[p];
+      if (q0 < p_lo || q1 > p_hi || q1 < q0) {
+        bad = true;
+      } else {
+        for (int32_t p = q0 - p_lo; p < q1 - p_lo; ++p) {
+          const int32_t c = s_ci[p];
+          if (c < 0 || (int64_t)c >= n) {
+            bad = true;
+            continue;
+          }
+          ld_row_ro<T, S>(X + (int64_t)c * S, x);
+          const A v = (A)s_val[p];
 #pragma unroll
-        for (int t = 0; t < S; ++t) acc[t] += v * (A)x[t];
+          for (int t = 0; t < S; ++t) acc[t] += v * (A)x[t];
+        }
       }
     } else {
       for (int32_t p = q0; p < q1; ++p) {
-        ld_row_ro<T, S>(X + (int64_t)__ldg(ci + p) * S, x);
+        const int32_t c = __ldg(ci + p);
+        if (c < 0 || (int64_t)c >= n) {
+          bad = true;
+          continue;
+        }
+        ld_row_ro<T, S>(X + (int64_t)c * S, x);
         const A v = (A)__ldg(val + p);
 #pragma unroll
         for (int t = 0; t < S; ++t) acc[t] += v * (A)x[t];
@@ -172,6 +190,11 @@ __global__ void __launch_bounds__(NT) spmm_kernel(const DevState* st, int64_t n,
 #pragma unroll
     for (int t = 0; t < S; ++t) y[t] = (T)acc[t];
     st_row<T, S>(Y + row * S, y);
+  }
+  if (bad && st != nullptr) {
+    DevState* ws = const_cast<DevState*>(st);
+    ws->breakdown_where = staged ? 300 : 301;
+    atomicExch(&ws->status, (int)ST_BREAKDOWN);
   }
   if (colmax != nullptr) {
     if (row < n) {
