@@ -445,9 +445,7 @@ def max_over_ranks(x: float, dist=None) -> float:
 # of one ncu capture of that kernel
 NCU_DRAM_PER_ALGORITHMIC = {
     ("gram", "fp64", False): (318.5, 318.8, "profiles/gram_update_fp64_convdiff64x48_s4.md"),
-    ("gram", "fp64", True): (788.3, 436.2, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
-    # the update class alternates the full (7 planes) and the second, two-plane update of a step
-    ("update", "fp64", True): (840.9 + 250.3, 2 * 444.6, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
+    # the tensor-core kernels (FP16 digit planes): entries return with their ncu capture
 }
 
 
@@ -546,7 +544,7 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "kernel": dname, "peak_src": f"{pk['src']} HBM copy",
                 "bytes_src": "algorithmic: the float64 basis (8 B per element) and the block Y, each read once; "
-                             "the kernel reads the basis as seven BF16 digit planes (14 B per element)"}
+                             "the kernel reads the basis as five FP16 digit planes (10 B per element)"}
     elif ai > ridge or dname.startswith("small_gemm"):
         roof = {"bound": "alu", "achieved": d["flops"] / (d["ms"] * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "kernel": dname,

@@ -84,9 +84,10 @@ typedef struct {
                           updates of eq. 3.4, 0 auto (tensor cores; CUDA cores if their digit planes do not
                           fit in device memory), 1 CUDA cores (float64 FMAs), 2 tensor cores (SYLV_ENOMEM if
                           they do not fit).  The tensor-core form holds each basis block, once it is built,
-                          as seven BF16 planes of 8-bit digits in two layouts (28 bytes per basis element
-                          besides the 8 of float64) and splits the other operand the same way; the products
-                          are exact sums of digit products, rounded once to float64 (Ozaki scheme) */
+                          as five FP16 planes of 11-bit digits in two layouts (20 bytes per basis element
+                          besides the 8 of float64) and splits the other operand into eight planes of 7-bit
+                          digits; the products are exact sums of digit products, rounded once to float64
+                          (Ozaki scheme) */
   double stop_margin;  /* with the true-residual certificate on (SYLV_FP64 by default): the recurrence test of
                           Algorithms 4.1/4.2 stops at ||R^_k|| <= stop_margin * tol * ||R^_0|| (0: 0.4), so
                           that the certificate (sylv_info.true_rel_bound <= tol) holds at the first check.

@@ -439,7 +439,7 @@ int ensure_capacity(sylv_handle* h, int method, int maxb, int hist_need) {
     TRY(alloc_solve(h, &p, sylv::ozaki_scratch_bytes((int)ldh)));
     h->oz_scratch = p;
   }
-  // digit planes of the float64 Arnoldi bases (twice 14 bytes per basis element per side);
+  // digit planes of the float64 Arnoldi bases (twice 10 bytes per basis element per side);
   // zero-filled once, so that padding rows and columns hold finite digits
   h->ob_unavailable = false;
   if (want_ob) {
@@ -509,9 +509,9 @@ void setup_qr(sylv_handle* h, int si) {
 }
 
 // Digit planes of the basis in the second BCGS2 update Y2 = Y1 - V H2.  Y1 is already orthogonal
-// to V up to rounding, so |H2| ~ eps ||Y||: the basis's top two digit planes (16 bits) leave an
-// error below 2^-17 of that correction, far under the float64 rounding of Y2 -- the pass reads
-// 4 bytes per basis element instead of 14.  The Gram products and the first update use all 7.
+// to V up to rounding, so |H2| ~ eps ||Y||: the basis's top two digit planes (22 bits) leave an
+// error below 2^-23 of that correction, far under the float64 rounding of Y2 -- the pass reads
+// 4 bytes per basis element instead of 10.  The Gram products and the first update use all 5.
 constexpr int kReorthPlanes = 2;
 
 // One block Lanczos (lanczos=true) or BCGS2 block Arnoldi step on side si:
@@ -562,7 +562,7 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
            sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1, false));
       PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
            nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr, !last,
-                                       last ? kReorthPlanes : 7));
+                                       last ? kReorthPlanes : 5));
       continue;
     }
     PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));
@@ -594,7 +594,7 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
   PROF(h, KC_SCALE, 2.0 * ns * b, ns * (s + 1),
        sylv::launch_cholscale<T>(st, h->st, spart2, nc, a, n, Y, nullptr, ob ? sd.ob.mx : nullptr));
   if (ob)
-    PROF(h, KC_BSPLIT, 2.0 * ns * b + 28.0 * ns, 0.0,
+    PROF(h, KC_BSPLIT, 2.0 * ns * b + 20.0 * ns, 0.0,
          sylv::launch_ob_split_basis(st, h->st, n, s, (const double*)Y, (q + 1) * s, sd.ob));
   h->prof_stream = nullptr;
 }

@@ -20,7 +20,7 @@ inline G counted(G grid) {
 }
 
 // ---------------------------------------------------------------- float64 basis products on the tensor cores
-// (kernels_obasis.cu) The Arnoldi basis of one side as seven BF16 planes of 8-bit digits, in a
+// (kernels_obasis.cu) The Arnoldi basis of one side as five FP16 planes of 11-bit digits, in a
 // Gram layout and an update layout, plus the digits of the block being orthogonalised (Y) and
 // of the coefficient block, and the column exponents.  One allocation of ob_side_bytes().
 struct ObSide {
@@ -49,7 +49,7 @@ void launch_ob_split_basis(cudaStream_t, const DevState*, int64_t n, int s, cons
 int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Y, const ObSide&, double* partial);
 // Y -= V Hc over the first js basis columns (Hc: js x s, the layout launch_reduce_H writes),
 // with the optional per-CTA partial Y^T Y of the result and, with ymax, the column maxima of
-// the result into mx[8, 16); V enters through its leading `planes` digit planes (7: all).
+// the result into mx[8, 16); V enters through its leading `planes` digit planes (5: all).
 // Returns the number of CTAs.
 int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
                      double* self_partial, bool ymax, int planes);

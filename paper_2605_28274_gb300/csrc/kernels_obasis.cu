@@ -5,33 +5,36 @@
 // each twice per step in block classical Gram-Schmidt -- do 2 s flops per basis element they
 // read.  GB300 executes float64 FMAs at 1/64 of its FP32 rate, so on CUDA cores those kernels
 // are bound by the FP64 pipe at about a sixth of the memory bandwidth.  Here the basis is also
-// held, written once per block when the block is made, as seven BF16 planes of integer digits
+// held, written once per block when the block is made, as five FP16 planes of 11-bit integer
+// digits (FP16 holds every integer up to 2^11 exactly):
 //
-//   v = 2^{e_c} sum_{p=0..6} d_p 2^{-8(p+1)},   d_p in [-128, 128]
+//   v = 2^{e_c} sum_{p=0..4} a_p 2^{-11(p+1)},   a_p in [-1024, 1024]
 //
 // (2^{e_c - 1}: the power of two above the column's largest |v|, so the digits are v rounded to
-// 55 bits of its largest entry), and the other operand -- the block Y, or the coefficient
-// block with the basis column scales folded in -- is split the same way for every product.
-// One MMA per basis digit plane p takes all seven digit planes q of the other operand at once
-// (MMA N = 7 s, padded to a multiple of 16); every pair (p, q) accumulates integers in its own
-// FP32 columns of tensor memory.  A pair's sum over 256 values of k is at most 2^14 * 256 =
-// 2^22 in magnitude, so FP32 holds it exactly; every 256 values of k the pairs with p + q <= 6
-// are added, as integers, into three int64 fixed-point words per output (levels 0-2, 3-5, 6).
-// The result is the exact product of the 55-bit operands, rounded once to float64; the
-// dropped pairs p + q > 6 weigh less than 2^-60 (scale of v)(scale of the other operand)
-// per term.  (Ozaki scheme I: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; its
-// tensor-core form: Mukunoki, Ozaki, Ogita, Imamura, ICCS 2020.)
+// 55 bits of its largest entry).  The other operand -- the block Y, or the coefficient block
+// with the basis column scales folded in -- is split for every product into eight planes of
+// 7-bit digits b_q in [-64, 64] (56 bits), also FP16.  One MMA per basis digit plane p takes
+// all eight digit planes q of the other operand at once (MMA N = 8 s, padded to a multiple of
+// 16); every pair (p, q) accumulates integers in its own FP32 columns of tensor memory.  A
+// pair's sum over 128 values of k is at most 2^10 * 2^6 * 128 = 2^23 in magnitude, so FP32
+// holds it exactly; every 128 values of k the pairs of weight w = 11 p + 7 q <= 55 are added,
+// as integers, into three int64 fixed-point words per output (w in [0, 20], [21, 41], [42, 55]).
+// The result is the exact product of the rounded operands, rounded once to float64; the
+// dropped pairs weigh less than 2^-58 (scale of v)(scale of the other operand) per term.
+// (Ozaki scheme I: Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012; its tensor-core
+// form: Mukunoki, Ozaki, Ogita, Imamura, ICCS 2020.)  Ten bytes per basis element: 11 of
+// FP16's 16 bits carry digits, where 8-bit digits in BF16 carry 8 (seven planes, 14 bytes).
 //
-// Layouts (BF16 elements).  A tile holds T rows x 32 values of k in the canonical no-swizzle
+// Layouts (FP16 elements).  A tile holds T rows x 32 values of k in the canonical no-swizzle
 // K-major layout of the tcgen05 shared-memory descriptor: 8-row x 16-byte core matrices, the
 // four core matrices of an 8-row group adjacent.  The basis is stored twice, so that each
 // kernel loads one chunk of a digit plane with one 1-D bulk copy (cp.async.bulk):
 //   Gram layout   (tile rows = basis columns m, k = basis rows i): tile (i / 32, m / 128)
 //   update layout (tile rows = basis rows i, k = basis columns m): tile (m / 32, i / 128)
-// Each kernel reads 14 bytes per basis element instead of 8 (the second update of a step, whose
+// Each kernel reads 10 bytes per basis element instead of 8 (the second update of a step, whose
 // coefficients are at rounding level, only the two leading planes: 4 bytes), and is bound by
 // memory bandwidth instead of the FP64 pipe.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -44,31 +47,45 @@ namespace sylv {
 
 namespace {
 
-constexpr int OB_P = 7;           // digits per operand
-constexpr int OB_LMAX = 6;        // pairs p + q <= OB_LMAX are folded
+constexpr int OB_PV = 5;          // digit planes of the basis
+constexpr int OB_WV = 11;         // bits per basis digit
+constexpr int OB_PY = 8;          // digit planes of the other operand
+constexpr int OB_WY = 7;          // bits per digit of the other operand
+constexpr int OB_WMAX = 55;       // pairs of weight 11 p + 7 q <= OB_WMAX are folded
 constexpr int OB_TM = 128;        // MMA M: tile rows
 constexpr int OB_KC = 32;         // k per chunk
-constexpr int OB_FOLD = 8;        // chunks per fold (256 values of k)
-constexpr int OB_STAGES = 3;      // chunks in flight for full 128-row tiles (more, smaller ones for narrow tiles)
+constexpr int OB_FOLD = 4;        // chunks per fold (128 values of k)
+constexpr int OB_STAGES = 4;      // chunks in flight for full 128-row tiles (more, smaller ones for narrow tiles)
 constexpr int OB_MAXSTAGES = 16;
 constexpr int OB_FOLD_THREADS = 128;  // warps 0-3 fold: TMEM lanes 0..127, one per tile row
 constexpr int OB_THREADS = OB_FOLD_THREADS + 64;  // + warp 4: bulk copies, warp 5: MMAs
-constexpr int OB_ATILE = OB_TM * OB_KC;  // BF16 elements of one basis digit tile (8 KB)
+constexpr int OB_ATILE = OB_TM * OB_KC;  // FP16 elements of one basis digit tile (8 KB)
 constexpr int OB_WAIT_ITERS = 1 << 20;
 constexpr int OB_EXP_BAD = 1 << 20;      // exponent sentinel: a non-finite value
 
+// Largest digit plane q of the other operand folded with basis plane p.
+__host__ __device__ constexpr int ob_qmax(int p) {
+  return (OB_WMAX - OB_WV * p) / OB_WY < OB_PY - 1 ? (OB_WMAX - OB_WV * p) / OB_WY : OB_PY - 1;
+}
+static_assert(OB_WV * (OB_PV - 1) <= OB_WMAX, "every basis plane meets at least one digit of the other operand");
+static_assert((1 << (OB_WV - 1)) * (1 << (OB_WY - 1)) * (OB_FOLD * OB_KC) <= (1 << 23),
+              "a fold period's pair sums stay exact in FP32");
+
 template <int S>
 struct ObShape {
-  static constexpr int NP = (OB_P * S + 15) / 16 * 16;  // MMA N: digit columns of the other operand
-  static constexpr int BTILE = NP * OB_KC;              // BF16 elements of one of its tiles
-  static constexpr int NBUF = 2 * OB_P * NP <= 512 ? 2 : 1;  // accumulator buffers
-  static constexpr int TMEM_COLS = NBUF * OB_P * NP <= 256 ? 256 : 512;
+  static constexpr int NP = (OB_PY * S + 15) / 16 * 16;  // MMA N: digit columns of the other operand
+  static constexpr int BTILE = NP * OB_KC;               // FP16 elements of one of its tiles
+  static constexpr int NBUF = 2 * OB_PV * NP <= 512 ? 2 : 1;  // accumulator buffers
+  static constexpr int TMEM_COLS = NBUF * OB_PV * NP <= 256 ? 256 : 512;
   static constexpr uint32_t ABYTES = OB_ATILE * 2;
   static constexpr uint32_t BBYTES = BTILE * 2;
-  static constexpr size_t STAGE = (size_t)OB_P * ABYTES + BBYTES;
+  static constexpr size_t STAGE = (size_t)OB_PV * ABYTES + BBYTES;
   static constexpr size_t REGION = OB_STAGES * STAGE;  // stage slots
   // + 8 KB: an MMA reads all 128 rows of a plane's tile, past a narrow slot's end
   static constexpr size_t SMEM = REGION + 8192 + 1024 + 512;
+  // a 32-column TMEM load of the last plane of the last buffer stays inside the allocation
+  static_assert((NBUF - 1) * OB_PV * NP + (OB_PV - 1) * NP + (((ob_qmax(OB_PV - 1) + 1) * S + 31) / 32) * 32 <=
+                    TMEM_COLS, "tensor-memory loads stay in the allocation");
 };
 
 __device__ __forceinline__ uint32_t ob_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -83,9 +100,9 @@ __device__ __forceinline__ uint64_t ob_sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+// Instruction descriptor of kind::f16: D FP32, A and B FP16 (type field 0), both K-major, M x N.
 constexpr uint32_t ob_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // Offset of element (row i, k) inside a T x 32 tile.
@@ -95,24 +112,28 @@ __device__ __forceinline__ int ob_cm(int i, int k) {
 
 // e = 2 + floor(log2 m) for the IEEE bits m of a non-negative double (0 for zero or
 // subnormal, OB_EXP_BAD for a non-finite value): every |x| <= m satisfies |x| < 2^{e-1}, one
-// bit of headroom that keeps every digit within [-128, 128].
+// bit of headroom that keeps the leading digit within the range of the others.
 __device__ __forceinline__ int ob_exponent(unsigned long long m) {
   if (m >= 0x7FF0000000000000ull) return OB_EXP_BAD;
   if (m < 0x0010000000000000ull) return 0;
   return (int)(m >> 52) - 1023 + 2;
 }
 
-// The seven digits of x 2^sc on the scale 2^e (|x 2^sc| < 2^{e-1}): N = round(x 2^{sc+56-e})
-// (ties away from zero; |N| <= 2^55), sliced from the top with rounding to nearest, so that
-// x 2^sc = 2^e sum_p d_p 2^{-8(p+1)} up to 2^{e-57}, every d_p in [-128, 128].  Integer
-// operations only (the FP64 pipe is narrow on this GPU); zero and subnormal x give zero digits.
-__device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P]) {
+// The D digits of W bits of x 2^sc on the scale 2^e (|x 2^sc| < 2^{e-1}): with B = D W,
+// N = round(x 2^{sc+B-e}) (ties away from zero; |N| <= 2^{B-1}), sliced from the top with
+// rounding to nearest, so that x 2^sc = 2^e sum_p d_p 2^{-W(p+1)} up to 2^{e-B-1}, every d_p
+// in [-2^{W-1}, 2^{W-1}].  Integer operations only (the FP64 pipe is narrow on this GPU); zero
+// and subnormal x give zero digits.
+template <int D, int W>
+__device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[D]) {
+  constexpr int B = D * W;
+  static_assert(B >= 54 && B <= 56, "the digits carry a float64 significand");
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   long long N = 0;
   if (ex != 0 && ex != 0x7FF && e != OB_EXP_BAD) {
     const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = ex - 1075 + sc + 56 - e;  // N = mant 2^sh; |x 2^sc| < 2^{e-1} gives sh <= 2
+    const int sh = ex - 1075 + sc + B - e;  // N = mant 2^sh; |x 2^sc| < 2^{e-1} gives sh <= B - 54
     unsigned long long u;
     if (sh >= 0)
       u = mant << sh;
@@ -123,24 +144,24 @@ __device__ __forceinline__ void ob_digits(double x, int sc, int e, int (&d)[OB_P
     N = (b >> 63) ? -(long long)u : (long long)u;
   }
 #pragma unroll
-  for (int p = 0; p < OB_P - 1; ++p) {
-    const int s = 8 * (OB_P - 1 - p);
+  for (int p = 0; p < D - 1; ++p) {
+    const int s = W * (D - 1 - p);
     const long long dp = (N + (1ll << (s - 1))) >> s;
     N -= dp << s;
     d[p] = (int)dp;
   }
-  d[OB_P - 1] = (int)N;
+  d[D - 1] = (int)N;
 }
 
-__device__ __forceinline__ __nv_bfloat16 ob_bf(int d) { return __float2bfloat16_rn((float)d); }  // |d| <= 128: exact
+__device__ __forceinline__ __half ob_h(int d) { return __int2half_rn(d); }  // |d| <= 1024: exact
 
 // Digits of the new basis block (columns col0 .. col0 + S - 1, row-major n x S) into both
 // layouts, and its column exponents into vexp.  One thread per basis row.
 template <int S>
 __global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Vb,
                                                        int col0, const unsigned long long* __restrict__ mx,
-                                                       int* __restrict__ vexp, __nv_bfloat16* __restrict__ G,
-                                                       __nv_bfloat16* __restrict__ U, int64_t plane, int MT, int IT) {
+                                                       int* __restrict__ vexp, __half* __restrict__ G,
+                                                       __half* __restrict__ U, int64_t plane, int MT, int IT) {
   if (stopped(st)) return;
   const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
   int e[S];
@@ -151,15 +172,15 @@ __global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64
   if (i >= n) return;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    int d[OB_P];
-    ob_digits(Vb[i * S + t], 0, e[t], d);
+    int d[OB_PV];
+    ob_digits<OB_PV, OB_WV>(Vb[i * S + t], 0, e[t], d);
     const int m = col0 + t;
     const int64_t og = ((i >> 5) * MT + (m >> 7)) * OB_ATILE + ob_cm(m & 127, (int)(i & 31));
     const int64_t ou = ((int64_t)(m >> 5) * IT + (i >> 7)) * OB_ATILE + ob_cm((int)(i & 127), m & 31);
 #pragma unroll
-    for (int p = 0; p < OB_P; ++p) {
-      G[p * plane + og] = ob_bf(d[p]);
-      U[p * plane + ou] = ob_bf(d[p]);
+    for (int p = 0; p < OB_PV; ++p) {
+      G[p * plane + og] = ob_h(d[p]);
+      U[p * plane + ou] = ob_h(d[p]);
     }
   }
 }
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64
 template <int S>
 __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Y,
                                                        const unsigned long long* __restrict__ mx, int* __restrict__ ey,
-                                                       __nv_bfloat16* __restrict__ YB) {
+                                                       __half* __restrict__ YB) {
   if (stopped(st)) return;
   constexpr int NP = ObShape<S>::NP;
   const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -182,10 +203,10 @@ __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64
   const int64_t base = (i >> 5) * (int64_t)(NP * OB_KC);
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    int d[OB_P];
-    ob_digits(Y[i * S + t], 0, e[t], d);
+    int d[OB_PY];
+    ob_digits<OB_PY, OB_WY>(Y[i * S + t], 0, e[t], d);
 #pragma unroll
-    for (int p = 0; p < OB_P; ++p) YB[base + ob_cm(p * S + t, (int)(i & 31))] = ob_bf(d[p]);
+    for (int q = 0; q < OB_PY; ++q) YB[base + ob_cm(q * S + t, (int)(i & 31))] = ob_h(d[q]);
   }
 }
 
@@ -197,7 +218,7 @@ __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64
 template <int S>
 __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int js, const double* __restrict__ Hc,
                                                        const int* __restrict__ vexp, int* __restrict__ eh,
-                                                       __nv_bfloat16* __restrict__ HB, unsigned long long* __restrict__ mx) {
+                                                       __half* __restrict__ HB, unsigned long long* __restrict__ mx) {
   if (stopped(st)) return;
   if (threadIdx.x < 16) mx[threadIdx.x] = 0;
   constexpr int NP = ObShape<S>::NP;
@@ -241,11 +262,11 @@ __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int j
     const int64_t base = (int64_t)(m >> 5) * (NP * OB_KC);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-      int d[OB_P];
+      int d[OB_PY];
       const double x = (m < js && sc != OB_EXP_BAD) ? Hc[(int64_t)m * S + t] : 0.0;
-      ob_digits(x, sc, esh[t], d);
+      ob_digits<OB_PY, OB_WY>(x, sc, esh[t], d);
 #pragma unroll
-      for (int p = 0; p < OB_P; ++p) HB[base + ob_cm(p * S + t, m & 31)] = ob_bf(d[p]);
+      for (int q = 0; q < OB_PY; ++q) HB[base + ob_cm(q * S + t, m & 31)] = ob_h(d[q]);
     }
   }
 }
@@ -263,12 +284,9 @@ __device__ __forceinline__ bool ob_wait(uint32_t bar, uint32_t phase) {
   return false;
 }
 
-// v: an FP32 pair sum, an exact integer with |v| <= 2^22 (at most 256 products of two digits
-// in [-128, 128]); its value from the bits of
-// v + 1.5 * 2^23 (exact in that range).
-__device__ __forceinline__ long long ob_int(uint32_t r) {
-  return (long long)(__float_as_int(__fadd_rn(__uint_as_float(r), 12582912.0f)) - 0x4B400000);
-}
+// v: an FP32 pair sum, an exact integer with |v| <= 2^23 (at most 128 products of a basis
+// digit in [-1024, 1024] and one in [-64, 64]); the conversion is exact.
+__device__ __forceinline__ long long ob_int(uint32_t r) { return (long long)__float2int_rn(__uint_as_float(r)); }
 
 __device__ __forceinline__ double ob_pow2(int x) {  // 2^x as a float64 (0 or inf outside the normal range)
   return x < -1022 ? 0.0 : (x > 1023 ? __longlong_as_double(0x7FF0000000000000ll)
@@ -277,10 +295,10 @@ __device__ __forceinline__ double ob_pow2(int x) {  // 2^x as a float64 (0 or in
 
 struct ObArgs {
   DevState* st;
-  const __nv_bfloat16* A;  // basis digit planes (Gram or update layout)
+  const __half* A;         // basis digit planes (Gram or update layout)
   int64_t plane;           // elements per plane
   int MT;                  // tiles per chunk row of that layout (Gram: Rp / 128, update: np / 128)
-  const __nv_bfloat16* B;  // digits of the other operand, one NP x 32 tile per chunk
+  const __half* B;         // digits of the other operand, one NP x 32 tile per chunk
   int64_t n;               // basis rows
   int js;                  // basis columns in use
   int cps;                 // Gram: chunks per k split (blockIdx.y)
@@ -289,7 +307,7 @@ struct ObArgs {
   double* out;             // Gram: partials [split][m S + t]; update: Y (row-major n x S)
   double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
   unsigned long long* ymax;  // update: column maxima of |result| as IEEE bits (nullptr: none)
-  int planes;              // basis digit planes used (the leading ones; OB_P: all)
+  int planes;              // basis digit planes used (the leading ones; OB_PV: all)
 };
 
 // GRAM: CTA (m tile, k split) writes the partial V^T Y of its rows.  Update: CTA c takes
@@ -377,8 +395,8 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         const int tile = i / nch, c = i - tile * nch;
         unsigned char* sa = base + stg * slot;
         unsigned char* sb = sa + a.planes * abytes;
-        const __nv_bfloat16* ga;
-        const __nv_bfloat16* gb;
+        const __half* ga;
+        const __half* gb;
         if (GRAM) {
           const int kc = c0 + c;
           ga = a.A + ((int64_t)kc * a.MT + mt) * OB_ATILE;
@@ -425,7 +443,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t sa = ob_smem_u32(base + stg * slot), sb = sa + a.planes * abytes;
-        const uint32_t dbase = tmem + (uint32_t)(buf * OB_P * NP);
+        const uint32_t dbase = tmem + (uint32_t)(buf * OB_PV * NP);
 #pragma unroll 1
         for (int p = 0; p < a.planes; ++p) {
 #pragma unroll
@@ -454,7 +472,9 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
     __syncwarp();
   } else {
     // ---------------------------------------------------------------- folds and results
-    long long w0[S], w1[S], w2[S];  // levels 0-2 (unit 2^-16), 3-5 (2^-40), 6 (2^-48) of the pair sums
+    // pair sums of weight w = 11 p + 7 q (unit 2^{-18-w}) in three words: w in [0, 20] (unit
+    // 2^-38), [21, 41] (2^-59), [42, 55] (2^-73)
+    long long w0[S], w1[S], w2[S];
     double acc[S][S];               // update: partial Y^T Y
     unsigned long long ym[S];       // update: column maxima of |result|
 #pragma unroll
@@ -472,13 +492,13 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * OB_P * NP);
+      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * OB_PV * NP);
 #pragma unroll
-      for (int p = 0; p < OB_P; ++p) {
-        constexpr int NCMAX = (OB_LMAX + 1) * S;
+      for (int p = 0; p < OB_PV; ++p) {
+        constexpr int NCMAX = OB_PY * S;
 #pragma unroll
         for (int cb = 0; cb < NCMAX; cb += 32) {
-          if (p < a.planes && cb < (OB_LMAX - p + 1) * S) {
+          if (p < a.planes && cb < (ob_qmax(p) + 1) * S) {
             uint32_t r[32];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -492,15 +512,15 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const int col = cb + j, q = col / S, t = col % S, L = p + q;
-              if (q <= OB_LMAX - p) {
+              const int col = cb + j, q = col / S, t = col % S, w = OB_WV * p + OB_WY * q;
+              if (q <= ob_qmax(p)) {
                 const long long v = ob_int(r[j]);
-                if (L <= 2)
-                  w0[t] += v << (8 * (2 - L));
-                else if (L <= 5)
-                  w1[t] += v << (8 * (5 - L));
+                if (w <= 20)
+                  w0[t] += v * (1ll << (20 - w));
+                else if (w <= 41)
+                  w1[t] += v * (1ll << (41 - w));
                 else
-                  w2[t] += v;
+                  w2[t] += v * (1ll << (55 - w));
               }
             }
           }
@@ -516,7 +536,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
 #pragma unroll
           for (int t = 0; t < S; ++t) {
             const int fe = a.eb[t];
-            double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
+            double v = fma((double)w0[t], 0x1p-38, fma((double)w1[t], 0x1p-59, (double)w2[t] * 0x1p-73));
             v = fe == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll) : v * ob_pow2(fe);
             y[t] = a.out[row * S + t] - v;
           }
@@ -545,7 +565,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
 #pragma unroll
         for (int t = 0; t < S; ++t) {
           const int fe = a.eb[t];
-          double v = fma((double)w0[t], 0x1p-32, fma((double)w1[t], 0x1p-56, (double)w2[t] * 0x1p-64));
+          double v = fma((double)w0[t], 0x1p-38, fma((double)w1[t], 0x1p-59, (double)w2[t] * 0x1p-73));
           // 2^{e+f} in two steps: each factor stays in the normal range
           v = (e == OB_EXP_BAD || fe == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
                                                     : v * ob_pow2(e) * ob_pow2(fe);
@@ -617,7 +637,7 @@ int ob_sms() {
 
 int ob_np(int64_t n) { return (int)((n + OB_TM - 1) / OB_TM * OB_TM); }
 int ob_rp(int R) { return (R + OB_TM - 1) / OB_TM * OB_TM; }
-int ob_NP(int s) { return (OB_P * s + 15) / 16 * 16; }
+int ob_NP(int s) { return (OB_PY * s + 15) / 16 * 16; }
 
 template <typename F>
 bool ob_for_each_kernel(F f) {
@@ -633,7 +653,7 @@ bool ob_for_each_kernel(F f) {
 
 size_t ob_side_bytes(int64_t n, int R, int s) {
   const size_t np = (size_t)ob_np(n), rp = (size_t)ob_rp(R), NPs = (size_t)ob_NP(s);
-  return 256 + 2 * (size_t)OB_P * np * rp * 2  // Gram and update layouts
+  return 256 + 2 * (size_t)OB_PV * np * rp * 2  // Gram and update layouts
          + np * NPs * 2 + rp * NPs * 2          // digits of Y and of the coefficient block
          + rp * sizeof(int) + 16 * sizeof(int)  // basis column exponents, ey, eh
          + 16 * sizeof(unsigned long long) + 1024;
@@ -650,8 +670,8 @@ void ob_carve(void* mem, int64_t n, int R, int s, ObSide& o) {
   o.np = (int64_t)np;
   o.rp = (int)rp;
   o.plane = (int64_t)(np * rp);
-  o.G = (uint16_t*)take((size_t)OB_P * np * rp * 2);
-  o.U = (uint16_t*)take((size_t)OB_P * np * rp * 2);
+  o.G = (uint16_t*)take((size_t)OB_PV * np * rp * 2);
+  o.U = (uint16_t*)take((size_t)OB_PV * np * rp * 2);
   o.YB = (uint16_t*)take(np * NPs * 2);
   o.HB = (uint16_t*)take(rp * NPs * 2);
   o.vexp = (int*)take(rp * sizeof(int));
@@ -672,8 +692,8 @@ void launch_ob_split_basis(cudaStream_t strm, const DevState* st, int64_t n, int
                            const ObSide& o) {
   if (n == 0) return;
   const unsigned gs = (unsigned)((n + NT - 1) / NT);
-  __nv_bfloat16* G = (__nv_bfloat16*)o.G;
-  __nv_bfloat16* U = (__nv_bfloat16*)o.U;
+  __half* G = (__half*)o.G;
+  __half* U = (__half*)o.U;
   const int MT = o.rp / OB_TM, IT = (int)(o.np / OB_TM);
 #define CASE(SV)                                                                                           \
   case SV:                                                                                                 \
@@ -693,10 +713,10 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
   ks = (kcn + cps - 1) / cps;  // no empty split
   ObArgs a{};
   a.st = st;
-  a.A = (const __nv_bfloat16*)o.G;
+  a.A = (const __half*)o.G;
   a.plane = o.plane;
   a.MT = o.rp / OB_TM;
-  a.B = (const __nv_bfloat16*)o.YB;
+  a.B = (const __half*)o.YB;
   a.n = n;
   a.js = js;
   a.cps = cps;
@@ -705,11 +725,11 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
   a.out = partial;
   a.self = nullptr;
   a.ymax = nullptr;
-  a.planes = OB_P;
+  a.planes = OB_PV;
   const dim3 grid((unsigned)mtv, (unsigned)ks);
 #define CASE(SV)                                                                                                 \
   case SV:                                                                                                       \
-    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, o.mx + 8, o.ey, (__nv_bfloat16*)o.YB);          \
+    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, o.mx + 8, o.ey, (__half*)o.YB);                  \
     ob_kernel<SV, true><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                              \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
@@ -723,10 +743,10 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   const int grid = std::min(itn, ob_sms());
   ObArgs a{};
   a.st = st;
-  a.A = (const __nv_bfloat16*)o.U;
+  a.A = (const __half*)o.U;
   a.plane = o.plane;
   a.MT = (int)(o.np / OB_TM);
-  a.B = (const __nv_bfloat16*)o.HB;
+  a.B = (const __half*)o.HB;
   a.n = n;
   a.js = js;
   a.cps = 0;
@@ -735,10 +755,10 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   a.out = Y;
   a.self = self_partial;
   a.ymax = ymax ? o.mx + 8 : nullptr;
-  a.planes = std::max(1, std::min(OB_P, planes));
+  a.planes = std::max(1, std::min(OB_PV, planes));
 #define CASE(SV)                                                                                              \
   case SV:                                                                                                    \
-    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__nv_bfloat16*)o.HB, o.mx);  \
+    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);          \
     ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
