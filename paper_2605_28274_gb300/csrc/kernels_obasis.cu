@@ -348,13 +348,19 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
     ntiles = (int)blockIdx.x < it ? (it - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     nch = (a.js + OB_KC - 1) / OB_KC;
   }
-  const int NI = ntiles * nch;
+  const uint32_t abytes = (uint32_t)rg * 512;  // per digit plane and chunk: the tile's row groups
+  // A stage holds G chunks: every stage costs a barrier round trip between the copy and MMA
+  // warps, and stages of 16 KB or less (the two-plane update, narrow Gram tiles) were measured
+  // to cap a CTA near 36 GB/s however many are in flight; 32 KB and more reach the copy rate.
+  const uint32_t cbytes = a.planes * abytes + Sh::BBYTES;  // one chunk: basis planes, then the other operand
+  const int G = a.planes * abytes <= 16384u ? 2 : 1;
+  const int nit = (nch + G - 1) / G;  // stages per tile
+  const int NI = ntiles * nit;
   const int npt = (nch + OB_FOLD - 1) / OB_FOLD;  // fold periods per tile
   const int NF = ntiles * npt;
-  const uint32_t abytes = (uint32_t)rg * 512;  // per digit plane and chunk: the tile's row groups
   // stage slots: a narrow tile (Gram, few basis columns) or fewer digit planes get more of them,
   // so that about the same number of bytes stays in flight
-  const uint32_t slot = a.planes * abytes + Sh::BBYTES;
+  const uint32_t slot = (uint32_t)G * cbytes;
   const int ns = min(OB_MAXSTAGES, (int)(Sh::REGION / slot));
 
   if (warp == 0) {
@@ -387,39 +393,41 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
       int i = 0;
       for (; i < NI; ++i) {
         const int stg = i % ns;
-        // the stage is free once the MMAs of its previous chunk are done
+        // the stage is free once the MMAs of its previous chunks are done
         if (i >= ns && !ob_wait(bempty + 8 * stg, (uint32_t)(i / ns - 1) & 1u)) {
           ok = false;
           break;
         }
-        const int tile = i / nch, c = i - tile * nch;
-        unsigned char* sa = base + stg * slot;
-        unsigned char* sb = sa + a.planes * abytes;
-        const __half* ga;
-        const __half* gb;
-        if (GRAM) {
-          const int kc = c0 + c;
-          ga = a.A + ((int64_t)kc * a.MT + mt) * OB_ATILE;
-          gb = a.B + (int64_t)kc * Sh::BTILE;
-        } else {
-          const int it = (int)blockIdx.x + tile * (int)gridDim.x;
-          ga = a.A + ((int64_t)c * a.MT + it) * OB_ATILE;
-          gb = a.B + (int64_t)c * Sh::BTILE;
-        }
+        const int tile = i / nit, cfirst = (i - tile * nit) * G, cn = min(G, nch - cfirst);
         const uint32_t bar = bfull + 8 * stg;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(a.planes * abytes + Sh::BBYTES)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)cn * cbytes)
                      : "memory");
+        for (int u = 0; u < cn; ++u) {
+          const int c = cfirst + u;
+          unsigned char* sa = base + stg * slot + u * cbytes;
+          unsigned char* sb = sa + a.planes * abytes;
+          const __half* ga;
+          const __half* gb;
+          if (GRAM) {
+            const int kc = c0 + c;
+            ga = a.A + ((int64_t)kc * a.MT + mt) * OB_ATILE;
+            gb = a.B + (int64_t)kc * Sh::BTILE;
+          } else {
+            const int it = (int)blockIdx.x + tile * (int)gridDim.x;
+            ga = a.A + ((int64_t)c * a.MT + it) * OB_ATILE;
+            gb = a.B + (int64_t)c * Sh::BTILE;
+          }
 #pragma unroll 1
-        for (int p = 0; p < a.planes; ++p)
+          for (int p = 0; p < a.planes; ++p)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             ob_smem_u32(sa + p * abytes)),
+                         "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
+                         : "memory");
           asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                           ob_smem_u32(sa + p * abytes)),
-                       "l"(ga + p * a.plane), "r"(abytes), "r"(bar)
+                           ob_smem_u32(sb)),
+                       "l"(gb), "r"(Sh::BBYTES), "r"(bar)
                        : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         ob_smem_u32(sb)),
-                     "l"(gb), "r"(Sh::BBYTES), "r"(bar)
-                     : "memory");
+        }
       }
       issued_sh = i;
       if (!ok) fail_sh = 1;
@@ -432,39 +440,47 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
       bool ok = true;
       int i = 0;
       for (; i < NI; ++i) {
-        const int tile = i / nch, c = i - tile * nch;
-        const int f = tile * npt + c / OB_FOLD, buf = f % NBUF;
-        const bool first = (c % OB_FOLD) == 0;
-        const bool last = (c % OB_FOLD) == OB_FOLD - 1 || c == nch - 1;
-        // the accumulator buffer is free once the fold of its previous period is done
-        if (first && f >= NBUF && !ob_wait(bacce + 8 * buf, (uint32_t)(f / NBUF - 1) & 1u)) ok = false;
+        const int tile = i / nit, cfirst = (i - tile * nit) * G, cn = min(G, nch - cfirst);
         const int stg = i % ns;
-        if (ok && !ob_wait(bfull + 8 * stg, (uint32_t)(i / ns) & 1u)) ok = false;
+        if (!ob_wait(bfull + 8 * stg, (uint32_t)(i / ns) & 1u)) ok = false;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t sa = ob_smem_u32(base + stg * slot), sb = sa + a.planes * abytes;
-        const uint32_t dbase = tmem + (uint32_t)(buf * OB_PV * NP);
-#pragma unroll 1
-        for (int p = 0; p < a.planes; ++p) {
-#pragma unroll
-          for (int ks = 0; ks < OB_KC / 16; ++ks) {
-            const uint64_t da = ob_sdesc(sa + p * abytes + ks * 256);
-            const uint64_t db = ob_sdesc(sb + ks * 256);
-            const uint32_t accf = (first && ks == 0) ? 0u : 1u;  // a period starts each plane afresh
-            asm volatile(
-                "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(dbase + (uint32_t)(p * NP)),
-                "l"(da), "l"(db), "r"(id), "r"(accf)
-                : "memory");
+        for (int u = 0; u < cn && ok; ++u) {
+          const int c = cfirst + u;
+          const int f = tile * npt + c / OB_FOLD, buf = f % NBUF;
+          const bool first = (c % OB_FOLD) == 0;
+          const bool last = (c % OB_FOLD) == OB_FOLD - 1 || c == nch - 1;
+          // the accumulator buffer is free once the fold of its previous period is done
+          if (first && f >= NBUF && !ob_wait(bacce + 8 * buf, (uint32_t)(f / NBUF - 1) & 1u)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = ob_smem_u32(base + stg * slot + u * cbytes), sb = sa + a.planes * abytes;
+          const uint32_t dbase = tmem + (uint32_t)(buf * OB_PV * NP);
+#pragma unroll 1
+          for (int p = 0; p < a.planes; ++p) {
+#pragma unroll
+            for (int ks = 0; ks < OB_KC / 16; ++ks) {
+              const uint64_t da = ob_sdesc(sa + p * abytes + ks * 256);
+              const uint64_t db = ob_sdesc(sb + ks * 256);
+              const uint32_t accf = (first && ks == 0) ? 0u : 1u;  // a period starts each plane afresh
+              asm volatile(
+                  "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}\n" ::"r"(dbase + (uint32_t)(p * NP)),
+                  "l"(da), "l"(db), "r"(id), "r"(accf)
+                  : "memory");
+            }
+          }
+          if (last)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             baccf + 8 * buf)
+                         : "memory");
         }
+        if (!ok) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          bempty + 8 * stg)
                      : "memory");
-        if (last)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           baccf + 8 * buf)
-                       : "memory");
       }
       consumed_sh = i;
       if (!ok) fail_sh = 1;
