@@ -104,6 +104,16 @@ __device__ __forceinline__ void block_reduce_tile(A (&acc)[S][S], double* out, d
   }
 }
 
+// Fills the lower triangle of a symmetric S x S register tile from its upper triangle (the
+// self-Gram partials accumulate t >= u only: GB300's FP64 pipe is narrow).
+template <typename A, int S>
+__device__ __forceinline__ void mirror_upper(A (&acc)[S][S]) {
+#pragma unroll
+  for (int u = 1; u < S; ++u)
+#pragma unroll
+    for (int t = 0; t < u; ++t) acc[u][t] = acc[t][u];
+}
+
 // ---------------------------------------------------------------- SpMM
 // Y = A X (- Xprev M, the three-term Lanczos term) over an s-wide block, one thread per row
 // computing its s outputs.  A CTA of NT rows first stages its slice of the CSR arrays (column
@@ -377,11 +387,14 @@ __global__ void __launch_bounds__(NT) update_kernel(const DevState* st, int64_t 
 #pragma unroll
         for (int u = 0; u < S; ++u)
 #pragma unroll
-          for (int t = 0; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];
+          for (int t = u; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];  // upper triangle
       }
     }
   }
-  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+  if constexpr (SELF) {
+    mirror_upper<A, S>(acc);
+    block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+  }
 }
 
 template <typename T, int S>
@@ -401,8 +414,9 @@ __global__ void __launch_bounds__(NT) selfgram_kernel(const DevState* st, int64_
 #pragma unroll
     for (int u = 0; u < S; ++u)
 #pragma unroll
-      for (int t = 0; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];
+      for (int t = u; t < S; ++t) acc[u][t] += (A)y[u] * (A)y[t];  // upper triangle
   }
+  mirror_upper<A, S>(acc);
   block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
 }
 
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n
 #pragma unroll
       for (int u = 0; u < S; ++u)
 #pragma unroll
-        for (int t = 0; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];
+        for (int t = u; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];  // upper triangle
     }
     if (colmax != nullptr) {
 #pragma unroll
@@ -452,7 +466,10 @@ __global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n
         zmax[t] = max(zmax[t], (unsigned long long)__double_as_longlong(fabs((double)z[t])));
     }
   }
-  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+  if constexpr (SELF) {
+    mirror_upper<A, S>(acc);
+    block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
+  }
   if (colmax != nullptr) {
 #pragma unroll
     for (int t = 0; t < S; ++t) {
@@ -693,7 +710,7 @@ __global__ void __launch_bounds__(NT) cholscale_kernel(DevState* st, const doubl
 #pragma unroll
       for (int u = 0; u < S; ++u)
 #pragma unroll
-        for (int t = 0; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];
+        for (int t = u; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];  // upper triangle
     }
     if (colmax != nullptr) {
 #pragma unroll
@@ -701,7 +718,10 @@ __global__ void __launch_bounds__(NT) cholscale_kernel(DevState* st, const doubl
         zmax[t] = max(zmax[t], (unsigned long long)__double_as_longlong(fabs((double)z[t])));
     }
   }
-  if constexpr (SELF) block_reduce_tile<A, S>(acc, partial_out + (int64_t)blockIdx.x * S * S, sh);
+  if constexpr (SELF) {
+    mirror_upper<A, S>(acc);
+    block_reduce_tile<A, S>(acc, partial_out + (int64_t)blockIdx.x * S * S, sh);
+  }
   if (colmax != nullptr) {
 #pragma unroll
     for (int t = 0; t < S; ++t) {

@@ -293,6 +293,40 @@ __device__ __forceinline__ double ob_pow2(int x) {  // 2^x as a float64 (0 or in
                                      : __longlong_as_double((long long)(x + 1023) << 52));
 }
 
+// 2^sc (w0 2^-38 + w1 2^-59 + w2 2^-73), the three fixed-point words of a fold, rounded once
+// to float64 (nearest, ties to even) with integer operations: the words are aligned into one
+// 128-bit integer W of unit 2^-73 (|W| < 2^98), whose leading 53 bits give the significand.
+// GB300's FP64 pipe is narrow, and this runs once per output in the epilogues.  A result
+// outside the normal float64 range takes the float64 formula (rounded more than once).
+__device__ __forceinline__ double ob_fixed_to_double(long long w0, long long w1, long long w2, int sc) {
+  const __int128 W = ((__int128)w0 << 35) + ((__int128)w1 << 14) + (__int128)w2;
+  if (W == 0) return 0.0;
+  const unsigned long long sign = W < 0 ? 1ull : 0ull;
+  const unsigned __int128 M = sign ? (unsigned __int128)(-W) : (unsigned __int128)W;
+  const unsigned long long mh = (unsigned long long)(M >> 64), ml = (unsigned long long)M;
+  int b = mh ? 127 - __clzll((long long)mh) : 63 - __clzll((long long)ml);  // leading bit of M
+  unsigned long long keep;
+  if (b <= 52) {
+    keep = ml << (52 - b);
+  } else {
+    const int sh = b - 52;
+    const unsigned __int128 q = M >> sh;
+    const unsigned __int128 rem = M - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    keep = (unsigned long long)q;
+    if (rem > half || (rem == half && (keep & 1ull))) ++keep;
+    if (keep >> 53) {
+      keep >>= 1;
+      ++b;
+    }
+  }
+  const int ex = b + sc - 73 + 1023;  // biased exponent of (keep 2^-52) 2^{b + sc - 73}
+  if (ex <= 0 || ex >= 2047)
+    return fma((double)w0, 0x1p-38, fma((double)w1, 0x1p-59, (double)w2 * 0x1p-73)) * ob_pow2(sc / 2) *
+           ob_pow2(sc - sc / 2);
+  return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)ex << 52) | (keep & 0xFFFFFFFFFFFFFull)));
+}
+
 struct ObArgs {
   DevState* st;
   const __half* A;         // basis digit planes (Gram or update layout)
@@ -503,6 +537,15 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
     bool ok = true;
     for (int f = 0; f < NF; ++f) {
       const int buf = f % NBUF;
+      // update: the last period of a tile; its rows of Y are loaded before the wait, so that
+      // their latency passes while the MMAs finish
+      const bool tile_end = !GRAM && f % npt == npt - 1;
+      const int64_t row = (int64_t)((int)blockIdx.x + (f / npt) * (int)gridDim.x) * OB_TM + tid;
+      double yold[S];
+      if (tile_end && row < a.n) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) yold[t] = a.out[row * S + t];
+      }
       if (!ob_wait(baccf + 8 * buf, (uint32_t)(f / NBUF) & 1u)) {
         ok = false;
         break;
@@ -544,28 +587,26 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bacce + 8 * buf) : "memory");
-      if (!GRAM && f % npt == npt - 1) {  // the tile is complete: Y -= V H on its rows
-        const int it = (int)blockIdx.x + (f / npt) * (int)gridDim.x;
-        const int64_t row = (int64_t)it * OB_TM + tid;
+      if (tile_end) {  // the tile is complete: Y -= V H on its rows
         if (row < a.n) {
           double y[S];
 #pragma unroll
           for (int t = 0; t < S; ++t) {
             const int fe = a.eb[t];
-            double v = fma((double)w0[t], 0x1p-38, fma((double)w1[t], 0x1p-59, (double)w2[t] * 0x1p-73));
-            v = fe == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll) : v * ob_pow2(fe);
-            y[t] = a.out[row * S + t] - v;
+            const double v = fe == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll)
+                                              : ob_fixed_to_double(w0[t], w1[t], w2[t], fe);
+            y[t] = yold[t] - v;
           }
 #pragma unroll
           for (int t = 0; t < S; ++t) {
             a.out[row * S + t] = y[t];
             ym[t] = max(ym[t], (unsigned long long)__double_as_longlong(fabs(y[t])));
           }
-          if (a.self) {
+          if (a.self) {  // the upper triangle (the partial is symmetric)
 #pragma unroll
             for (int u = 0; u < S; ++u)
 #pragma unroll
-              for (int t = 0; t < S; ++t) acc[u][t] += y[u] * y[t];
+              for (int t = u; t < S; ++t) acc[u][t] += y[u] * y[t];
           }
         }
 #pragma unroll
@@ -581,10 +622,8 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
 #pragma unroll
         for (int t = 0; t < S; ++t) {
           const int fe = a.eb[t];
-          double v = fma((double)w0[t], 0x1p-38, fma((double)w1[t], 0x1p-59, (double)w2[t] * 0x1p-73));
-          // 2^{e+f} in two steps: each factor stays in the normal range
-          v = (e == OB_EXP_BAD || fe == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
-                                                    : v * ob_pow2(e) * ob_pow2(fe);
+          const double v = (e == OB_EXP_BAD || fe == OB_EXP_BAD) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                                 : ob_fixed_to_double(w0[t], w1[t], w2[t], e + fe);
           o[t] = v;
         }
       }
@@ -603,7 +642,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
       for (int u = 0; u < S; ++u)
 #pragma unroll
         for (int t = 0; t < S; ++t) {
-          double v = acc[u][t];
+          double v = u <= t ? acc[u][t] : acc[t][u];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           if (lane == 0) shred[warp * S * S + u * S + t] = v;
