@@ -71,6 +71,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Sum of partials[i * stride + off], i < nb, by every thread of the calling CTA: each thread
+// adds a strided subset, then block_sum (a fixed order).  All threads of the CTA must call it.
+// The last CTA of a reduction uses it: one thread adding thousands of partials in sequence
+// spent tens of microseconds in float64 additions on this GPU.
+__device__ __forceinline__ double cta_sum(const double* partials, int nb, int stride, int off, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += __ldcg(partials + (int64_t)i * stride + off);
+  return block_sum(v, sh);
+}
+
 // Last-CTA detection after each CTA has written its partial result.
 // Returns true in exactly one CTA (the last to arrive); that CTA resets the ticket.
 __device__ __forceinline__ bool last_cta(unsigned int* ticket, int* flag_sh) {

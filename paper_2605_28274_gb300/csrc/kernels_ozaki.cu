@@ -453,20 +453,18 @@ __global__ void __launch_bounds__(NT) oz_omega_kernel(DevState* st, int r, int r
     partials[2 * blockIdx.x] = ts;
     partials[2 * blockIdx.x + 1] = tt;
   }
-  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) {
-      s1 += __ldcg(partials + 2 * i);
-      s2 += __ldcg(partials + 2 * i + 1);
-    }
-    if (!isfinite(s1) || !isfinite(s2)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 4;
-    } else if (s2 == 0.0 || s1 == 0.0) {
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 5;
-    } else {
-      st->omega = s1 / s2;
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh)) {
+    const double s1 = cta_sum(partials, (int)gridDim.x, 2, 0, sh), s2 = cta_sum(partials, (int)gridDim.x, 2, 1, sh);
+    if (threadIdx.x == 0) {
+      if (!isfinite(s1) || !isfinite(s2)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 4;
+      } else if (s2 == 0.0 || s1 == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 5;
+      } else {
+        st->omega = s1 / s2;
+      }
     }
   }
 }

@@ -327,10 +327,11 @@ __global__ void sumsq_kernel(int64_t count, const double* __restrict__ x, double
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < count; i += (int64_t)gridDim.x * NT) v += x[i] * x[i];
   v = block_sum(v, sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = v;
-  if (last_cta(ticket, &last_sh) && threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(partials + i);
-    *out = t;
+  if (last_cta(ticket, &last_sh)) {
+    const double t = cta_sum(partials, (int)gridDim.x, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      *out = t;
+    }
   }
 }
 

@@ -93,26 +93,27 @@ __global__ void __launch_bounds__(NT) cg_q_kernel(DevState* st, int mode, int r,
   pq = block_sum(pq, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = pq;
-  if (last_cta(&st->tickets[TK_CG_Q], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_CG_Q], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    if (!isfinite(tot)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 1;
-    } else if (cr) {
-      if (tot == 0.0) {  // <R, L(R)> = 0: the CR recurrence breaks down
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      if (!isfinite(tot)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 1;
+      } else if (cr) {
+        if (tot == 0.0) {  // <R, L(R)> = 0: the CR recurrence breaks down
+          st->status = ST_BREAKDOWN;
+          st->breakdown_where = 20;
+        } else {
+          if (!first) st->beta = tot / st->rho;
+          st->rho = tot;
+        }
+      } else if (!(tot > 0.0)) {  // <P, Q> <= 0: F not positive definite on this direction
         st->status = ST_BREAKDOWN;
-        st->breakdown_where = 20;
+        st->breakdown_where = 2;
       } else {
-        if (!first) st->beta = tot / st->rho;
-        st->rho = tot;
+        st->alpha = st->rho / tot;
       }
-    } else if (!(tot > 0.0)) {  // <P, Q> <= 0: F not positive definite on this direction
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 2;
-    } else {
-      st->alpha = st->rho / tot;
     }
   }
 }
@@ -142,22 +143,23 @@ __global__ void __launch_bounds__(NT) cg_update_kernel(DevState* st, double* his
   rr = block_sum(rr, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = rr;
-  if (last_cta(&st->tickets[TK_CG_UPD], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_CG_UPD], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    const double rn = sqrt(tot);
-    hist[k + 1] = rn / st->r0;
-    st->rnorm = rn;
-    st->iters = k + 1;
-    if (!isfinite(rn)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 3;
-    } else if (rn <= st->r0 * st->tol) {
-      st->status = ST_CONVERGED;
-    } else if (!cr) {
-      st->beta = tot / st->rho;
-      st->rho = tot;
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      const double rn = sqrt(tot);
+      hist[k + 1] = rn / st->r0;
+      st->rnorm = rn;
+      st->iters = k + 1;
+      if (!isfinite(rn)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 3;
+      } else if (rn <= st->r0 * st->tol) {
+        st->status = ST_CONVERGED;
+      } else if (!cr) {
+        st->beta = tot / st->rho;
+        st->rho = tot;
+      }
     }
   }
 }
@@ -184,18 +186,19 @@ __global__ void __launch_bounds__(NT) cr_p_kernel(DevState* st, int rpp, double*
   qq = block_sum(qq, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = qq;
-  if (last_cta(&st->tickets[TK_CG_Q], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_CG_Q], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    if (!isfinite(tot)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 21;
-    } else if (tot == 0.0) {
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 22;
-    } else {
-      st->alpha = st->rho / tot;
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      if (!isfinite(tot)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 21;
+      } else if (tot == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 22;
+      } else {
+        st->alpha = st->rho / tot;
+      }
     }
   }
 }
@@ -307,21 +310,19 @@ __global__ void __launch_bounds__(NT) sylv_gemm_kernel(DevState* st, int r, int 
     partials[2 * bid] = ts;
     partials[2 * bid + 1] = tt;
   }
-  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      s1 += __ldcg(partials + 2 * i);
-      s2 += __ldcg(partials + 2 * i + 1);
-    }
-    if (!isfinite(s1) || !isfinite(s2)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 4;
-    } else if (s2 == 0.0 || s1 == 0.0) {  // T = 0 or omega = 0
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 5;
-    } else {
-      st->omega = s1 / s2;
+    const double s1 = cta_sum(partials, nb, 2, 0, sh), s2 = cta_sum(partials, nb, 2, 1, sh);
+    if (threadIdx.x == 0) {
+      if (!isfinite(s1) || !isfinite(s2)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 4;
+      } else if (s2 == 0.0 || s1 == 0.0) {  // T = 0 or omega = 0
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 5;
+      } else {
+        st->omega = s1 / s2;
+      }
     }
   }
 }
@@ -452,21 +453,19 @@ __global__ void __launch_bounds__(NT) sylv_gemm_df_kernel(DevState* st, int r, i
     partials[2 * bid] = ts;
     partials[2 * bid + 1] = tt;
   }
-  if (last_cta(&st->tickets[TK_BI_T], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_BI_T], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < nb; ++i) {
-      s1 += __ldcg(partials + 2 * i);
-      s2 += __ldcg(partials + 2 * i + 1);
-    }
-    if (!isfinite(s1) || !isfinite(s2)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 4;
-    } else if (s2 == 0.0 || s1 == 0.0) {
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 5;
-    } else {
-      st->omega = s1 / s2;
+    const double s1 = cta_sum(partials, nb, 2, 0, sh), s2 = cta_sum(partials, nb, 2, 1, sh);
+    if (threadIdx.x == 0) {
+      if (!isfinite(s1) || !isfinite(s2)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 4;
+      } else if (s2 == 0.0 || s1 == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 5;
+      } else {
+        st->omega = s1 / s2;
+      }
     }
   }
 }
@@ -527,29 +526,30 @@ __global__ void __launch_bounds__(NT) bicg_update_kernel(DevState* st, double* h
   rr = block_sum(rr, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = rr;
-  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    const double rn = sqrt(tot);
-    hist[k + 1] = rn / st->r0;
-    st->rnorm = rn;
-    st->iters = k + 1;
-    if (!isfinite(rn)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 8;
-    } else if (rn <= st->r0 * st->tol) {
-      st->status = ST_CONVERGED;
-    } else {
-      double rho_new = 0.0;
-      for (int t = 0; t < s; ++t)
-        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
-      if (rho_new == 0.0) {
-        st->status = ST_BREAKDOWN;
-        st->breakdown_where = 9;
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      const double rn = sqrt(tot);
+      hist[k + 1] = rn / st->r0;
+      st->rnorm = rn;
+      st->iters = k + 1;
+      if (!isfinite(rn)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 8;
+      } else if (rn <= st->r0 * st->tol) {
+        st->status = ST_CONVERGED;
       } else {
-        st->beta = (alpha / omega) * (rho_new / st->rho);
-        st->rho = rho_new;
+        double rho_new = 0.0;
+        for (int t = 0; t < s; ++t)
+          for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+        if (rho_new == 0.0) {
+          st->status = ST_BREAKDOWN;
+          st->breakdown_where = 9;
+        } else {
+          st->beta = (alpha / omega) * (rho_new / st->rho);
+          st->rho = rho_new;
+        }
       }
     }
   }
@@ -613,29 +613,30 @@ __global__ void __launch_bounds__(NT) cgs_update_kernel(DevState* st, double* hi
   rr = block_sum(rr, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = rr;
-  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    const double rn = sqrt(tot);
-    hist[k + 1] = rn / st->r0;
-    st->rnorm = rn;
-    st->iters = k + 1;
-    if (!isfinite(rn)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 8;
-    } else if (rn <= st->r0 * st->tol) {
-      st->status = ST_CONVERGED;
-    } else {
-      double rho_new = 0.0;
-      for (int t = 0; t < s; ++t)
-        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
-      if (rho_new == 0.0) {
-        st->status = ST_BREAKDOWN;
-        st->breakdown_where = 9;
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      const double rn = sqrt(tot);
+      hist[k + 1] = rn / st->r0;
+      st->rnorm = rn;
+      st->iters = k + 1;
+      if (!isfinite(rn)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 8;
+      } else if (rn <= st->r0 * st->tol) {
+        st->status = ST_CONVERGED;
       } else {
-        st->beta = rho_new / st->rho;
-        st->rho = rho_new;
+        double rho_new = 0.0;
+        for (int t = 0; t < s; ++t)
+          for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+        if (rho_new == 0.0) {
+          st->status = ST_BREAKDOWN;
+          st->breakdown_where = 9;
+        } else {
+          st->beta = rho_new / st->rho;
+          st->rho = rho_new;
+        }
       }
     }
   }
@@ -727,28 +728,29 @@ __global__ void __launch_bounds__(NT) gp_zeta_kernel(DevState* st, int k, int e2
     o[3] = ty;
     o[4] = aa;
   }
-  if (last_cta(&st->tickets[TK_GP_ZETA], &last_sh) && threadIdx.x == 0) {
-    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int c = 0; c < (int)gridDim.x; ++c)
-      for (int j = 0; j < 5; ++j) v[j] += __ldcg(part + 5 * (int64_t)c + j);
-    double zeta, eta;
-    if (k == 0) {
-      zeta = v[1] / v[4];
-      eta = 0.0;
-    } else {
-      const double den = v[4] * v[0] - v[3] * v[3];
-      zeta = (v[0] * v[1] - v[2] * v[3]) / den;
-      eta = (v[4] * v[2] - v[3] * v[1]) / den;
-    }
-    if (!isfinite(zeta) || !isfinite(eta)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 30;
-    } else if (zeta == 0.0) {
-      st->status = ST_BREAKDOWN;
-      st->breakdown_where = 31;
-    } else {
-      st->omega = zeta;
-      st->eta = eta;
+  if (last_cta(&st->tickets[TK_GP_ZETA], &last_sh)) {
+    double v[5];
+    for (int j = 0; j < 5; ++j) v[j] = cta_sum(part, (int)gridDim.x, 5, j, sh);
+    if (threadIdx.x == 0) {
+      double zeta, eta;
+      if (k == 0) {
+        zeta = v[1] / v[4];
+        eta = 0.0;
+      } else {
+        const double den = v[4] * v[0] - v[3] * v[3];
+        zeta = (v[0] * v[1] - v[2] * v[3]) / den;
+        eta = (v[4] * v[2] - v[3] * v[1]) / den;
+      }
+      if (!isfinite(zeta) || !isfinite(eta)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 30;
+      } else if (zeta == 0.0) {
+        st->status = ST_BREAKDOWN;
+        st->breakdown_where = 31;
+      } else {
+        st->omega = zeta;
+        st->eta = eta;
+      }
     }
   }
 }
@@ -788,29 +790,30 @@ __global__ void __launch_bounds__(NT) gp_update_kernel(DevState* st, double* his
   rr = block_sum(rr, sh);
   const int bid = blockIdx.x + blockIdx.y * gridDim.x;
   if (threadIdx.x == 0) partials[bid] = rr;
-  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh) && threadIdx.x == 0) {
+  if (last_cta(&st->tickets[TK_BI_UPD], &last_sh)) {
     const int nb = gridDim.x * gridDim.y;
-    double tot = 0.0;
-    for (int i = 0; i < nb; ++i) tot += __ldcg(partials + i);
-    const double rn = sqrt(tot);
-    hist[k + 1] = rn / st->r0;
-    st->rnorm = rn;
-    st->iters = k + 1;
-    if (!isfinite(rn)) {
-      st->status = ST_NONFINITE;
-      st->breakdown_where = 32;
-    } else if (rn <= st->r0 * st->tol) {
-      st->status = ST_CONVERGED;
-    } else {
-      double rho_new = 0.0;
-      for (int t = 0; t < s; ++t)
-        for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
-      if (rho_new == 0.0) {
-        st->status = ST_BREAKDOWN;
-        st->breakdown_where = 33;
+    const double tot = cta_sum(partials, nb, 1, 0, sh);
+    if (threadIdx.x == 0) {
+      const double rn = sqrt(tot);
+      hist[k + 1] = rn / st->r0;
+      st->rnorm = rn;
+      st->iters = k + 1;
+      if (!isfinite(rn)) {
+        st->status = ST_NONFINITE;
+        st->breakdown_where = 32;
+      } else if (rn <= st->r0 * st->tol) {
+        st->status = ST_CONVERGED;
       } else {
-        st->beta = (alpha / zeta) * (rho_new / st->rho);
-        st->rho = rho_new;
+        double rho_new = 0.0;
+        for (int t = 0; t < s; ++t)
+          for (int u = 0; u < s; ++u) rho_new += Rt[u + t * s] * __ldcg(R + u + (int64_t)t * lds);
+        if (rho_new == 0.0) {
+          st->status = ST_BREAKDOWN;
+          st->breakdown_where = 33;
+        } else {
+          st->beta = (alpha / zeta) * (rho_new / st->rho);
+          st->rho = rho_new;
+        }
       }
     }
   }
