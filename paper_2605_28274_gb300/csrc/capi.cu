@@ -652,7 +652,14 @@ int wait_status(sylv_handle* h, int slot, double deadline) {
 
 int ensure_streams(sylv_handle* h) {
   if (h->sbas[0]) return SYLV_OK;
-  for (auto& sb : h->sbas) CU(cudaStreamCreateWithFlags(&sb, cudaStreamNonBlocking));
+  // The larger side's basis chain is the solve's critical path (its HBM-bound Gram and updates
+  // take the most time); its stream gets the highest priority, so that the other side's kernels
+  // fill the SMs its latency-bound kernels (CholQR, digit splits, reductions) leave idle.
+  int prio_lo = 0, prio_hi = 0;
+  CU(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  const int big = (!h->lyap && h->side[1].n > h->side[0].n) ? 1 : 0;
+  for (int i = 0; i < 2; ++i)
+    CU(cudaStreamCreateWithPriority(&h->sbas[i], cudaStreamNonBlocking, i == big ? prio_hi : prio_lo));
   CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   for (auto& pr : h->ev_bas)
     for (auto& e : pr) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
