@@ -14,6 +14,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sylv.h"
@@ -1026,6 +1027,56 @@ std::vector<RoundView> round_views(const sylv_handle* h) {
 
 
 
+// The float64 bases held as digit planes (section: tensor-core basis): X^(T) Min with the basis
+// products on the tensor cores, float64-accurate like the Gram and update of the solve, in
+// 8-column halves of Min.  One round only (the float64 solve has no corrections).
+int apply_X_ob(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, const RoundView& v) {
+  int rc = SYLV_OK;
+  const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
+  const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
+  const Side& sv = h->side[0];
+  const Side& sw = h->side[h->lyap ? 0 : 1];
+  const Side& sin = trans ? sv : sw;    // Min's side: X^T Min = W X^T (V^T Min)
+  const Side& sout = trans ? sw : sv;
+  const int r = v.nb * v.s;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  constexpr int HW = 8;  // columns per product
+  const int64_t nmax = std::max(n, m);
+  const int rmax = std::max(sv.ob.rp, sw.ob.rp);
+  void* scr = sk_buf(h, 24, sylv::ob_cols_scratch_bytes(nmax, rmax, HW), &rc);
+  double* part = sk_buf(h, 25, (size_t)sms * r * HW * sizeof(double), &rc);
+  double* H8 = sk_buf(h, 26, (size_t)r * HW * sizeof(double), &rc);
+  double* P = sk_buf(h, 0, (size_t)r * k * sizeof(double), &rc);
+  double* P2 = sk_buf(h, 1, (size_t)r * k * sizeof(double), &rc);
+  if (rc) return rc;
+  sylv::ObSide oin = sin.ob, oout = sout.ob;
+  sylv::ob_cols_carve(scr, nmax, rmax, HW, oin);  // the operand digits: scratch shared by both sides
+  oout.YB = oin.YB;
+  oout.HB = oin.HB;
+  oout.ey = oin.ey;
+  oout.eh = oin.eh;
+  oout.mx = oin.mx;
+  const double fl = 2.0 * (double)r * k;
+  for (int c0 = 0; c0 < k; c0 += HW)
+    PROF(h, KC_RESID_TSG, (double)rows_in * (r * 8.0 + HW * 8.0), fl / (k / HW) * rows_in,
+         sylv::launch_ob_gram_cols(h->stream, h->st_sk, rows_in, HW, r, Min + c0, k, oin, part, P, k, c0));
+  PROF(h, KC_RESID_SMALL, 0.0, 2.0 * r * r * k, sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2));
+  CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
+  for (int c0 = 0; c0 < k; c0 += HW) {
+    CU(cudaMemcpy2DAsync(H8, HW * sizeof(double), P2 + c0, k * sizeof(double), HW * sizeof(double), r,
+                         cudaMemcpyDeviceToDevice, h->stream));
+    PROF(h, KC_RESID_TSU, (double)rows_out * (r * 8.0 + 2.0 * HW * 8.0), fl / (k / HW) * rows_out,
+         sylv::launch_ob_update_cols(h->stream, h->st_sk, rows_out, HW, r, H8, Yout + c0, k, oout));
+  }
+  return SYLV_OK;
+}
+
 // Yout (rows x k) = X Min (trans = false; Min is m x k) or X^T Min (trans = true; Min is n x k).
 template <typename T>
 int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, size_t from_round = 0) {
@@ -1034,6 +1085,9 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
   auto views = round_views(h);
   if (from_round > 0) views.erase(views.begin(), views.begin() + std::min(from_round, views.size()));
+  if (std::is_same<T, double>::value && views.size() == 1 && views[0].nb > 0 && k % 8 == 0 &&
+      h->side[0].ob.G != nullptr && (h->lyap || h->side[1].ob.G != nullptr))
+    return apply_X_ob(h, trans, Min, k, Yout, views[0]);
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
   const int max_rc = 0;  // launch_tsg picks the row chunks
@@ -1218,6 +1272,9 @@ int sketch_finish(sylv_handle* h, double* est, double* bound, bool* ok) {
   DevState dst;
   std::memcpy(&dst, h->sk_host + 8, sizeof(DevState));
   if (h->cnorm < 0) h->cnorm = std::sqrt(std::max(0.0, hs[2]));
+  if (dst.status == sylv::ST_WAIT_TIMEOUT)
+    return fail(SYLV_ETIMEOUT, "a device-side wait of the true-residual certificate gave up (site " +
+                                   std::to_string(dst.breakdown_where) + ")");
   const double q = cert_q();
   // the range part is used only when the range finder's CholQR succeeded (R of rank >= 8)
   *ok = h->mixed && dst.status == sylv::ST_RUNNING;

@@ -54,6 +54,20 @@ int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const doub
 int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
                      double* self_partial, bool ymax, int planes);
 
+// Products of the float64 true-residual certificate on a side's digit planes (float64-accurate
+// like the basis kernels).  o: the side's ObSide with YB, HB, ey, eh, mx replaced by scratch of
+// ob_cols_scratch_bytes(rows, basis columns, s) bytes carved by ob_cols_carve (the operands here
+// have s columns, not the basis block width).
+size_t ob_cols_scratch_bytes(int64_t n_max, int R_max, int s);
+void ob_cols_carve(void* mem, int64_t n_max, int R_max, int s, ObSide& o);
+// P[m ldp + col0 + t] = (V^T Y)(m, t) over the first js basis columns; Y n x s with row stride ldy.
+// partial: scratch of (number of SMs) x js x s doubles.  Returns the number of k splits.
+int launch_ob_gram_cols(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Y, int64_t ldy,
+                        const ObSide&, double* partial, double* P, int64_t ldp, int col0);
+// Z (n x s, row stride ldz) += V Hc over the first js basis columns (Hc js x s row-major).
+void launch_ob_update_cols(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Z, int64_t ldz,
+                           const ObSide&);
+
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64
 // q S + t of row (k =) i; exponents into ey.  One thread per row.
 template <int S>
 __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Y,
-                                                       const unsigned long long* __restrict__ mx, int* __restrict__ ey,
-                                                       __half* __restrict__ YB) {
+                                                       int64_t ldy, const unsigned long long* __restrict__ mx,
+                                                       int* __restrict__ ey, __half* __restrict__ YB) {
   if (stopped(st)) return;
   constexpr int NP = ObShape<S>::NP;
   const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64
 #pragma unroll
   for (int t = 0; t < S; ++t) {
     int d[OB_PY];
-    ob_digits<OB_PY, OB_WY>(Y[i * S + t], 0, e[t], d);
+    ob_digits<OB_PY, OB_WY>(Y[i * ldy + t], 0, e[t], d);
 #pragma unroll
     for (int q = 0; q < OB_PY; ++q) YB[base + ob_cm(q * S + t, (int)(i & 31))] = ob_h(d[q]);
   }
@@ -342,6 +342,8 @@ struct ObArgs {
   double* self;            // update: per-CTA partial Y^T Y of the result (nullptr: none)
   unsigned long long* ymax;  // update: column maxima of |result| as IEEE bits (nullptr: none)
   int planes;              // basis digit planes used (the leading ones; OB_PV: all)
+  int64_t ldy;             // update: row stride of Y (S for a block of its own)
+  int add;                 // update: Y += V H instead of Y -= V H
 };
 
 // GRAM: CTA (m tile, k split) writes the partial V^T Y of its rows.  Update: CTA c takes
@@ -544,7 +546,7 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
       double yold[S];
       if (tile_end && row < a.n) {
 #pragma unroll
-        for (int t = 0; t < S; ++t) yold[t] = a.out[row * S + t];
+        for (int t = 0; t < S; ++t) yold[t] = a.out[row * a.ldy + t];
       }
       if (!ob_wait(baccf + 8 * buf, (uint32_t)(f / NBUF) & 1u)) {
         ok = false;
@@ -595,11 +597,11 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
             const int fe = a.eb[t];
             const double v = fe == OB_EXP_BAD ? __longlong_as_double(0x7FF8000000000000ll)
                                               : ob_fixed_to_double(w0[t], w1[t], w2[t], fe);
-            y[t] = yold[t] - v;
+            y[t] = a.add ? yold[t] + v : yold[t] - v;
           }
 #pragma unroll
           for (int t = 0; t < S; ++t) {
-            a.out[row * S + t] = y[t];
+            a.out[row * a.ldy + t] = y[t];
             ym[t] = max(ym[t], (unsigned long long)__double_as_longlong(fabs(y[t])));
           }
           if (a.self) {  // the upper triangle (the partial is symmetric)
@@ -677,6 +679,44 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TMEM_COLS));
+}
+
+// Column maxima of |Y| (n x S, row stride ldy) as IEEE bits (non-negative doubles order like
+// their bit patterns), combined into mx (zeroed beforehand) with atomicMax: the true-residual
+// certificate's blocks, whose producers do not record them.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_colmax_kernel(int64_t n, const double* __restrict__ Y, int64_t ldy,
+                                                       unsigned long long* __restrict__ mx) {
+  __shared__ unsigned long long sm[S];
+  if (threadIdx.x < S) sm[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long m[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) m[t] = 0;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      m[t] = max(m[t], (unsigned long long)__double_as_longlong(Y[i * ldy + t]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    unsigned long long v = m[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&sm[t], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < S && sm[threadIdx.x]) atomicMax(mx + threadIdx.x, sm[threadIdx.x]);
+}
+
+// P[m ldp + col0 + t] = the sum over the ks splits of partial[z][m S + t] (m < js), in split order.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_sum_splits_kernel(int ks, int js, const double* __restrict__ partial,
+                                                           double* __restrict__ P, int64_t ldp, int col0) {
+  const int idx = blockIdx.x * NT + threadIdx.x;
+  if (idx >= js * S) return;
+  double v = 0.0;
+  for (int z = 0; z < ks; ++z) v += partial[(int64_t)z * js * S + idx];
+  P[(int64_t)(idx / S) * ldp + col0 + idx % S] = v;
 }
 
 int ob_sms() {
@@ -781,10 +821,12 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
   a.self = nullptr;
   a.ymax = nullptr;
   a.planes = OB_PV;
+  a.ldy = s;
+  a.add = 0;
   const dim3 grid((unsigned)mtv, (unsigned)ks);
 #define CASE(SV)                                                                                                 \
   case SV:                                                                                                       \
-    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, o.mx + 8, o.ey, (__half*)o.YB);                  \
+    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, SV, o.mx + 8, o.ey, (__half*)o.YB);                  \
     ob_kernel<SV, true><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                              \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
@@ -811,6 +853,8 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   a.self = self_partial;
   a.ymax = ymax ? o.mx + 8 : nullptr;
   a.planes = std::max(1, std::min(OB_PV, planes));
+  a.ldy = s;
+  a.add = 0;
 #define CASE(SV)                                                                                              \
   case SV:                                                                                                    \
     ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);          \
@@ -819,6 +863,96 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   switch (s) { SYLV_OB_S_CASES(CASE) }
 #undef CASE
   return grid;
+}
+
+// ---------------------------------------------------------------- certificate products
+size_t ob_cols_scratch_bytes(int64_t n_max, int R_max, int S) {
+  const size_t np = (size_t)ob_np(n_max), rp = (size_t)ob_rp(R_max), NPs = (size_t)ob_NP(S);
+  return 256 + np * NPs * 2 + rp * NPs * 2 + 16 * sizeof(int) + 16 * sizeof(unsigned long long) + 1024;
+}
+
+void ob_cols_carve(void* mem, int64_t n_max, int R_max, int S, ObSide& o) {
+  const size_t np = (size_t)ob_np(n_max), rp = (size_t)ob_rp(R_max), NPs = (size_t)ob_NP(S);
+  uintptr_t p = ((uintptr_t)mem + 255) & ~(uintptr_t)255;
+  auto take = [&](size_t bytes) {
+    void* q = (void*)p;
+    p = (p + bytes + 255) & ~(uintptr_t)255;
+    return q;
+  };
+  o.YB = (uint16_t*)take(np * NPs * 2);
+  o.HB = (uint16_t*)take(rp * NPs * 2);
+  o.ey = (int*)take(8 * sizeof(int));
+  o.eh = (int*)take(8 * sizeof(int));
+  o.mx = (unsigned long long*)take(16 * sizeof(unsigned long long));
+}
+
+int launch_ob_gram_cols(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Y, int64_t ldy,
+                        const ObSide& o, double* partial, double* P, int64_t ldp, int col0) {
+  if (js <= 0) return 0;
+  const unsigned gs = (unsigned)std::max<int64_t>(1, (n + NT - 1) / NT);
+  const unsigned gm = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (n + NT - 1) / NT), 2 * ob_sms());
+  const int mtv = (js + OB_TM - 1) / OB_TM;
+  const int kcn = (int)std::max<int64_t>(1, (n + OB_KC - 1) / OB_KC);
+  int ks = std::max(1, std::min(kcn, ob_sms() / mtv));
+  const int cps = (kcn + ks - 1) / ks;
+  ks = (kcn + cps - 1) / cps;  // no empty split
+  ObArgs a{};
+  a.st = st;
+  a.A = (const __half*)o.G;
+  a.plane = o.plane;
+  a.MT = o.rp / OB_TM;
+  a.B = (const __half*)o.YB;
+  a.n = n;
+  a.js = js;
+  a.cps = cps;
+  a.ea = o.vexp;
+  a.eb = o.ey;
+  a.out = partial;
+  a.planes = OB_PV;
+  a.ldy = s;
+  a.add = 0;
+  const dim3 grid((unsigned)mtv, (unsigned)ks);
+  const unsigned gr = (unsigned)(((int64_t)js * s + NT - 1) / NT);
+  cudaMemsetAsync(o.mx + 8, 0, 8 * sizeof(unsigned long long), strm);
+#define CASE(SV)                                                                                                 \
+  case SV:                                                                                                       \
+    ob_colmax_kernel<SV><<<counted(gm), NT, 0, strm>>>(n, Y, ldy, o.mx + 8);                                     \
+    ob_ysplit_kernel<SV><<<counted(gs), NT, 0, strm>>>(st, n, Y, ldy, o.mx + 8, o.ey, (__half*)o.YB);            \
+    ob_kernel<SV, true><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                              \
+    ob_sum_splits_kernel<SV><<<counted(gr), NT, 0, strm>>>(ks, js, partial, P, ldp, col0);                       \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+  return ks;
+}
+
+void launch_ob_update_cols(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Hc, double* Z,
+                           int64_t ldz, const ObSide& o) {
+  if (js <= 0 || n == 0) return;
+  const int itn = (int)std::max<int64_t>(1, (n + OB_TM - 1) / OB_TM);
+  const int grid = std::min(itn, ob_sms());
+  ObArgs a{};
+  a.st = st;
+  a.A = (const __half*)o.U;
+  a.plane = o.plane;
+  a.MT = (int)(o.np / OB_TM);
+  a.B = (const __half*)o.HB;
+  a.n = n;
+  a.js = js;
+  a.eb = o.eh;
+  a.out = Z;
+  a.self = nullptr;
+  a.ymax = nullptr;
+  a.planes = OB_PV;
+  a.ldy = ldz;
+  a.add = 1;
+#define CASE(SV)                                                                                              \
+  case SV:                                                                                                    \
+    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);          \
+    ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
 }
 
 }  // namespace sylv
