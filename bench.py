@@ -607,14 +607,17 @@ def run_ours(args):
            Bp.val.nbytes + C1p.nbytes + C2p.nbytes)
     barrier()
     e2e_times, d2h = [], 0
-    for _ in range(e2e_steps):
+    # warm-up steps as for the device timing (the first transfer into the freshly pinned output
+    # buffers costs ~0.35 s once), then e2e_steps timed ones
+    for step in range(args.warmup + e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with ps.Solver(Ap, Bp, C1p, C2p, precision=args.precision, cuda_stream=stream.cuda_stream) as sv2:
             inf2 = sv2.bicgstab(p.tol, p.maxit)
             V, X, W = sv2.factors(out={"V": outV, "X": outX, "W": outW})
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        if step >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
         d2h = V.nbytes + X.nbytes + W.nbytes
     e2e_s = max_over_ranks(statistics.mean(e2e_times), dist)
 

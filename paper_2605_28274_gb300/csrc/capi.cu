@@ -981,23 +981,12 @@ int prepare_residual_ops(sylv_handle* h, const sylv_csr* A, const sylv_csr* B) {
   TRY(alloc_fixed(h, &h->C2rm, m * s));
   sylv::launch_pack<double>(h->stream, n, s, h->side[0].C, h->C1rm);
   sylv::launch_pack<double>(h->stream, m, s, h->lyap ? h->side[0].C : h->side[1].C, h->C2rm);
-  // Gaussian probes: SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller, fixed seed
-  std::vector<double> om((size_t)m * (SKK + SKT));  // range block, then the tail probe blocks
-  uint64_t state = 0x5eedc0de12345678ull;
-  auto next = [&state]() {
-    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-  };
-  for (size_t i = 0; i < om.size(); i += 2) {
-    const double u1 = ((double)(next() >> 11) + 1.0) * 0x1.0p-53, u2 = (double)(next() >> 11) * 0x1.0p-53;
-    const double rr = std::sqrt(-2.0 * std::log(u1));
-    om[i] = rr * std::cos(6.283185307179586 * u2);
-    if (i + 1 < om.size()) om[i + 1] = rr * std::sin(6.283185307179586 * u2);
-  }
-  TRY(alloc_fixed(h, &h->Om, om.size()));
-  CU(cudaMemcpyAsync(h->Om, om.data(), om.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  // Gaussian probes: SplitMix64 (Steele, Lea, Flood 2014) + Box-Muller, fixed seed, drawn on the
+  // device (counter-based: output i of the stream is a function of i alone)
+  const size_t om_count = (size_t)m * (SKK + SKT);  // range block, then the tail probe blocks
+  TRY(alloc_fixed(h, &h->Om, om_count));
+  sylv::launch_gauss_probes(h->stream, h->Om, om_count, 0x5eedc0de12345678ull);
+  CU(cudaGetLastError());
   TRY(alloc_fixed(h, &h->st_sk, 1));
   CU(cudaMallocHost(&h->sk_host, 8 * sizeof(double) + sizeof(DevState)));
   CU(cudaStreamSynchronize(h->stream));

@@ -68,6 +68,8 @@ int launch_ob_gram_cols(cudaStream_t, DevState*, int64_t n, int s, int js, const
 void launch_ob_update_cols(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Z, int64_t ldz,
                            const ObSide&);
 
+// out[0, count) ~ N(0, 1): SplitMix64 from seed and Box-Muller (counter-based, one thread per pair).
+void launch_gauss_probes(cudaStream_t, double* out, size_t count, uint64_t seed);
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -441,4 +441,34 @@ template void launch_tsu<float>(cudaStream_t, int64_t, const float*, int64_t, in
 template void launch_tsu<double>(cudaStream_t, int64_t, const double*, int64_t, int, int, const double*, int, double,
                                  double, double*);
 
+// out[i] ~ N(0, 1), i < count: the SplitMix64 stream (Steele, Lea, Flood, OOPSLA 2014) from
+// seed, whose output j is mix(seed + (j + 1) * 0x9E3779B97F4A7C15), taken in pairs (u1, u2) of
+// 53-bit uniforms (u1 in (0, 1]) and Box-Muller: out[2i] = r cos(2 pi u2), out[2i+1] = r sin(2 pi u2),
+// r = sqrt(-2 ln u1).  One thread per pair.
+namespace {
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j) {
+  uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void __launch_bounds__(NT) gauss_probes_kernel(double* __restrict__ out, int64_t count, uint64_t seed) {
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (2 * i >= count) return;
+  const double u1 = ((double)(splitmix64_at(seed, 2 * (uint64_t)i) >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(splitmix64_at(seed, 2 * (uint64_t)i + 1) >> 11) * 0x1.0p-53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  out[2 * i] = r * cs;
+  if (2 * i + 1 < count) out[2 * i + 1] = r * sn;
+}
+}  // namespace
+
+void launch_gauss_probes(cudaStream_t strm, double* out, size_t count, uint64_t seed) {
+  if (count == 0) return;
+  const int64_t pairs = (int64_t)((count + 1) / 2);
+  gauss_probes_kernel<<<counted((unsigned)((pairs + NT - 1) / NT)), NT, 0, strm>>>(out, (int64_t)count, seed);
+}
+
 }  // namespace sylv
