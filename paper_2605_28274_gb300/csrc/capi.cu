@@ -165,6 +165,14 @@ struct sylv_handle {
   std::vector<std::pair<void*, size_t>> sk;  // sketch scratch buffers (pointer, bytes)
   std::vector<sylv_handle*> subs;  // correction solves of the last mixed solve
   bool is_sub = false;
+  // the last solve's bases as digit planes for the certificate's products (float32 bases, or
+  // float64 ones kept on the CUDA cores); built at the first certificate after a solve
+  void* cert_mem = nullptr;
+  size_t cert_bytes = 0;
+  sylv::ObSide cert_ob[2];
+  bool cert_valid = false, cert_failed = false;
+  int64_t cert_R = 0;            // basis columns the planes hold
+  const void* cert_V = nullptr;  // side 0's basis they were split from
   // batched Lyapunov CG: one internal handle per instance
   std::vector<sylv_handle*> batch;
   sylv::BatchInst* d_insts = nullptr;
@@ -679,6 +687,8 @@ int run_inner(sylv_handle* h, int method, double tol, int maxit, sylv_info* info
   // CG: V_{k+2} in iteration k; CR: one step ahead (L(R_{k+1}) needs V_{k+3}); Arnoldi: two per iteration
   const int maxb = std::max(2, method == M_CG ? maxit + 1 : method == M_CR ? maxit + 2 : 2 * maxit + 1);
   TRY(ensure_capacity(h, method, maxb, maxit + 1));
+  h->cert_valid = false;  // the bases change
+  h->cert_failed = false;
   const int s = (int)h->s;
   cudaStream_t strm = h->stream;
   CU(cudaMemsetAsync(h->st, 0, sizeof(DevState), strm));
@@ -1016,17 +1026,81 @@ std::vector<RoundView> round_views(const sylv_handle* h) {
 
 
 
-// The float64 bases held as digit planes (section: tensor-core basis): X^(T) Min with the basis
-// products on the tensor cores, float64-accurate like the Gram and update of the solve, in
-// 8-column halves of Min.  One round only (the float64 solve has no corrections).
-int apply_X_ob(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, const RoundView& v) {
+// Digit planes of handle x's bases (side 0, side 1) for the certificate's products: the solve's
+// own planes where its float64 Arnoldi bases are on the tensor cores; otherwise (float32 bases of
+// the mixed mode, or float64 bases on the CUDA cores) built once after the solve, when they take
+// at most 30% of the free device memory (the correction solves that follow need the rest), for
+// bases of 2^25 elements and more.
+// Returns false where none are available (the double-float kernels run instead).
+bool cert_planes(sylv_handle* x, const sylv::ObSide** pv, const sylv::ObSide** pw) {
+  const int sw = x->lyap ? 0 : 1;
+  if (!x->mixed && x->side[0].ob.G != nullptr && x->side[sw].ob.G != nullptr) {
+    *pv = &x->side[0].ob;
+    *pw = &x->side[sw].ob;
+    return true;
+  }
+  // small bases (batched instances, tests): the double-float kernels, without the split's launches
+  if (x->cert_failed || x->width <= 0 || (double)x->side[0].n * (double)x->width < 33554432.0) return false;
+  if (x->cert_valid && (x->cert_R != x->width || x->cert_V != x->side[0].V)) x->cert_valid = false;
+  if (!x->cert_valid) {
+    const int s = (int)x->s;
+    const int nb = (int)(x->width / s);
+    const int R = (int)x->width;
+    size_t bytes[2] = {sylv::ob_side_bytes(x->side[0].n, R, s), x->lyap ? 0 : sylv::ob_side_bytes(x->side[1].n, R, s)};
+    const size_t need = bytes[0] + bytes[1] + (size_t)R * sizeof(unsigned long long) + 1024;
+    if (x->cert_bytes < need) {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || (double)need > 0.3 * (double)(free_b + x->cert_bytes) ||
+          !sylv::ob_setup()) {
+        cudaGetLastError();
+        x->cert_failed = true;
+        return false;
+      }
+      if (x->cert_mem) cudaFree(x->cert_mem);
+      x->cert_mem = nullptr;
+      x->cert_bytes = 0;
+      if (cudaMalloc(&x->cert_mem, need) != cudaSuccess) {
+        cudaGetLastError();
+        x->cert_mem = nullptr;
+        x->cert_failed = true;
+        return false;
+      }
+      x->cert_bytes = need;
+    }
+    unsigned char* p = (unsigned char*)x->cert_mem;
+    unsigned long long* mx_all = (unsigned long long*)(((uintptr_t)(p + bytes[0] + bytes[1]) + 255) & ~(uintptr_t)255);
+    for (int i = 0; i < (x->lyap ? 1 : 2); ++i) {
+      Side& sd = x->side[i];
+      sylv::ob_carve(p, sd.n, R, s, x->cert_ob[i]);
+      // zero-filled, so that padding rows and columns hold finite digits
+      if (cudaMemsetAsync(p, 0, bytes[i], x->stream) != cudaSuccess) {
+        cudaGetLastError();
+        x->cert_failed = true;
+        return false;
+      }
+      sylv::launch_ob_split_bases(x->stream, sd.n, s, nb, sd.V, x->mixed, sd.n * s, mx_all, x->cert_ob[i]);
+      p += bytes[i];
+    }
+    if (x->lyap) x->cert_ob[1] = x->cert_ob[0];
+    x->cert_valid = true;
+    x->cert_R = x->width;
+    x->cert_V = x->side[0].V;
+  }
+  *pv = &x->cert_ob[0];
+  *pw = &x->cert_ob[sw];
+  return true;
+}
+
+// X^(T) Min for one round whose bases have digit planes (pv: side 0, pw: side 1): the basis
+// products on the tensor cores, float64-accurate like the Gram and update of the float64 solve,
+// in 8-column pieces of Min; Yout = (first ? 0 : Yout) + the round's term.
+int apply_round_ob(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, const RoundView& v,
+                   const sylv::ObSide& pv, const sylv::ObSide& pw, bool first) {
   int rc = SYLV_OK;
   const int64_t n = h->side[0].n, m = h->lyap ? n : h->side[1].n;
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
-  const Side& sv = h->side[0];
-  const Side& sw = h->side[h->lyap ? 0 : 1];
-  const Side& sin = trans ? sv : sw;    // Min's side: X^T Min = W X^T (V^T Min)
-  const Side& sout = trans ? sw : sv;
+  const sylv::ObSide& oin0 = trans ? pv : pw;  // Min's side: X^T Min = W X^T (V^T Min)
+  const sylv::ObSide& oout0 = trans ? pw : pv;
   const int r = v.nb * v.s;
   static int sms = 0;
   if (sms == 0) {
@@ -1037,14 +1111,14 @@ int apply_X_ob(sylv_handle* h, bool trans, const double* Min, int k, double* You
   }
   constexpr int HW = 8;  // columns per product
   const int64_t nmax = std::max(n, m);
-  const int rmax = std::max(sv.ob.rp, sw.ob.rp);
+  const int rmax = std::max(pv.rp, pw.rp);
   void* scr = sk_buf(h, 24, sylv::ob_cols_scratch_bytes(nmax, rmax, HW), &rc);
   double* part = sk_buf(h, 25, (size_t)sms * r * HW * sizeof(double), &rc);
   double* H8 = sk_buf(h, 26, (size_t)r * HW * sizeof(double), &rc);
   double* P = sk_buf(h, 0, (size_t)r * k * sizeof(double), &rc);
   double* P2 = sk_buf(h, 1, (size_t)r * k * sizeof(double), &rc);
   if (rc) return rc;
-  sylv::ObSide oin = sin.ob, oout = sout.ob;
+  sylv::ObSide oin = oin0, oout = oout0;
   sylv::ob_cols_carve(scr, nmax, rmax, HW, oin);  // the operand digits: scratch shared by both sides
   oout.YB = oin.YB;
   oout.HB = oin.HB;
@@ -1056,7 +1130,7 @@ int apply_X_ob(sylv_handle* h, bool trans, const double* Min, int k, double* You
     PROF(h, KC_RESID_TSG, (double)rows_in * (r * 8.0 + HW * 8.0), fl / (k / HW) * rows_in,
          sylv::launch_ob_gram_cols(h->stream, h->st_sk, rows_in, HW, r, Min + c0, k, oin, part, P, k, c0));
   PROF(h, KC_RESID_SMALL, 0.0, 2.0 * r * r * k, sylv::launch_small_apply(h->stream, r, k, v.Xh, v.lds, trans, P, P2));
-  CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
+  if (first) CU(cudaMemsetAsync(Yout, 0, (size_t)rows_out * k * sizeof(double), h->stream));
   for (int c0 = 0; c0 < k; c0 += HW) {
     CU(cudaMemcpy2DAsync(H8, HW * sizeof(double), P2 + c0, k * sizeof(double), HW * sizeof(double), r,
                          cudaMemcpyDeviceToDevice, h->stream));
@@ -1074,9 +1148,10 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
   auto views = round_views(h);
   if (from_round > 0) views.erase(views.begin(), views.begin() + std::min(from_round, views.size()));
-  if (std::is_same<T, double>::value && views.size() == 1 && views[0].nb > 0 && k % 8 == 0 &&
-      h->side[0].ob.G != nullptr && (h->lyap || h->side[1].ob.G != nullptr))
-    return apply_X_ob(h, trans, Min, k, Yout, views[0]);
+  // the main round's bases as digit planes (the corrections of the mixed mode are narrow: their
+  // products stay on the double-float kernels)
+  const sylv::ObSide *pv = nullptr, *pw = nullptr;
+  const bool main_ob = from_round == 0 && k % 8 == 0 && !views.empty() && views[0].nb > 0 && cert_planes(h, &pv, &pw);
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
   const int max_rc = 0;  // launch_tsg picks the row chunks
@@ -1085,8 +1160,14 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
   double* part = sk_buf(h, 2, (size_t)sylv::tsg_partial_elems(maxw, k) * sizeof(double), &rc);
   if (rc) return rc;
   bool first = true;
-  for (auto& v : views) {
+  for (size_t vi = 0; vi < views.size(); ++vi) {
+    const RoundView& v = views[vi];
     if (v.nb <= 0) continue;
+    if (vi == 0 && main_ob) {
+      TRY(apply_round_ob(h, trans, Min, k, Yout, v, *pv, *pw, first));
+      first = false;
+      continue;
+    }
     const T* Uin = (const T*)(trans ? v.V : v.W);
     const T* Uout = (const T*)(trans ? v.W : v.V);
     const int64_t bsin = trans ? v.bsV : v.bsW, bsout = trans ? v.bsW : v.bsV;
@@ -1602,6 +1683,8 @@ int batch_cg(sylv_handle* h, double tol, int maxit, sylv_info* info) {
     x->method = M_CG;
     x->iters = ds.iters;
     x->width = (int64_t)ds.iters * x->s;
+    x->cert_valid = false;  // new bases
+    x->cert_failed = false;
     x->total_iters = x->iters;
     x->total_width = x->width;
     x->nblocks = ds.iters + 1;
@@ -2200,6 +2283,7 @@ void sylv_destroy(sylv_handle* h) {
   free_sketch(h);
   free_compressed(h);
   free_solve(h);
+  if (h->cert_mem) cudaFree(h->cert_mem);
   for (void* p : h->fixed_allocs) cudaFree(p);
   h->fixed_allocs.clear();
   if (h->st_host) cudaFreeHost(h->st_host);

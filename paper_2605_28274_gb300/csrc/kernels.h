@@ -70,6 +70,12 @@ void launch_ob_update_cols(cudaStream_t, DevState*, int64_t n, int s, int js, co
 
 // out[0, count) ~ N(0, 1): SplitMix64 from seed and Box-Muller (counter-based, one thread per pair).
 void launch_gauss_probes(cudaStream_t, double* out, size_t count, uint64_t seed);
+// Digit planes (both layouts) and column exponents of all nb blocks of a basis already built
+// (float32 or float64 elements), for the true-residual certificate's products; mx_all: scratch
+// of nb * s column maxima.  o: carved by ob_carve for at least nb * s columns.
+void launch_ob_split_bases(cudaStream_t, int64_t n, int s, int nb, const void* V, bool is_float, int64_t bstride,
+                           unsigned long long* mx_all, const ObSide& o);
+
 // Sets the message returned by sylv_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -681,6 +681,66 @@ __global__ void __launch_bounds__(OB_THREADS, 1) ob_kernel(ObArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Sh::TMEM_COLS));
 }
 
+// Column maxima of |V| over the nb blocks of a basis (block b: n x S row-major at V + b bstride,
+// element T) as IEEE bits of the float64 value into mx[b S + t] (zeroed beforehand).  Grid: (row
+// chunks, blocks).
+template <int S, typename T>
+__global__ void __launch_bounds__(NT) ob_colmax_blocks_kernel(int64_t n, const T* __restrict__ V, int64_t bstride,
+                                                              unsigned long long* __restrict__ mx) {
+  __shared__ unsigned long long sm[S];
+  if (threadIdx.x < S) sm[threadIdx.x] = 0;
+  __syncthreads();
+  const T* Vb = V + (int64_t)blockIdx.y * bstride;
+  unsigned long long m[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) m[t] = 0;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      m[t] = max(m[t], (unsigned long long)__double_as_longlong((double)Vb[i * S + t]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    unsigned long long v = m[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&sm[t], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < S && sm[threadIdx.x]) atomicMax(mx + (int64_t)blockIdx.y * S + threadIdx.x, sm[threadIdx.x]);
+}
+
+// Digits of all nb blocks of a basis (element T, float64 or float32: both exact in 53 bits)
+// into both layouts, and the column exponents into vexp; the column maxima in mx[b S + t].
+// Thread per (row, block): grid (row chunks, blocks).
+template <int S, typename T>
+__global__ void __launch_bounds__(NT) ob_vsplit_blocks_kernel(int64_t n, const T* __restrict__ V, int64_t bstride,
+                                                              const unsigned long long* __restrict__ mx,
+                                                              int* __restrict__ vexp, __half* __restrict__ G,
+                                                              __half* __restrict__ U, int64_t plane, int MT, int IT) {
+  const int b = (int)blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int e[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) e[t] = ob_exponent(mx[(int64_t)b * S + t]);
+  if (i == 0)
+    for (int t = 0; t < S; ++t) vexp[b * S + t] = e[t];
+  if (i >= n) return;
+  const T* Vb = V + (int64_t)b * bstride;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    int d[OB_PV];
+    ob_digits<OB_PV, OB_WV>((double)Vb[i * S + t], 0, e[t], d);
+    const int m = b * S + t;
+    const int64_t og = ((i >> 5) * MT + (m >> 7)) * OB_ATILE + ob_cm(m & 127, (int)(i & 31));
+    const int64_t ou = ((int64_t)(m >> 5) * IT + (i >> 7)) * OB_ATILE + ob_cm((int)(i & 127), m & 31);
+#pragma unroll
+    for (int p = 0; p < OB_PV; ++p) {
+      G[p * plane + og] = ob_h(d[p]);
+      U[p * plane + ou] = ob_h(d[p]);
+    }
+  }
+}
+
 // Column maxima of |Y| (n x S, row stride ldy) as IEEE bits (non-negative doubles order like
 // their bit patterns), combined into mx (zeroed beforehand) with atomicMax: the true-residual
 // certificate's blocks, whose producers do not record them.
@@ -950,6 +1010,32 @@ void launch_ob_update_cols(cudaStream_t strm, DevState* st, int64_t n, int s, in
   case SV:                                                                                                    \
     ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);          \
     ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+}
+
+void launch_ob_split_bases(cudaStream_t strm, int64_t n, int s, int nb, const void* V, bool is_float, int64_t bstride,
+                           unsigned long long* mx_all, const ObSide& o) {
+  if (n == 0 || nb == 0) return;
+  cudaMemsetAsync(mx_all, 0, (size_t)nb * s * sizeof(unsigned long long), strm);
+  const unsigned gx = (unsigned)((n + NT - 1) / NT);
+  const dim3 gm((unsigned)std::min<int64_t>(gx, 16), (unsigned)nb);
+  const dim3 gs(gx, (unsigned)nb);
+  __half* G = (__half*)o.G;
+  __half* U = (__half*)o.U;
+  const int MT = o.rp / OB_TM, IT = (int)(o.np / OB_TM);
+#define CASE(SV)                                                                                                   \
+  case SV:                                                                                                         \
+    if (is_float) {                                                                                                \
+      ob_colmax_blocks_kernel<SV, float><<<counted(gm), NT, 0, strm>>>(n, (const float*)V, bstride, mx_all);       \
+      ob_vsplit_blocks_kernel<SV, float><<<counted(gs), NT, 0, strm>>>(n, (const float*)V, bstride, mx_all,        \
+                                                                       o.vexp, G, U, o.plane, MT, IT);             \
+    } else {                                                                                                       \
+      ob_colmax_blocks_kernel<SV, double><<<counted(gm), NT, 0, strm>>>(n, (const double*)V, bstride, mx_all);     \
+      ob_vsplit_blocks_kernel<SV, double><<<counted(gs), NT, 0, strm>>>(n, (const double*)V, bstride, mx_all,      \
+                                                                        o.vexp, G, U, o.plane, MT, IT);            \
+    }                                                                                                              \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
 #undef CASE
