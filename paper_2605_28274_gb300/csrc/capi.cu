@@ -1148,10 +1148,11 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
   const int64_t rows_in = trans ? n : m, rows_out = trans ? m : n;
   auto views = round_views(h);
   if (from_round > 0) views.erase(views.begin(), views.begin() + std::min(from_round, views.size()));
-  // the main round's bases as digit planes (the corrections of the mixed mode are narrow: their
-  // products stay on the double-float kernels)
-  const sylv::ObSide *pv = nullptr, *pw = nullptr;
-  const bool main_ob = from_round == 0 && k % 8 == 0 && !views.empty() && views[0].nb > 0 && cert_planes(h, &pv, &pw);
+  // rounds whose bases have digit planes run on the tensor cores, the others on the double-float
+  // kernels (round 0 is the main solve, round i its i-th correction)
+  std::vector<sylv_handle*> hs{h};
+  for (sylv_handle* sb : h->subs) hs.push_back(sb);
+  if (from_round > 0) hs.erase(hs.begin(), hs.begin() + std::min(from_round, hs.size()));
   int maxw = 1;
   for (auto& v : views) maxw = std::max(maxw, v.nb * v.s);
   const int max_rc = 0;  // launch_tsg picks the row chunks
@@ -1163,7 +1164,8 @@ int apply_X(sylv_handle* h, bool trans, const double* Min, int k, double* Yout, 
   for (size_t vi = 0; vi < views.size(); ++vi) {
     const RoundView& v = views[vi];
     if (v.nb <= 0) continue;
-    if (vi == 0 && main_ob) {
+    const sylv::ObSide *pv = nullptr, *pw = nullptr;
+    if (k % 8 == 0 && vi < hs.size() && cert_planes(hs[vi], &pv, &pw)) {
       TRY(apply_round_ob(h, trans, Min, k, Yout, v, *pv, *pw, first));
       first = false;
       continue;
