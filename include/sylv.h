@@ -92,6 +92,13 @@ typedef struct {
                           Algorithms 4.1/4.2 stops at ||R^_k|| <= stop_margin * tol * ||R^_0|| (0: 0.4), so
                           that the certificate (sylv_info.true_rel_bound <= tol) holds at the first check.
                           1.0 gives the printed test.  SYLV_MIXED inner solves are not affected */
+  int32_t cert_gemm;   /* where the certificate's tall-skinny products with the bases run: 0 auto (on the
+                          tensor cores, on digit planes of the bases -- the float64 Arnoldi bases' own, or
+                          split once after the solve from bases of 2^25 elements or more when they take at
+                          most 30% of the free device memory; otherwise double-float kernels on the FP32
+                          pipes), 1 always the double-float kernels, 2 digit planes at every size (within
+                          the same memory rule).  Both are accurate far below the certified bound's
+                          resolution; the choice changes the time only */
 } sylv_options;
 
 typedef struct {

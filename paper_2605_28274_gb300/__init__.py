@@ -44,7 +44,7 @@ class sylv_options(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("deflate_tol", ctypes.c_double), ("timeout_s", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("no_true_residual", ctypes.c_int32), ("stream_mode", ctypes.c_int32), ("small_gemm", ctypes.c_int32),
-                ("basis_gemm", ctypes.c_int32), ("stop_margin", ctypes.c_double)]
+                ("basis_gemm", ctypes.c_int32), ("stop_margin", ctypes.c_double), ("cert_gemm", ctypes.c_int32)]
 
 
 class sylv_kernel_stat(ctypes.Structure):
@@ -409,8 +409,9 @@ class Solver:
     def __init__(self, A, B, C1, C2, precision: str = "fp64", lyapunov: bool = False, poll_every: int = 0,
                  deflate_tol: float = 0.0, cuda_stream: int = 0, timeout_s: float = 0.0, refine_max: int = 0,
                  profile: bool = False, stream_mode: int = 0, small_gemm: int = 0, basis_gemm: int = 0,
-                 no_true_residual: bool = False, stop_margin: float = 0.0):
+                 no_true_residual: bool = False, stop_margin: float = 0.0, cert_gemm: int = 0):
         o = sylv_default_options()
+        o.cert_gemm = cert_gemm
         o.no_true_residual = 1 if no_true_residual else 0
         o.stop_margin = stop_margin
         o.precision = SYLV_MIXED if precision == "mixed" else SYLV_FP64

@@ -1034,13 +1034,16 @@ std::vector<RoundView> round_views(const sylv_handle* h) {
 // Returns false where none are available (the double-float kernels run instead).
 bool cert_planes(sylv_handle* x, const sylv::ObSide** pv, const sylv::ObSide** pw) {
   const int sw = x->lyap ? 0 : 1;
+  if (x->opt.cert_gemm == 1) return false;
   if (!x->mixed && x->side[0].ob.G != nullptr && x->side[sw].ob.G != nullptr) {
     *pv = &x->side[0].ob;
     *pw = &x->side[sw].ob;
     return true;
   }
   // small bases (batched instances, tests): the double-float kernels, without the split's launches
-  if (x->cert_failed || x->width <= 0 || (double)x->side[0].n * (double)x->width < 33554432.0) return false;
+  if (x->cert_failed || x->width <= 0 ||
+      (x->opt.cert_gemm != 2 && (double)x->side[0].n * (double)x->width < 33554432.0))
+    return false;
   if (x->cert_valid && (x->cert_R != x->width || x->cert_V != x->side[0].V)) x->cert_valid = false;
   if (!x->cert_valid) {
     const int s = (int)x->s;
@@ -1820,6 +1823,7 @@ int sylv_create(const sylv_csr* A, const sylv_csr* B, const double* C1, const do
   if (s < 1 || s > 8) return fail(SYLV_EINVAL, "s must be in [1, 8]");
   if (o.precision != SYLV_FP64 && o.precision != SYLV_MIXED) return fail(SYLV_EINVAL, "unknown precision");
   if (o.basis_gemm < 0 || o.basis_gemm > 2) return fail(SYLV_EINVAL, "basis_gemm must be 0, 1 or 2");
+  if (o.cert_gemm < 0 || o.cert_gemm > 2) return fail(SYLV_EINVAL, "cert_gemm must be 0, 1 or 2");
   TRY(check_csr(A, "A", -1));
   const bool lyap = o.lyapunov != 0;
   if (lyap) {

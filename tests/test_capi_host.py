@@ -42,7 +42,7 @@ def test_strerror_and_defaults(lib):
     assert b"breakdown" in lib.sylv_strerror(4)
     o = ps.sylv_default_options()
     assert o.precision == 0 and o.poll_every == 8 and o.timeout_s == 3600.0 and o.refine_max == 12
-    assert o.small_gemm == 0 and o.basis_gemm == 0
+    assert o.small_gemm == 0 and o.basis_gemm == 0 and o.cert_gemm == 0
 
 
 def _create(A, B, C1, C2, s=None, opt=None):
@@ -78,6 +78,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert _create(A, A, C1, C2, opt=o)[0] == ps.SYLV_EINVAL
     o.precision = 0
     o.basis_gemm = 3
+    assert _create(A, A, C1, C2, opt=o)[0] == ps.SYLV_EINVAL
+    o.basis_gemm = 0
+    o.cert_gemm = 3
     assert _create(A, A, C1, C2, opt=o)[0] == ps.SYLV_EINVAL
     small = wl.laplacian_2d(1)
     assert _create(small, small, np.ones((1, 2)), np.ones((1, 2)))[0] == ps.SYLV_EINVAL  # n < s
