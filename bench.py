@@ -447,7 +447,7 @@ NCU_DRAM_PER_ALGORITHMIC = {
     ("gram", "fp64", False): (318.5, 318.8, "profiles/gram_update_fp64_convdiff64x48_s4.md"),
     ("gram", "fp64", True): (565.3, 436.2, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
     # the update class alternates the full (5 planes) and the second, two-plane update of a step
-    ("update", "fp64", True): (605.2 + 250.8, 2 * 444.6, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
+    ("update", "fp64", True): (605.5 + 250.9, 2 * 444.6, "profiles/ob_gram_update_fp64_convdiff64x48_s4.md"),
 }
 
 
