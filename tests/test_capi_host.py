@@ -103,3 +103,39 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     C1, C2 = wl.rhs(16, 16, 1, 0)
     rc, h = _create(A, A, C1, C2)
     assert rc == ps.SYLV_ECUDA and not h.value
+
+
+def test_struct_layouts_match_the_c_header(tmp_path):
+    """The ctypes mirrors of the C structs (sylv_csr, sylv_options, sylv_info, sylv_kernel_stat)
+    have the header's sizes and field offsets: a field added on one side only would shift every
+    later field of a call silently.  A C program compiled against include/sylv.h prints them."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [ps.sylv_csr, ps.sylv_options, ps.sylv_info, ps.sylv_kernel_stat]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sylv.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            *key, val = ln.split()
+            got[" ".join(key)] = int(val)
+    for st in structs:
+        name = st.__name__
+        assert got[f"{name} size"] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[f"{name} {field}"] == getattr(st, field).offset, (name, field)
