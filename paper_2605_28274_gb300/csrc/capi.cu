@@ -567,11 +567,13 @@ void basis_step(sylv_handle* h, int si, int q, bool lanczos) {
     if (ob) {
       double* Yd = (double*)Y;
       PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_ob_gram(st, h->st, n, s, js, Yd, sd.ob, gpart));
+      // the reduction's last CTA also writes the coefficient digits for the update
       PROF(h, KC_REDUCE, (double)nc * nb * s * s * 8.0, (double)nc * nb * s * s,
-           sylv::launch_reduce_H(st, h->st, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1, false));
+           sylv::launch_ob_reduce_H(st, h->st, si, gpart, nc, nb, s, sd.H, ldh, 0, (int64_t)q * s, Hc, pass == 1,
+                                    sd.ob));
       PROF(h, KC_UPDATE, upd_bytes, upd_flops + (last ? ns * s : 0.0),
            nc = sylv::launch_ob_update(st, h->st, n, s, js, Hc, Yd, sd.ob, last ? spart : nullptr, !last,
-                                       last ? kReorthPlanes : 5));
+                                       last ? kReorthPlanes : 5, true));
       continue;
     }
     PROF(h, KC_GRAM, gram_bytes, gram_flops, nc = sylv::launch_gram<T>(st, h->st, n, s, Vfirst, bstride, nb, Y, gpart));

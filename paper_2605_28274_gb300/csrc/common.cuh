@@ -23,6 +23,8 @@ enum Ticket : int {
   TK_BI_T = 2,
   TK_BI_UPD = 3,
   TK_GP_ZETA = 4,
+  TK_OB_H0 = 5,  // the H reduction + coefficient digits of basis side 0 / 1 (concurrent streams)
+  TK_OB_H1 = 6,
   TK_NUM = 8
 };
 

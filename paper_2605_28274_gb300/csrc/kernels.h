@@ -52,7 +52,12 @@ int launch_ob_gram(cudaStream_t, DevState*, int64_t n, int s, int js, const doub
 // the result into mx[8, 16); V enters through its leading `planes` digit planes (5: all).
 // Returns the number of CTAs.
 int launch_ob_update(cudaStream_t, DevState*, int64_t n, int s, int js, const double* Hc, double* Y, const ObSide&,
-                     double* self_partial, bool ymax, int planes);
+                     double* self_partial, bool ymax, int planes, bool split_done = false);
+// H_{1:j,j} (+)= the sum of the ncta Gram partials (the partial layout of launch_ob_gram), also
+// into Hc, and the digits of Hc for the next launch_ob_update (split_done = true) in the last CTA
+// of the same launch.  side: 0 or 1 (each side's launches count on their own ticket).
+void launch_ob_reduce_H(cudaStream_t, DevState*, int side, const double* partial, int ncta, int nb, int s, double* H,
+                        int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add, const ObSide&);
 
 // Products of the float64 true-residual certificate on a side's digit planes (float64-accurate
 // like the basis kernels).  o: the side's ObSide with YB, HB, ey, eh, mx replaced by scratch of

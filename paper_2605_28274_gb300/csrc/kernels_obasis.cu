@@ -210,16 +210,10 @@ __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64
   }
 }
 
-// Digits of the coefficient block H'(m, t) = 2^{vexp[m]} Hc[m S + t] (m < js; zero up to the
-// next multiple of 32) as the update's other operand, exponents into eh.  One CTA: the column
-// maxima of H' come from integer keys bits(|Hc|) + vexp 2^52, which order like the values.
-// Also zeroes the column maxima mx[0, 16): the ones of the update's result (the next Gram's Y)
-// and of the block that CholQR will scale are combined into them from zero.
 template <int S>
-__global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int js, const double* __restrict__ Hc,
-                                                       const int* __restrict__ vexp, int* __restrict__ eh,
-                                                       __half* __restrict__ HB, unsigned long long* __restrict__ mx) {
-  if (stopped(st)) return;
+__device__ __forceinline__ void ob_hsplit_body(int js, const double* __restrict__ Hc, const int* __restrict__ vexp,
+                                               int* __restrict__ eh, __half* __restrict__ HB,
+                                               unsigned long long* __restrict__ mx) {
   if (threadIdx.x < 16) mx[threadIdx.x] = 0;
   constexpr int NP = ObShape<S>::NP;
   __shared__ long long kmax[NT / 32][S];
@@ -233,7 +227,8 @@ __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int j
     if (sc == OB_EXP_BAD) bad = 1;
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(Hc[(int64_t)m * S + t]) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong(__ldcg(Hc + (int64_t)m * S + t)) & 0x7FFFFFFFFFFFFFFFull;
       const int ex = (int)(b >> 52);
       if (ex == 0x7FF) bad = 1;
       else if (ex != 0 && sc != OB_EXP_BAD) km[t] = max(km[t], (long long)b + ((long long)sc << 52));
@@ -263,12 +258,66 @@ __global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int j
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       int d[OB_PY];
-      const double x = (m < js && sc != OB_EXP_BAD) ? Hc[(int64_t)m * S + t] : 0.0;
+      const double x = (m < js && sc != OB_EXP_BAD) ? __ldcg(Hc + (int64_t)m * S + t) : 0.0;
       ob_digits<OB_PY, OB_WY>(x, sc, esh[t], d);
 #pragma unroll
       for (int q = 0; q < OB_PY; ++q) HB[base + ob_cm(q * S + t, m & 31)] = ob_h(d[q]);
     }
   }
+}
+
+// Digits of the coefficient block H'(m, t) = 2^{vexp[m]} Hc[m S + t] (m < js; zero up to the
+// next multiple of 32) as the update's other operand, exponents into eh.  One CTA: the column
+// maxima of H' come from integer keys bits(|Hc|) + vexp 2^52, which order like the values.
+// Also zeroes the column maxima mx[0, 16): the ones of the update's result (the next Gram's Y)
+// and of the block that CholQR will scale are combined into them from zero.
+template <int S>
+__global__ void __launch_bounds__(NT) ob_hsplit_kernel(const DevState* st, int js, const double* __restrict__ Hc,
+                                                       const int* __restrict__ vexp, int* __restrict__ eh,
+                                                       __half* __restrict__ HB, unsigned long long* __restrict__ mx) {
+  if (stopped(st)) return;
+  ob_hsplit_body<S>(js, Hc, vexp, eh, HB, mx);
+}
+
+// The BCGS2 coefficient block of one pass in one launch: H_{1:j,j} (+)= the sum of the Gram
+// partials (partial[c E + e], E = nb S S, c < ncta, summed in a fixed order), also into Hc
+// (js x S row-major), then the last CTA to finish (ticket) writes Hc's digits for the update
+// (ob_hsplit_body).  256 threads: 8 outputs x 32 partial groups per CTA.
+constexpr int OB_RED_E = 8, OB_RED_G = 32;
+template <int S>
+__global__ void __launch_bounds__(NT) ob_reduce_hsplit_kernel(DevState* st, const double* __restrict__ partial,
+                                                              int ncta, int nb, double* __restrict__ H, int64_t ldh,
+                                                              int64_t row0, int64_t col0, double* __restrict__ Hc,
+                                                              int add, unsigned int* ticket, const int* __restrict__ vexp,
+                                                              int* __restrict__ eh, __half* __restrict__ HB,
+                                                              unsigned long long* __restrict__ mx) {
+  if (stopped(st)) return;
+  __shared__ double part[OB_RED_G][OB_RED_E];
+  __shared__ int last_sh;
+  const int E = nb * S * S;
+  const int el = threadIdx.x % OB_RED_E, g = threadIdx.x / OB_RED_E;
+  const int e = blockIdx.x * OB_RED_E + el;
+  double v0 = 0.0, v1 = 0.0;
+  if (e < E) {
+    int c = g;
+    for (; c + OB_RED_G < ncta; c += 2 * OB_RED_G) {
+      v0 += partial[(int64_t)c * E + e];
+      v1 += partial[(int64_t)(c + OB_RED_G) * E + e];
+    }
+    if (c < ncta) v0 += partial[(int64_t)c * E + e];
+  }
+  part[g][el] = v0 + v1;
+  __syncthreads();
+  if (g == 0 && e < E) {
+    double vs = 0.0;
+    for (int q = 0; q < OB_RED_G; ++q) vs += part[q][el];
+    Hc[e] = vs;
+    const int b = e / (S * S), r = e - b * S * S, u = r / S, t = r - u * S;
+    double* h = H + (row0 + (int64_t)b * S + u) + (col0 + t) * ldh;
+    *h = add ? (*h + vs) : vs;
+  }
+  if (!last_cta(ticket, &last_sh)) return;
+  ob_hsplit_body<S>(nb * S, Hc, vexp, eh, HB, mx);
 }
 
 __device__ __forceinline__ bool ob_wait(uint32_t bar, uint32_t phase) {
@@ -895,7 +944,7 @@ int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, co
 }
 
 int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Hc, double* Y,
-                     const ObSide& o, double* self_partial, bool ymax, int planes) {
+                     const ObSide& o, double* self_partial, bool ymax, int planes, bool split_done) {
   const int itn = (int)std::max<int64_t>(1, (n + OB_TM - 1) / OB_TM);
   const int grid = std::min(itn, ob_sms());
   ObArgs a{};
@@ -917,7 +966,8 @@ int launch_ob_update(cudaStream_t strm, DevState* st, int64_t n, int s, int js, 
   a.add = 0;
 #define CASE(SV)                                                                                              \
   case SV:                                                                                                    \
-    ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);          \
+    if (!split_done)                                                                                          \
+      ob_hsplit_kernel<SV><<<counted(1), NT, 0, strm>>>(st, js, Hc, o.vexp, o.eh, (__half*)o.HB, o.mx);        \
     ob_kernel<SV, false><<<counted(grid), OB_THREADS, ObShape<SV>::SMEM, strm>>>(a);                          \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
@@ -1036,6 +1086,21 @@ void launch_ob_split_bases(cudaStream_t strm, int64_t n, int s, int nb, const vo
       ob_vsplit_blocks_kernel<SV, double><<<counted(gs), NT, 0, strm>>>(n, (const double*)V, bstride, mx_all,      \
                                                                         o.vexp, G, U, o.plane, MT, IT);            \
     }                                                                                                              \
+    break;
+  switch (s) { SYLV_OB_S_CASES(CASE) }
+#undef CASE
+}
+
+void launch_ob_reduce_H(cudaStream_t strm, DevState* st, int side, const double* partial, int ncta, int nb, int s,
+                        double* H, int64_t ldh, int64_t row0, int64_t col0, double* Hc, bool add, const ObSide& o) {
+  const int E = nb * s * s;
+  const unsigned grid = (unsigned)((E + OB_RED_E - 1) / OB_RED_E);
+  unsigned int* ticket = &st->tickets[side == 0 ? TK_OB_H0 : TK_OB_H1];
+#define CASE(SV)                                                                                                    \
+  case SV:                                                                                                          \
+    ob_reduce_hsplit_kernel<SV><<<counted(grid), NT, 0, strm>>>(st, partial, ncta, nb, H, ldh, row0, col0, Hc,      \
+                                                                add ? 1 : 0, ticket, o.vexp, o.eh, (__half*)o.HB,   \
+                                                                o.mx);                                              \
     break;
   switch (s) { SYLV_OB_S_CASES(CASE) }
 #undef CASE
