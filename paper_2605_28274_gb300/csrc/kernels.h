@@ -117,13 +117,7 @@ int launch_update(cudaStream_t, const DevState*, int64_t n, int s, const T* V, i
 template <typename T>
 int launch_selfgram(cudaStream_t, const DevState*, int64_t n, int s, const T* Y, double* self_partial);
 
-// Y <- Y Rinv (Rinv s x s upper triangular, column-major), optionally with partials of
-// the new Y^T Y.  Returns the number of CTAs.
-template <typename T>
-int launch_scale(cudaStream_t, const DevState*, int64_t n, int s, T* Y, const T* RinvT, double* self_partial,
-                 unsigned long long* colmax = nullptr);
-
-// One Cholesky pass of CholQR2 on the s x s Gram reduced from the partials.
+// Arguments of one Cholesky pass of CholQR2 on the s x s Gram reduced from the partials.
 struct CholArgs {
   int side;           // 0: A basis, 1: B^T basis (exhaustion flag slot)
   int pass;           // 1 or 2
@@ -140,12 +134,11 @@ struct CholArgs {
   double* Rout;       // pass 2: R2 R1 also stored here (s x s, ld s), or NULL
   int setup;          // QR of C1/C2: any loss of rank is a breakdown
 };
-void launch_chol(cudaStream_t, DevState*, const double* self_partial, int ncta, const CholArgs&);
 // One CholQR pass in one launch: Cholesky of the s x s Gram summed from partial_in (ncta_in
-// partials, as launch_chol) in every CTA, then Y <- Y R^{-1} over the n x s block, with the
+// Gram partials) in every CTA, then Y <- Y R^{-1} over the n x s block, with the
 // optional per-CTA partial Y^T Y of the result into partial_out (a different buffer from
 // partial_in, at least 2 x SMs x s^2 doubles) and column maxima into colmax.  The factors are
-// stored as by launch_chol.  Returns the number of CTAs (the partial_out count).
+// stored by CTA 0 as the fields of CholArgs say.  Returns the number of CTAs (the partial_out count).
 template <typename T>
 int launch_cholscale(cudaStream_t, DevState*, const double* partial_in, int ncta_in, const CholArgs&, int64_t n, T* Y,
                      double* partial_out, unsigned long long* colmax);

@@ -420,68 +420,6 @@ __global__ void __launch_bounds__(NT) selfgram_kernel(const DevState* st, int64_
   block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
 }
 
-// colmax (float64 only, may be null): the column maxima of |result| as IEEE bits (atomicMax).
-template <typename T, int S, bool SELF>
-__global__ void __launch_bounds__(NT) scale_kernel(const DevState* st, int64_t n, T* __restrict__ Y,
-                                                   const T* __restrict__ Rinv, double* __restrict__ partial,
-                                                   unsigned long long* __restrict__ colmax) {
-  if (stopped(st)) return;
-  __shared__ T rs[S * S];
-  __shared__ double sh[(NT / 32) * S * S];
-  __shared__ unsigned long long smx[S];
-  unsigned long long zmax[S];
-#pragma unroll
-  for (int t = 0; t < S; ++t) zmax[t] = 0;
-  if (threadIdx.x < S) smx[threadIdx.x] = 0;
-  if (threadIdx.x < S * S) rs[threadIdx.x] = Rinv[threadIdx.x];
-  __syncthreads();
-  using A = typename AccOf<T>::type;
-  A acc[S][S];
-  if constexpr (SELF) {
-#pragma unroll
-    for (int u = 0; u < S; ++u)
-#pragma unroll
-      for (int t = 0; t < S; ++t) acc[u][t] = 0;
-  }
-  for (int64_t row = (int64_t)blockIdx.x * NT + threadIdx.x; row < n; row += (int64_t)gridDim.x * NT) {
-    T y[S], z[S];
-    ld_row<T, S>(Y + row * S, y);
-#pragma unroll
-    for (int t = 0; t < S; ++t) {
-      T a = 0;
-#pragma unroll
-      for (int u = 0; u <= t; ++u) a += y[u] * rs[u + t * S];
-      z[t] = a;
-    }
-    st_row<T, S>(Y + row * S, z);
-    if constexpr (SELF) {
-#pragma unroll
-      for (int u = 0; u < S; ++u)
-#pragma unroll
-        for (int t = u; t < S; ++t) acc[u][t] += (A)z[u] * (A)z[t];  // upper triangle
-    }
-    if (colmax != nullptr) {
-#pragma unroll
-      for (int t = 0; t < S; ++t)
-        zmax[t] = max(zmax[t], (unsigned long long)__double_as_longlong(fabs((double)z[t])));
-    }
-  }
-  if constexpr (SELF) {
-    mirror_upper<A, S>(acc);
-    block_reduce_tile<A, S>(acc, partial + (int64_t)blockIdx.x * S * S, sh);
-  }
-  if (colmax != nullptr) {
-#pragma unroll
-    for (int t = 0; t < S; ++t) {
-      unsigned long long v = zmax[t];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if ((threadIdx.x & 31) == 0 && v) atomicMax(&smx[t], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < S && smx[threadIdx.x]) atomicMax(colmax + threadIdx.x, smx[threadIdx.x]);
-  }
-}
 
 // ---------------------------------------------------------------- CholQR pass
 // Single CTA: G = sum of the partial Gram tiles; nu^2 = ||H_{1:j,j}||^2 + tr(G);
@@ -659,12 +597,6 @@ __device__ int chol_block(DevState* st, const double* __restrict__ partial, int 
   return out;
 }
 
-__global__ void __launch_bounds__(NT) chol_kernel(DevState* st, const double* __restrict__ partial, int ncta,
-                                                  CholArgs a) {
-  if (stopped(st)) return;
-  __shared__ double Ri[64];
-  chol_block(st, partial, ncta, a, true, Ri);
-}
 
 // One CholQR pass in one launch: every CTA forms the s x s Gram from the partials of the
 // previous kernel and factors it (chol_block: the same factors in every CTA; CTA 0 stores
@@ -840,25 +772,7 @@ int launch_selfgram(cudaStream_t strm, const DevState* st, int64_t n, int s, con
   return grid;
 }
 
-template <typename T>
-int launch_scale(cudaStream_t strm, const DevState* st, int64_t n, int s, T* Y, const T* RinvT, double* self_partial,
-                 unsigned long long* colmax) {
-  const int grid = grid_for(n, NT, 4 * num_sms());
-#define CASE(SV)                                                                               \
-  case SV:                                                                                     \
-    if (self_partial)                                                                          \
-      scale_kernel<T, SV, true><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, self_partial, colmax); \
-    else                                                                                       \
-      scale_kernel<T, SV, false><<<counted(grid), NT, 0, strm>>>(st, n, Y, RinvT, nullptr, colmax);     \
-    break;
-  switch (s) { SYLV_S_CASES(CASE) }
-#undef CASE
-  return grid;
-}
 
-void launch_chol(cudaStream_t strm, DevState* st, const double* self_partial, int ncta, const CholArgs& a) {
-  chol_kernel<<<counted(1), NT, 0, strm>>>(st, self_partial, ncta, a);
-}
 
 template <typename T>
 int launch_cholscale(cudaStream_t strm, DevState* st, const double* partial_in, int ncta_in, const CholArgs& a,
@@ -910,8 +824,6 @@ void launch_convert(cudaStream_t strm, int64_t count, const double* src, T* dst)
   template int launch_update<T>(cudaStream_t, const DevState*, int64_t, int, const T*, int64_t, int,             \
                                 const double*, T*, double*);                                                     \
   template int launch_selfgram<T>(cudaStream_t, const DevState*, int64_t, int, const T*, double*);               \
-  template int launch_scale<T>(cudaStream_t, const DevState*, int64_t, int, T*, const T*, double*,              \
-                                unsigned long long*);                                                            \
   template int launch_cholscale<T>(cudaStream_t, DevState*, const double*, int, const CholArgs&, int64_t, T*,    \
                                    double*, unsigned long long*);                                                \
   template void launch_pack<T>(cudaStream_t, int64_t, int, const double*, T*);                                  \
