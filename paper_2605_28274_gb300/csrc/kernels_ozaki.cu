@@ -85,9 +85,8 @@ __device__ __forceinline__ int oz_in_block(int i, int k) {
 // x(i, k) = X[i * si + k * sk], i < R, k < K.  A CTA covers 32 rows x 64 values of k (8 per
 // thread) and combines into mx (zeroed beforehand) with atomicMax: the result does not depend
 // on the order.
-__global__ void __launch_bounds__(NT) oz_max_kernel(const DevState* st, const double* __restrict__ X, int64_t si,
-                                                    int64_t sk, int R, int K, unsigned long long* __restrict__ mx) {
-  if (stopped(st)) return;
+__device__ __forceinline__ void oz_max_body(const double* __restrict__ X, int64_t si, int64_t sk, int R, int K,
+                                            unsigned long long* __restrict__ mx) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   const int k0 = blockIdx.y * 64 + (threadIdx.x >> 5) * 8;
   if (i >= R) return;
@@ -111,12 +110,9 @@ __device__ __forceinline__ int oz_exponent(unsigned long long m) {
 // Digits of x(i, k) for one row i and 8 consecutive k: thread per (i, k group).  Writes the
 // 8 digit planes, each as one 16-byte core-matrix row.  Layout of a plane: blocks
 // [row tile][k chunk] of T x 64, T = rows per tile.
-__global__ void __launch_bounds__(NT) oz_split_kernel(const DevState* st, const double* __restrict__ X, int64_t si,
-                                                      int64_t sk, int R, int K, int Rp, int Kp, int T,
-                                                      const unsigned long long* __restrict__ mx,
-                                                      int* __restrict__ ex, __nv_bfloat16* __restrict__ dig,
-                                                      int64_t plane) {
-  if (stopped(st)) return;
+__device__ __forceinline__ void oz_split_body(const double* __restrict__ X, int64_t si, int64_t sk, int R, int K,
+                                              int Rp, int Kp, int T, const unsigned long long* __restrict__ mx,
+                                              int* __restrict__ ex, __nv_bfloat16* __restrict__ dig, int64_t plane) {
   const int kg_n = Kp / 8;
   const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (t >= (int64_t)Rp * kg_n) return;
@@ -172,6 +168,38 @@ __global__ void __launch_bounds__(NT) oz_split_kernel(const DevState* st, const 
     }
     *reinterpret_cast<uint4*>(dig + (int64_t)(p - 1) * plane + blk + inb) = *reinterpret_cast<const uint4*>(v);
   }
+}
+
+// The four operands of one small-operator call (pass 1: H, Z; pass 2: Z, G^T), so that their
+// column maxima and their digits take one launch each instead of four.
+struct OzOp {
+  const double* X;  // x(i, k) = X[i si + k sk], i < R, k < K
+  int64_t si, sk;
+  int R, Rp, T;     // rows, rows padded to the tile, rows per tile
+  unsigned long long* mx;
+  int* ex;
+  __nv_bfloat16* dig;
+  int64_t plane;
+};
+struct OzOps {
+  OzOp op[4];
+  int K, Kp;
+};
+
+// Column maxima of the four operands: blockIdx.z selects the operand; CTAs beyond an
+// operand's extent find no rows or no k and return without writing.
+__global__ void __launch_bounds__(NT) oz_max4_kernel(const DevState* st, OzOps ops) {
+  if (stopped(st)) return;
+  const OzOp& o = ops.op[blockIdx.z];
+  oz_max_body(o.X, o.si, o.sk, o.R, ops.K, o.mx);
+}
+
+// Digits of the four operands: blockIdx.y selects the operand (threads beyond its padded
+// extent return).
+__global__ void __launch_bounds__(NT) oz_split4_kernel(const DevState* st, OzOps ops) {
+  if (stopped(st)) return;
+  const OzOp& o = ops.op[blockIdx.y];
+  oz_split_body(o.X, o.si, o.sk, o.R, ops.K, o.Rp, ops.Kp, o.T, o.mx, o.ex, o.dig, o.plane);
 }
 
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t phase) {
@@ -475,11 +503,12 @@ int oz_pad(int x, int t) { return (x + t - 1) / t * t; }
 
 size_t ozaki_scratch_bytes(int rmax) {
   const int Mp = oz_pad(rmax, OZ_TM), Kp = oz_pad(rmax, OZ_KC * OZ_FOLD);
-  // two digit sets (A and B operand) of Mp x Kp BF16 x 8 planes, exponents, omega partials,
-  // k-split partial sums (two int64 per output of at most OZ_MAX_SPLIT_CTAS tiles)
-  return (size_t)2 * OZ_P * Mp * Kp * 2 + (size_t)2 * Mp * sizeof(int) + (size_t)4 * Mp * sizeof(unsigned long long) +
+  // two passes x two digit sets (A and B operand) of Mp x Kp BF16 x 8 planes, their exponents,
+  // column maxima, omega partials, k-split partial sums (two int64 per output of at most
+  // OZ_MAX_SPLIT_CTAS tiles)
+  return (size_t)4 * OZ_P * Mp * Kp * 2 + (size_t)4 * Mp * sizeof(int) + (size_t)4 * Mp * sizeof(unsigned long long) +
          (size_t)2 * OZ_OMEGA_CTAS * sizeof(double) + (size_t)OZ_MAX_SPLIT_CTAS * OZ_TM * OZ_TN * 2 * sizeof(long long) +
-         512;
+         1024;
 }
 
 bool ozaki_setup() {
@@ -497,11 +526,16 @@ int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const 
   const int Kp = oz_pad(r, OZ_KC * OZ_FOLD);  // contraction length
   const int nkc = Kp / OZ_KC;
   const int64_t planeA = (int64_t)Mp * Kp, planeB = (int64_t)Np * Kp;
-  __nv_bfloat16* Ad = (__nv_bfloat16*)scratch;
-  __nv_bfloat16* Bd = Ad + (size_t)OZ_P * planeA;
-  int* ea = (int*)(Bd + (size_t)OZ_P * planeB);
-  int* fb = ea + Mp;
-  unsigned long long* mx = (unsigned long long*)(((uintptr_t)(fb + Mp) + 15) & ~(uintptr_t)15);  // 4 x Mp
+  // digits of both passes' operands (pass 1: A = H, B = Z; pass 2: A = Z, B = G^T), split up front
+  __nv_bfloat16* Ad1 = (__nv_bfloat16*)scratch;
+  __nv_bfloat16* Bd1 = Ad1 + (size_t)OZ_P * planeA;
+  __nv_bfloat16* Ad2 = Bd1 + (size_t)OZ_P * planeB;
+  __nv_bfloat16* Bd2 = Ad2 + (size_t)OZ_P * planeA;
+  int* ea1 = (int*)(Bd2 + (size_t)OZ_P * planeB);
+  int* fb1 = ea1 + Mp;
+  int* ea2 = fb1 + Mp;
+  int* fb2 = ea2 + Mp;
+  unsigned long long* mx = (unsigned long long*)(((uintptr_t)(fb2 + Mp) + 15) & ~(uintptr_t)15);  // 4 x Mp
   double* partials = (double*)(mx + 4 * (size_t)Mp);
   long long* kpart = (long long*)(((uintptr_t)(partials + 2 * OZ_OMEGA_CTAS) + 255) & ~(uintptr_t)255);
   // k splits: the tiles alone leave SMs idle at most orders (28 tiles at r = 448); split each
@@ -527,27 +561,26 @@ int launch_sylv_gemm_ozaki(cudaStream_t strm, DevState* st, int r, int s, const 
   const dim3 grid(tm, tn, ks);
   const unsigned gr = (unsigned)(((int64_t)rp * rp + NT - 1) / NT);
   const dim3 gmA((unsigned)((rp + 31) / 32), (unsigned)((r + 63) / 64));
-  const dim3 gmZ((unsigned)((r + 31) / 32), (unsigned)((r + 63) / 64));
   const unsigned gsA = (unsigned)(((int64_t)Mp * (Kp / 8) + NT - 1) / NT);
-  const unsigned gsB = (unsigned)(((int64_t)Np * (Kp / 8) + NT - 1) / NT);
   cudaMemsetAsync(mx, 0, (size_t)4 * Mp * sizeof(unsigned long long), strm);
-  // pass 1: Out = H Z  (A(a, c) = H[a + c ldh], B(b, c) = Z[c + b lds]), all rp x rp outputs
-  oz_max_kernel<<<counted(gmA), NT, 0, strm>>>(st, H, 1, ldh, rp, r, mx);
-  oz_max_kernel<<<counted(gmZ), NT, 0, strm>>>(st, Z, lds, 1, r, r, mx + Mp);
-  oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, H, 1, ldh, rp, r, Mp, Kp, OZ_TM, mx, ea, Ad, planeA);
-  oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, Z, lds, 1, r, r, Np, Kp, OZ_TN, mx + Mp, fb, Bd, planeB);
-  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 1, s, Out, lds, rp,
-                                                               rp, 0, kpart);
-  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea, fb, Out, lds, rp, rp, 0);
+  // pass 1: Out = H Z  (A(a, c) = H[a + c ldh], B(b, c) = Z[c + b lds]), all rp x rp outputs;
   // pass 2: Out += Z G^T  (A(a, c) = Z[a + c lds], B(b, c) = G[b + c ldh]), rows a < r
-  oz_max_kernel<<<counted(gmZ), NT, 0, strm>>>(st, Z, 1, lds, r, r, mx + 2 * (size_t)Mp);
-  oz_max_kernel<<<counted(gmA), NT, 0, strm>>>(st, G, 1, ldh, rp, r, mx + 3 * (size_t)Mp);
-  oz_split_kernel<<<counted(gsA), NT, 0, strm>>>(st, Z, 1, lds, r, r, Mp, Kp, OZ_TM, mx + 2 * (size_t)Mp, ea, Ad, planeA);
-  oz_split_kernel<<<counted(gsB), NT, 0, strm>>>(st, G, 1, ldh, rp, r, Np, Kp, OZ_TN, mx + 3 * (size_t)Mp, fb, Bd, planeB);
-  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad, planeA, Bd, planeB, nkc, ea, fb, 2, s, Out, lds, r,
-                                                               rp, 1, kpart);
-  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea, fb, Out, lds, r, rp, 1);
-  int launched = ks > 1 ? 12 : 10;
+  OzOps ops{};
+  ops.K = r;
+  ops.Kp = Kp;
+  ops.op[0] = {H, 1, ldh, rp, Mp, OZ_TM, mx, ea1, Ad1, planeA};
+  ops.op[1] = {Z, lds, 1, r, Np, OZ_TN, mx + Mp, fb1, Bd1, planeB};
+  ops.op[2] = {Z, 1, lds, r, Mp, OZ_TM, mx + 2 * (size_t)Mp, ea2, Ad2, planeA};
+  ops.op[3] = {G, 1, ldh, rp, Np, OZ_TN, mx + 3 * (size_t)Mp, fb2, Bd2, planeB};
+  oz_max4_kernel<<<counted(dim3(gmA.x, gmA.y, 4)), NT, 0, strm>>>(st, ops);
+  oz_split4_kernel<<<counted(dim3(gsA, 4)), NT, 0, strm>>>(st, ops);
+  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad1, planeA, Bd1, planeB, nkc, ea1, fb1, 1, s, Out,
+                                                               lds, rp, rp, 0, kpart);
+  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea1, fb1, Out, lds, rp, rp, 0);
+  oz_gemm_kernel<<<counted(grid), OZ_THREADS, OZ_SMEM, strm>>>(st, Ad2, planeA, Bd2, planeB, nkc, ea2, fb2, 2, s, Out,
+                                                               lds, r, rp, 1, kpart);
+  if (ks > 1) oz_reduce_kernel<<<counted(gr), NT, 0, strm>>>(st, kpart, ks, tm, tn, ea2, fb2, Out, lds, r, rp, 1);
+  int launched = ks > 1 ? 6 : 4;
   if (omega) {
     const int64_t E = (int64_t)rp * rp;
     const unsigned g = (unsigned)std::min<int64_t>((E + NT - 1) / NT, OZ_OMEGA_CTAS);
