@@ -185,28 +185,40 @@ __global__ void __launch_bounds__(NT) ob_vsplit_kernel(const DevState* st, int64
   }
 }
 
-// Digits of the block Y (row-major n x S) as the Gram's other operand: digit column
-// q S + t of row (k =) i; exponents into ey.  One thread per row.
+// Digits of the block Y (n x S, row stride ldy) as the Gram's other operand: digit column
+// q S + t of row (k =) i; exponents into ey.  Thread per (8 consecutive rows, column t): the 8
+// rows' digits of a plane are one 16-byte core-matrix row, stored at once.  Rows from n up to
+// the next multiple of 32 (the rest of the Gram's last 32-row chunk) get zero digits, so the
+// operand never depends on what the buffer held before.
 template <int S>
 __global__ void __launch_bounds__(NT) ob_ysplit_kernel(const DevState* st, int64_t n, const double* __restrict__ Y,
                                                        int64_t ldy, const unsigned long long* __restrict__ mx,
                                                        int* __restrict__ ey, __half* __restrict__ YB) {
   if (stopped(st)) return;
   constexpr int NP = ObShape<S>::NP;
-  const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
-  int e[S];
+  const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  if (tid < S) ey[tid] = ob_exponent(mx[tid]);
+  const int64_t g = tid / S;
+  const int t = (int)(tid - g * S);
+  const int64_t i0 = g * 8;
+  if (i0 >= (n + 31) / 32 * 32) return;
+  const int e = ob_exponent(mx[t]);
+  int d[OB_PY][8];
 #pragma unroll
-  for (int t = 0; t < S; ++t) e[t] = ob_exponent(mx[t]);
-  if (i == 0)
-    for (int t = 0; t < S; ++t) ey[t] = e[t];
-  if (i >= n) return;
-  const int64_t base = (i >> 5) * (int64_t)(NP * OB_KC);
+  for (int j = 0; j < 8; ++j) {
+    int dj[OB_PY];
+    const double x = i0 + j < n ? Y[(i0 + j) * ldy + t] : 0.0;
+    ob_digits<OB_PY, OB_WY>(x, 0, e, dj);
 #pragma unroll
-  for (int t = 0; t < S; ++t) {
-    int d[OB_PY];
-    ob_digits<OB_PY, OB_WY>(Y[i * ldy + t], 0, e[t], d);
+    for (int q = 0; q < OB_PY; ++q) d[q][j] = dj[q];
+  }
+  const int64_t base = (i0 >> 5) * (int64_t)(NP * OB_KC);
 #pragma unroll
-    for (int q = 0; q < OB_PY; ++q) YB[base + ob_cm(q * S + t, (int)(i & 31))] = ob_h(d[q]);
+  for (int q = 0; q < OB_PY; ++q) {
+    __align__(16) __half v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = ob_h(d[q][j]);
+    *reinterpret_cast<uint4*>(YB + base + ob_cm(q * S + t, (int)(i0 & 31))) = *reinterpret_cast<const uint4*>(v);
   }
 }
 
@@ -909,7 +921,8 @@ void launch_ob_split_basis(cudaStream_t strm, const DevState* st, int64_t n, int
 
 int launch_ob_gram(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Y, const ObSide& o,
                    double* partial) {
-  const unsigned gs = (unsigned)std::max<int64_t>(1, (n + NT - 1) / NT);
+  // digit split: a thread per (8 rows, column) up to the next multiple of 32 rows
+  const unsigned gs = (unsigned)std::max<int64_t>(1, ((n + 31) / 32 * 4 * s + NT - 1) / NT);
   const int mtv = (js + OB_TM - 1) / OB_TM;
   const int kcn = (int)std::max<int64_t>(1, (n + OB_KC - 1) / OB_KC);
   int ks = std::max(1, std::min(kcn, ob_sms() / mtv));
@@ -999,7 +1012,8 @@ void ob_cols_carve(void* mem, int64_t n_max, int R_max, int S, ObSide& o) {
 int launch_ob_gram_cols(cudaStream_t strm, DevState* st, int64_t n, int s, int js, const double* Y, int64_t ldy,
                         const ObSide& o, double* partial, double* P, int64_t ldp, int col0) {
   if (js <= 0) return 0;
-  const unsigned gs = (unsigned)std::max<int64_t>(1, (n + NT - 1) / NT);
+  // digit split: a thread per (8 rows, column) up to the next multiple of 32 rows
+  const unsigned gs = (unsigned)std::max<int64_t>(1, ((n + 31) / 32 * 4 * s + NT - 1) / NT);
   const unsigned gm = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (n + NT - 1) / NT), 2 * ob_sms());
   const int mtv = (js + OB_TM - 1) / OB_TM;
   const int kcn = (int)std::max<int64_t>(1, (n + OB_KC - 1) / OB_KC);
